@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark: solid-substep particle-updates/s of the multi-time-step SPH scheme.
+
+Workload: the 3D J2-plasticity cylinder (L = 50 mm, R = 5 mm, dx = 0.25 mm,
+252,800 particles, Wendland C2 h = 1.3 dx, saturation hardening with seeded
+sigma0/sigma_inf, both 3-layer end caps pulled to +-15 % over 500 slow
+steps, eta = 1e4, kinetic-energy stop at 5e-3 of the reference energy).
+One benchmark step = one slow step (Sec. 4.2): the load jump followed by
+damped substeps until the kinetic-energy criterion holds.  Inputs are
+synthetic (seeded lattice + jitter); the working set (~0.2-0.3 GB) is larger
+than L2, so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle (the only reference there is: the
+paper ships no code) on the host cores on a bounded sample of the same
+workload.
+
+Multi-GPU: one single body does not shard (halo exchanges every substep), so
+N ranks run N independent replicas (weak scaling); the value is the sum over
+ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solid-substep particle-updates/s; time-to-equilibrium vs plain FP64 at tol"
+UNIT = "particle-substeps/s"
+STAGES = {1: "k_stress", 2: "k_force", 3: "k_damp", 4: "k_drift"}
+# algorithmic bytes per particle per launch, 3D mixed precision, J2 (per-pass
+# counts: CSR int32 indices 4k with k = 80, X, u, B0, PB, v, plastic state)
+ALGO_BYTES_3D_MIXED = {1: 428 + 56, 2: 392, 3: 244, 4: 244}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--check-every", type=int, default=64)
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="slow steps of the plain-FP64 GPU comparison (0 = skip)")
+    ap.add_argument("--cpu-substeps", type=int, default=2,
+                    help="substeps in the oracle CPU-baseline sample (0 = skip)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--ref-substeps", type=int, default=1,
+                    help="oracle substeps per reference-arm step")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2309_04010_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, n: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
+    to n particles; None when the summary is missing or for other sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_hash") != source_hash():
+            return None
+        k = d["kernels"][kernel]
+        return k["dram_bytes_per_particle"] * n
+    except Exception:
+        return None
+
+
+def cylinder_case():
+    from synth import bodies as B
+    return B.cylinder3d()
+
+
+def oracle_sample(case, substeps: int):
+    """Oracle particle-substeps/s on the host cores (setup not timed)."""
+    import oracle
+    ob = oracle.body_from_case(case)
+    t0 = time.perf_counter()
+    ob.advance(ramp=1.0 / case.plan.n_ramp, ke_tol=-1.0, max_substeps=substeps)
+    dt = time.perf_counter() - t0
+    return case.n * substeps / dt, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    case = cylinder_case()
+    ob = oracle.body_from_case(case)
+    total, t_all = 0, 0.0
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ob.advance(ramp=(s + 1) / case.plan.n_ramp, ke_tol=-1.0, max_substeps=args.ref_substeps)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            total += case.n * args.ref_substeps
+            t_all += dt
+    value = total / t_all
+    sample = (f"{args.ref_substeps} substep(s) of each of {args.steps} slow steps of the "
+              f"{case.n}-particle J2 cylinder, FP64 oracle, 1 thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "cylinder3d-j2-252800", "n_particles": case.n,
+                   "sample": "bounded: oracle substeps per slow step as stated"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2309_04010_gb300 import _build
+    _build.build()
+    from paper_2309_04010_gb300 import mtssph as M
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    case = cylinder_case()
+    prec = M.MIXED if args.precision == "mixed" else M.FP64
+    ctx = M.Context(local)
+    t0 = time.perf_counter()
+    gb = M.body_from_case(ctx, case, prec)
+    setup_s = time.perf_counter() - t0
+    off, _ = gb.neighbors()
+    nnz = int(off[-1])
+    plan = case.plan
+    stream = ctx.stream
+
+    def slow_step(l):
+        return gb.advance_slow_step(ramp=l / plan.n_ramp, ke_tol=plan.ke_tol, ke_ref=plan.ke_ref,
+                                    ke_mode=plan.ke_mode, max_substeps=plan.max_substeps,
+                                    check_every=args.check_every)
+
+    # warm-up: also time each stage once to find the dominant kernel
+    stage_ms = {}
+    for w in range(args.warmup):
+        st = (w % 4) + 1
+        gb.set_profiling(st)
+        r = slow_step(w + 1)
+        if r.prof_count:
+            stage_ms[st] = r.prof_ms / r.prof_count
+    dom = max(stage_ms, key=stage_ms.get) if stage_ms else 2
+    gb.set_profiling(dom)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    substeps, launches, prof_ms, prof_n = 0, 0, 0.0, 0
+    reps = []
+    for s in range(args.steps):
+        r = slow_step(args.warmup + s + 1)
+        substeps += r.substeps
+        launches += r.kernel_launches
+        prof_ms += r.prof_ms
+        prof_n += r.prof_count
+        reps.append(r)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        tot = torch.tensor([float(substeps)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tot)
+        total_updates = float(tot.item()) * case.n
+        dist.barrier()
+    else:
+        total_updates = float(substeps) * case.n
+    value = total_updates / (ms * 1e-3)
+
+    # e2e through the C ABI with host-resident state: upload (u, v) from pinned
+    # host memory, advance one slow step, read (u, v) back
+    U = torch.from_numpy(gb.read(M.F_U)).pin_memory().numpy()
+    Vv = torch.from_numpy(gb.read(M.F_V)).pin_memory().numpy()
+    e2e_sub, e2e_t = 0, 0.0
+    l0 = args.warmup + args.steps
+    for s in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        gb.write(M.F_U, U)
+        gb.write(M.F_V, Vv)
+        r = slow_step(l0 + s + 1)
+        U[:] = gb.read(M.F_U)
+        Vv[:] = gb.read(M.F_V)
+        e2e_t += time.perf_counter() - t0
+        e2e_sub += r.substeps
+    e2e_value = case.n * e2e_sub / e2e_t if e2e_t > 0 else None
+
+    # plain FP64 GPU form on the same slow steps (time to equilibrium)
+    fp64 = None
+    if args.fp64_steps > 0 and prec == M.MIXED and rank == 0:
+        g64 = M.body_from_case(ctx, case, M.FP64)
+        g32 = M.body_from_case(ctx, case, M.MIXED)
+        t64, t32, s64, s32 = 0.0, 0.0, 0, 0
+        for l in range(1, args.fp64_steps + 1):
+            kw = dict(ramp=l / plan.n_ramp, ke_tol=plan.ke_tol, ke_ref=plan.ke_ref,
+                      ke_mode=plan.ke_mode, max_substeps=plan.max_substeps,
+                      check_every=args.check_every)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r64 = g64.advance_slow_step(**kw)
+            t64 += time.perf_counter() - t0
+            t0 = time.perf_counter()
+            r32 = g32.advance_slow_step(**kw)
+            t32 += time.perf_counter() - t0
+            s64 += r64.substeps
+            s32 += r32.substeps
+        u64, u32 = g64.read(M.F_U), g32.read(M.F_U)
+        fp64 = {"slow_steps": args.fp64_steps, "fp64_s": t64, "mixed_s": t32,
+                "fp64_substeps": s64, "mixed_substeps": s32,
+                "time_to_equilibrium_speedup": t64 / t32 if t32 > 0 else None,
+                "fp64_value": case.n * s64 / t64 if t64 > 0 else None,
+                "mixed_u_rel_err_vs_fp64": float(np.max(np.abs(u32 - u64)) / np.max(np.abs(u64)))}
+        g64.close()
+        g32.close()
+
+    if rank != 0:
+        return
+    hbm, peak_kind = peaks()
+    kname = STAGES[dom]
+    per_launch_ms = prof_ms / prof_n if prof_n else None
+    algo = ALGO_BYTES_3D_MIXED[dom] * case.n
+    achieved = algo / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms else None
+    cpu = None
+    if args.cpu_substeps > 0 and world == 1:
+        v, dt = oracle_sample(case, args.cpu_substeps)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_substeps} substeps of slow step 1 of the same "
+                         f"{case.n}-particle cylinder, FP64 oracle, 1 thread ({dt:.1f} s)"}
+    h2d = 2 * case.n * 3 * 8
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == M.MIXED else "f64", "data": "synthetic",
+        "config": {"workload": "cylinder3d-j2-252800", "n_particles": case.n,
+                   "neighbours_per_particle": nnz / case.n, "precision": args.precision,
+                   "precision_note": "f32 per-particle arithmetic; f64 displacement and "
+                                     "kinetic-energy/max reductions" if prec == M.MIXED else "f64",
+                   "slow_steps": f"{args.warmup + 1}..{args.warmup + args.steps} of 500",
+                   "substeps_per_step": [r.substeps for r in reps],
+                   "converged": [r.converged for r in reps],
+                   "l2": "working set larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single", "setup_s": setup_s},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm if achieved else None,
+                     "traffic": ncu_traffic(kname, case.n), "peak_kind": peak_kind,
+                     "launch_ms": per_launch_ms,
+                     "stage_ms_per_substep": {STAGES[k]: v for k, v in stage_ms.items()}},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": h2d},
+        "fp64_comparison": fp64,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * mtssph.h -- C ABI of the GB300 (sm_103a) multi-time-step SPH solid library.
+ *
+ * The library advances an elastic or elasto-plastic particle body with the
+ * explicit multi-time-step scheme of Tang, Wu, Wang, Haidn and Hu, "An
+ * explicit multi-time stepping algorithm for multi-time scale coupling
+ * problems in SPH" (arXiv 2309.04010): an outer slow step (a load increment,
+ * Sec. 4.1 dt_l, or an explicit concentration-diffusion step, Sec. 4.1 dt_d)
+ * followed by many damped total-Lagrangian solid substeps (Sec. 3.1, Sec. 4.3)
+ * until the kinetic-energy criterion of Sec. 4.2 holds.
+ *
+ * Conventions for every call:
+ *   - every function returns mts_status (MTS_OK = 0); no C++ exception or
+ *     longjmp crosses the ABI; mts_last_error() gives a message for the last
+ *     failing call on the calling thread;
+ *   - host pointers are plain host memory owned by the caller; the library
+ *     copies what it needs before returning and never keeps a host pointer;
+ *   - particle arrays passed in or out use the caller's ORIGINAL particle
+ *     order; vectors are n x dim row-major, FP64;
+ *   - device memory belongs to the library (allocated through the context's
+ *     allocator) and is released by the matching destroy call;
+ *   - calls on one context (and its bodies) are not thread-safe; all GPU work
+ *     of a context is ordered on the context's stream;
+ *   - a call that fails leaves the body usable unless it returns MTS_ERR_CUDA.
+ */
+#ifndef MTSSPH_H
+#define MTSSPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MTS_OK = 0,
+    MTS_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is out of range        */
+    MTS_ERR_OOM = 2,         /* the allocator returned NULL                          */
+    MTS_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the code)   */
+    MTS_ERR_SINGULAR_B = 4,  /* a correction matrix sum (Sec. 3.1) is singular      */
+    MTS_ERR_NONFINITE = 5,   /* NaN/Inf in an input or in the kinetic energy         */
+    MTS_ERR_TIMEOUT = 6,     /* reserved: a device wait ran out of its limit         */
+    MTS_ERR_UNSTABLE_DT = 7, /* diffusion step above the stable limit                */
+    MTS_ERR_STATE = 8        /* call not valid in the current state                  */
+} mts_status;
+
+typedef enum { MTS_FP64 = 0, MTS_MIXED = 1 } mts_precision;
+typedef enum { MTS_ELASTIC_SVK = 0, MTS_NEOHOOKE_J2 = 1 } mts_material_model;
+
+typedef struct mts_ctx mts_ctx;
+typedef struct mts_body mts_body;
+
+/* Device allocator hook.  alloc returns a device pointer (NULL on failure),
+ * release frees it.  Pass NULL to mts_ctx_create to use cudaMalloc/cudaFree.
+ * The Python binding passes PyTorch's caching allocator here. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*release)(void *ptr, size_t bytes, void *user);
+    void *user;
+} mts_allocator;
+
+/* Context: one CUDA device and one stream.  stream = NULL creates a private
+ * non-blocking stream owned by the context; otherwise the caller's
+ * cudaStream_t is used and stays owned by the caller. */
+mts_status mts_ctx_create(int device, void *cuda_stream, const mts_allocator *alloc,
+                          mts_ctx **out);
+void mts_ctx_destroy(mts_ctx *ctx);
+/* Message for the last failing call on this thread ("" if none). */
+const char *mts_last_error(void);
+/* Library version: major * 10000 + minor * 100 + patch. */
+int mts_version(void);
+
+/* ------------------------------------------------------------------ */
+/* Body and its fixed neighbourhood (Sec. 3.1: total Lagrangian, the    */
+/* neighbour set and the correction matrix B0 are built once in the     */
+/* reference configuration).                                             */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t dim;             /* 2 (plane strain) or 3                                 */
+    int32_t precision;       /* mts_precision                                         */
+    int64_t n;               /* particle count, 2 <= n < 2^31                         */
+    const double *X;         /* host, n x dim reference positions, copied             */
+    double dx;               /* lattice spacing: particle volume dx^dim               */
+    double h_over_dx;        /* smoothing length h = h_over_dx * dx, support 2h       */
+} mts_body_desc;
+
+/* Builds, on the GPU: the Morton order of the particles (cell = floor((X -
+ * Xmin)/dx), bit-interleaved key with x lowest, ties by original index), the
+ * neighbour CSR (all j != i with |X_i - X_j|^2 < (2h)^2 evaluated in FP64
+ * without fused multiply-add, ascending), B0 (Sec. 3.1, correction matrix),
+ * and the canonical damping order (owner blocks, colours, greedy
+ * sub-colours).  Errors: MTS_ERR_INVALID_ARG (bad desc, non-finite X),
+ * MTS_ERR_SINGULAR_B, MTS_ERR_OOM. */
+mts_status mts_body_create(mts_ctx *ctx, const mts_body_desc *desc, mts_body **out);
+void mts_body_destroy(mts_body *body);
+
+/* Sorted position -> original index (n entries, host). */
+mts_status mts_body_permutation(const mts_body *body, int64_t *perm);
+/* Neighbour CSR in SORTED index space.  *nnz receives the entry count;
+ * offsets (n + 1) and idx (nnz) are filled when non-NULL. */
+mts_status mts_body_neighbors(const mts_body *body, int64_t *nnz, int64_t *offsets,
+                              int32_t *idx);
+/* Canonical pairwise-damping order (Sec. 4.3, pairwise splitting): one entry
+ * per neighbour pair a < b (sorted indices), listed in the sequential order
+ * colour, owner-block Morton key, sub-colour, a, b.  Pairs of one (colour,
+ * sub-colour) touch disjoint particles.  Any output pointer may be NULL. */
+mts_status mts_body_colouring(const mts_body *body, int64_t *npairs, int32_t *pair_a,
+                              int32_t *pair_b, int32_t *colour, int64_t *block_key,
+                              int32_t *sub_colour);
+
+/* ------------------------------------------------------------------ */
+/* Material, damping, diffusion and boundary conditions                  */
+/* ------------------------------------------------------------------ */
+/* App. A / App. B.2.  E, nu give mu = E/(2(1+nu)), K = E/(3(1-2nu)),
+ * lambda = K - 2mu/3 (App. A.2 moduli relation).  MTS_ELASTIC_SVK: St
+ * Venant-Kirchhoff; MTS_NEOHOOKE_J2: Alg. 1 with k(a) = sigma0 +
+ * (sigma_inf - sigma0)(1 - exp(-delta a)) + H a.  Hardening arguments are
+ * ignored for SVK. */
+mts_status mts_set_material(mts_body *body, mts_material_model model, double rho0, double E,
+                            double nu, double sigma0, double sigma_inf, double delta,
+                            double H);
+/* Sec. 4.3 viscous damping coefficient eta >= 0 (0 switches damping off). */
+mts_status mts_set_damping(mts_body *body, double eta);
+/* Slow process (Sec. 2.2 Fick's law reduced to a scalar concentration c):
+ * dc_i/dt = 2 D sum_j V (c_i - c_j) W'(r_ij)/r_ij; swelling pressure
+ * p = 3 K beta (c - c0) enters the stress as -p J F^-T (App. B.2).  Sets c = c0
+ * on particles that are not held. */
+mts_status mts_set_diffusion(mts_body *body, double D, double beta, double c0);
+/* Prescribed displacement u = ramp * u_unit on the axes of axis_mask (bit k =
+ * axis k) for `count` particles `ids` (original indices).  u_unit: host,
+ * count x dim, NULL = zeros (clamp).  report_force marks the set whose internal
+ * force is reported as the end force.  Calls accumulate. */
+mts_status mts_set_bc_displacement(mts_body *body, int64_t count, const int64_t *ids,
+                                   uint32_t axis_mask, const double *u_per_unit_ramp,
+                                   int32_t report_force);
+/* Hold c = c_value on `count` particles (Dirichlet layers of the slow step). */
+mts_status mts_set_bc_concentration(mts_body *body, int64_t count, const int64_t *ids,
+                                    double c_value);
+/* Particles whose mean displacement is reported as the tip deflection. */
+mts_status mts_set_tip(mts_body *body, int64_t count, const int64_t *ids);
+/* Diffusion step limits: dt_paper = 0.5 h^2 / D (Sec. 4.1) and the stable
+ * limit 0.9 / max_i sum_j 2 D V |W'_ij|/r_ij of the explicit update. */
+mts_status mts_diffusion_dt(mts_body *body, double *dt_paper, double *dt_stable);
+
+/* ------------------------------------------------------------------ */
+/* Slow step with its damped substeps (Sec. 4.1, Sec. 4.2, Sec. 4.3)     */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double dt_slow;          /* diffusion step; 0 = no diffusion this slow step         */
+    double ramp_value;       /* load scale: prescribed u = ramp * u_unit (Sec. 4.1 dt_l) */
+    double dt_sub_override;  /* > 0: fixed substep size instead of the Sec. 4.1 rule     */
+    double ke_tol;           /* stop when E_k <= ke_tol * ke_ref; < 0 disables the stop  */
+    double ke_ref;           /* reference energy (mode 0) or energy density (mode 1)    */
+    int64_t max_substeps;    /* cap on substeps (>= 1); reaching it is not an error     */
+    int32_t ke_mode;         /* 0: total E_k; 1: E_k per unit volume                    */
+    int32_t check_every;     /* substeps per host check of the stop flag (>= 1)         */
+    int32_t force_dt;        /* 1: accept dt_slow above the stable diffusion limit      */
+    int32_t reserved;
+} mts_step_params;
+
+typedef struct {
+    int64_t substeps;        /* substeps taken                                         */
+    int32_t converged;       /* 1 if the kinetic-energy criterion stopped the loop      */
+    int32_t status;          /* mts_status of the step                                 */
+    double ke_final;         /* E_k after the last substep                             */
+    double max_v;            /* max |v| after the last substep (free axes)             */
+    double max_a;            /* max |dv/dt| of the last substep (free axes)            */
+    double dt_last;          /* size of the last substep                               */
+    double end_force[3];     /* -sum m a over the report_force set, last substep       */
+    double tip_deflection[3];/* mean u over the tip set                                */
+    int64_t kernel_launches; /* library kernels launched by this call (incl. no-ops)   */
+    int64_t prof_count;      /* substeps whose profiled stage was timed (see below)    */
+    double prof_ms;          /* summed CUDA-event time of the profiled stage           */
+} mts_step_report;
+
+/* One slow step: jump prescribed axes to ramp * u_unit (v = 0 there), run
+ * the diffusion step if dt_slow > 0, then substeps (stress, force and kick,
+ * symmetric pairwise damping, BC and drift, FP64 kinetic energy) until
+ * E_k <= ke_tol * ke_ref or max_substeps.  The substep size follows
+ * Sec. 4.1: dt0 = 0.6 h / c_s, then 0.6 min(h / (c_s + |v|max),
+ * sqrt(h / |dv/dt|max)) with c_s = sqrt(K / rho0).  The stop flag lives on the
+ * device; the host checks it every check_every substeps, so the substep count
+ * is exact.  Errors: MTS_ERR_UNSTABLE_DT, MTS_ERR_NONFINITE (report.status
+ * says so too), MTS_ERR_STATE (no material set). */
+mts_status mts_advance_slow_step(mts_body *body, const mts_step_params *params,
+                                 mts_step_report *report);
+
+/* Time one stage of every substep with CUDA events recorded inside the
+ * captured graph, on the library stream: 0 = off, 1 = stress (deformation
+ * gradient, stress, P B0), 2 = force and kick, 3 = the whole damping sweep
+ * (all colour launches), 4 = BC, drift and reductions.  The next
+ * mts_advance_slow_step reports the summed time in prof_ms over prof_count
+ * substeps.  The events add a small cost to each substep. */
+mts_status mts_set_profiling(mts_body *body, int32_t stage);
+
+/* Stage-by-stage entry for tests: runs one substep of size dt with load scale
+ * ramp up to stage `upto` (1 = deformation gradient + stress + P B0, 2 = +
+ * force and kick, 3 = + damping sweep, 4 = + BC and drift, i.e. a full
+ * substep) without the stop logic. */
+mts_status mts_substep_partial(mts_body *body, double dt, double ramp, int32_t upto);
+
+typedef enum {
+    MTS_F_U = 0,       /* displacement, n x dim                              */
+    MTS_F_X = 1,       /* reference position, n x dim (read only)            */
+    MTS_F_V = 2,       /* velocity, n x dim                                  */
+    MTS_F_DEFGRAD = 3, /* deformation gradient from the current u, n x 9     */
+    MTS_F_PB = 4,      /* P B0 of the last stress stage, n x dim x dim       */
+    MTS_F_C = 5,       /* concentration, n                                   */
+    MTS_F_ALPHA = 6,   /* equivalent plastic strain, n                       */
+    MTS_F_CPINV = 7,   /* inverse plastic right Cauchy-Green (xx,yy,zz,xy,yz,xz) */
+    MTS_F_ACC = 8      /* internal acceleration of the last force stage       */
+} mts_field;
+
+/* Copy a field to/from a caller-owned host buffer of exactly `len` doubles
+ * (n times the field width), original order.  Writes: U, V, C, ALPHA, CPINV. */
+mts_status mts_read_field(mts_body *body, int32_t field, double *host_out, int64_t len);
+mts_status mts_write_field(mts_body *body, int32_t field, const double *host_in, int64_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MTSSPH_H */

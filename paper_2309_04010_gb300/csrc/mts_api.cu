@@ -1,0 +1,724 @@
+// mts_api.cu -- the C ABI (include/mtssph.h): contexts, bodies, boundary
+// conditions, the slow-step driver and field transfers.
+//
+// The slow-step driver (Sec. 4.2 two-loop scheme) keeps the inner loop on the
+// device: a chunk of `check_every` substeps is captured once into a CUDA graph
+// and replayed; every kernel reads dt, the load scale and the stop flag from a
+// device control block, so the graph is valid for every slow step and the
+// substeps after the stop inside a chunk are no-ops.  The host reads the
+// control block back once per chunk.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "mts_internal.cuh"
+
+namespace mts {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+mts_status cuda_fail(cudaError_t e, const char *what) {
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return MTS_ERR_CUDA;
+}
+
+void *dalloc(mts_ctx *ctx, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (ctx->alloc.custom) {
+        p = ctx->alloc.a.alloc(bytes, ctx->alloc.a.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dfree(mts_ctx *ctx, void *p) {
+    if (!p) return;
+    if (ctx->alloc.custom)
+        ctx->alloc.a.release(p, 0, ctx->alloc.a.user);
+    else
+        cudaFree(p);
+}
+
+mts_status dalloc_into(mts_ctx *ctx, void **p, size_t bytes) {
+    *p = dalloc(ctx, bytes);
+    if (!*p) {
+        set_error("device allocation of %zu bytes failed", bytes);
+        return MTS_ERR_OOM;
+    }
+    return MTS_OK;
+}
+
+}  // namespace mts
+
+using namespace mts;
+
+namespace {
+
+template <class T>
+void free_dev(mts_body *b, T *&p) {
+    dfree(b->ctx, (void *)p);
+    p = nullptr;
+}
+
+void body_free(mts_body *b) {
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaEvent_t e : b->prof_ev) cudaEventDestroy(e);
+    void **ptrs[] = {(void **)&b->perm, (void **)&b->rank, (void **)&b->X64, (void **)&b->nb_off,
+                     (void **)&b->nb_idx, (void **)&b->ell, (void **)&b->slice_off,
+                     (void **)&b->slice_w, (void **)&b->pair_a, (void **)&b->pair_b,
+                     (void **)&b->pair_col, (void **)&b->pair_sub, (void **)&b->pair_key,
+                     (void **)&b->pair_ab, (void **)&b->pair_g, (void **)&b->lvl_pair,
+                     (void **)&b->grp_lvl, (void **)&b->touch_start, (void **)&b->touch_cnt,
+                     (void **)&b->X, (void **)&b->B0, (void **)&b->uf, (void **)&b->v,
+                     (void **)&b->acc, (void **)&b->PB, (void **)&b->cp, (void **)&b->c,
+                     (void **)&b->c_tmp, (void **)&b->c_held, (void **)&b->u, (void **)&b->u_unit,
+                     (void **)&b->flags, (void **)&b->ctrl, (void **)&b->part_force,
+                     (void **)&b->part_drift, (void **)&b->scratch};
+    for (void **pp : ptrs) {
+        dfree(b->ctx, *pp);
+        *pp = nullptr;
+    }
+    if (b->h_ctrl) cudaFreeHost(b->h_ctrl);
+    if (b->h_stage) cudaFreeHost(b->h_stage);
+    delete b;
+}
+
+__global__ void k_init_state(double *u, void *uf, void *v, void *acc, void *cp, void *c,
+                             void *c_held, uint8_t *flags, double *u_unit, long long n, int pad,
+                             int rsize) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = 0; k < pad; ++k) {
+        u[i * pad + k] = 0.0;
+        u_unit[i * pad + k] = 0.0;
+    }
+    flags[i] = 0;
+    if (rsize == 4) {
+        float *f;
+        if (uf) { f = (float *)uf; for (int k = 0; k < pad; ++k) f[i * pad + k] = 0.f; }
+        f = (float *)v; for (int k = 0; k < pad; ++k) f[i * pad + k] = 0.f;
+        f = (float *)acc; for (int k = 0; k < pad; ++k) f[i * pad + k] = 0.f;
+        f = (float *)cp; for (int k = 0; k < 8; ++k) f[i * 8 + k] = k < 3 ? 1.f : 0.f;
+        ((float *)c)[i] = 0.f;
+        ((float *)c_held)[i] = 0.f;
+    } else {
+        double *f;
+        f = (double *)v; for (int k = 0; k < pad; ++k) f[i * pad + k] = 0.0;
+        f = (double *)acc; for (int k = 0; k < pad; ++k) f[i * pad + k] = 0.0;
+        f = (double *)cp; for (int k = 0; k < 8; ++k) f[i * 8 + k] = k < 3 ? 1.0 : 0.0;
+        ((double *)c)[i] = 0.0;
+        ((double *)c_held)[i] = 0.0;
+    }
+}
+
+// c <- c0 on particles that are not held, c <- c_held on held ones
+__global__ void k_set_c(void *c, const void *c_held, const uint8_t *flags, long long n, double c0,
+                        int rsize, int only_held) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool held = flags[i] & kCHeldBit;
+    if (only_held && !held) return;
+    if (rsize == 4)
+        ((float *)c)[i] = held ? ((const float *)c_held)[i] : (float)c0;
+    else
+        ((double *)c)[i] = held ? ((const double *)c_held)[i] : c0;
+}
+
+mts_status upload_bc(mts_body *b, const std::vector<double> &u_unit_sorted) {
+    cudaStream_t st = b->ctx->stream;
+    MTS_CUDA(cudaMemcpyAsync(b->flags, b->h_flags.data(), b->n, cudaMemcpyHostToDevice, st));
+    if (!u_unit_sorted.empty())
+        MTS_CUDA(cudaMemcpyAsync(b->u_unit, u_unit_sorted.data(),
+                                 u_unit_sorted.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    MTS_CUDA(cudaStreamSynchronize(st));
+    return MTS_OK;
+}
+
+mts_status get_rank_host(mts_body *b, std::vector<long long> &rank) {
+    rank.resize(b->n);
+    MTS_CUDA(cudaMemcpyAsync(rank.data(), b->rank, b->n * sizeof(long long), cudaMemcpyDeviceToHost,
+                             b->ctx->stream));
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    return MTS_OK;
+}
+
+mts_status capture_chunk(mts_body *b, int chunk) {
+    if (b->graph && !b->graph_dirty && b->graph_chunk == chunk &&
+        b->graph_prof_stage == b->prof_stage)
+        return MTS_OK;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    MTS_TRY(prepare_kernels(b));
+    cudaStream_t st = b->ctx->stream;
+    const int ps = b->prof_stage;
+    if (ps > 0) {
+        while ((int)b->prof_ev.size() < 2 * chunk) {
+            cudaEvent_t e;
+            MTS_CUDA(cudaEventCreate(&e));
+            b->prof_ev.push_back(e);
+        }
+    }
+    MTS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    mts_status s = MTS_OK;
+    long long ndamp = 0;
+    auto mark = [&](int k, int stage, int end) {
+        if (s == MTS_OK && ps == stage) {
+            cudaError_t e = cudaEventRecordWithFlags(b->prof_ev[2 * k + end], st,
+                                                     cudaEventRecordExternal);
+            if (e != cudaSuccess) s = cuda_fail(e, "cudaEventRecordWithFlags");
+        }
+    };
+    for (int k = 0; k < chunk && s == MTS_OK; ++k) {
+        mark(k, 1, 0);
+        s = launch_stress(b);
+        mark(k, 1, 1);
+        mark(k, 2, 0);
+        if (s == MTS_OK) s = launch_force(b);
+        mark(k, 2, 1);
+        mark(k, 3, 0);
+        if (s == MTS_OK) s = launch_damping(b, &ndamp);
+        mark(k, 3, 1);
+        mark(k, 4, 0);
+        if (s == MTS_OK) s = launch_drift(b);
+        mark(k, 4, 1);
+    }
+    b->launches_per_substep = 3 + ndamp;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (s != MTS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    b->graph_chunk = chunk;
+    b->graph_prof_stage = ps;
+    b->graph_dirty = false;
+    return MTS_OK;
+}
+
+bool valid_field(int f) { return f >= MTS_F_U && f <= MTS_F_ACC; }
+
+}  // namespace
+
+extern "C" {
+
+const char *mts_last_error(void) { return g_err; }
+int mts_version(void) { return 100; }
+
+mts_status mts_ctx_create(int device, void *cuda_stream, const mts_allocator *alloc, mts_ctx **out) {
+    if (!out) {
+        set_error("mts_ctx_create: out is NULL");
+        return MTS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int ndev = 0;
+    MTS_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) {
+        set_error("mts_ctx_create: device %d not present (%d devices)", device, ndev);
+        return MTS_ERR_INVALID_ARG;
+    }
+    if (alloc && (!alloc->alloc || !alloc->release)) {
+        set_error("mts_ctx_create: allocator needs both alloc and release");
+        return MTS_ERR_INVALID_ARG;
+    }
+    MTS_CUDA(cudaSetDevice(device));
+    mts_ctx *c = new (std::nothrow) mts_ctx();
+    if (!c) return MTS_ERR_OOM;
+    c->device = device;
+    c->alloc.custom = alloc != nullptr;
+    if (alloc) c->alloc.a = *alloc;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+        c->own_stream = false;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_fail(e, "cudaStreamCreateWithFlags");
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+    return MTS_OK;
+}
+
+void mts_ctx_destroy(mts_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->own_stream) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaStreamDestroy(ctx->stream);
+    }
+    delete ctx;
+}
+
+mts_status mts_body_create(mts_ctx *ctx, const mts_body_desc *desc, mts_body **out) {
+    if (!ctx || !desc || !out || !desc->X) {
+        set_error("mts_body_create: NULL argument");
+        return MTS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if ((desc->dim != 2 && desc->dim != 3) || desc->n < 2 || desc->n >= (1LL << 31) ||
+        !(desc->dx > 0) || !std::isfinite(desc->dx) || !(desc->h_over_dx > 0) ||
+        !(desc->h_over_dx < 8) || (desc->precision != MTS_FP64 && desc->precision != MTS_MIXED)) {
+        set_error("mts_body_create: invalid descriptor (dim %d, n %lld, dx %g, h/dx %g, precision %d)",
+                  desc->dim, (long long)desc->n, desc->dx, desc->h_over_dx, desc->precision);
+        return MTS_ERR_INVALID_ARG;
+    }
+    MTS_CUDA(cudaSetDevice(ctx->device));
+    mts_body *b = new (std::nothrow) mts_body();
+    if (!b) return MTS_ERR_OOM;
+    b->ctx = ctx;
+    b->dim = desc->dim;
+    b->precision = desc->precision;
+    b->n = desc->n;
+    b->dx = desc->dx;
+    b->h = desc->h_over_dx * desc->dx;
+    const double w = 2.0 * b->h;
+    b->cut2 = w * w;
+    b->V = b->dim == 2 ? b->dx * b->dx : b->dx * b->dx * b->dx;
+    long long need = (long long)std::floor(w / b->dx) + 1;
+    b->blk_shift = 0;
+    while ((1LL << b->blk_shift) < need) ++b->blk_shift;
+    b->rsize = b->precision == MTS_FP64 ? 8 : 4;
+    b->graph_dirty = true;
+    const long long n = b->n;
+    const int pad = b->dim == 2 ? 2 : 4;
+    const int ms = b->dim == 2 ? 4 : 12;
+    const size_t R = b->rsize;
+    mts_status s = MTS_OK;
+    auto A = [&](void **p, size_t bytes) {
+        if (s == MTS_OK) s = dalloc_into(ctx, p, bytes + 16);
+    };
+    A((void **)&b->perm, n * 8);
+    A((void **)&b->rank, n * 8);
+    A((void **)&b->X64, n * pad * 8);
+    A(&b->X, n * pad * R);
+    A(&b->B0, n * ms * R);
+    A((void **)&b->u, n * pad * 8);
+    if (R == 4) A(&b->uf, n * pad * R);
+    A(&b->v, n * pad * R);
+    A(&b->acc, n * pad * R);
+    A(&b->PB, n * ms * R);
+    A(&b->cp, n * 8 * R);
+    A(&b->c, n * R);
+    A(&b->c_tmp, n * R);
+    A(&b->c_held, n * R);
+    A((void **)&b->u_unit, n * pad * 8);
+    A((void **)&b->flags, n);
+    A((void **)&b->ctrl, sizeof(Control));
+    const long long grid = (n + kBlock - 1) / kBlock;
+    A((void **)&b->part_force, grid * 4 * 8);
+    A((void **)&b->part_drift, grid * 2 * 8);
+    A((void **)&b->scratch, (size_t)n * 18 * 8);
+    if (s == MTS_OK && cudaMallocHost((void **)&b->h_ctrl, sizeof(Control)) != cudaSuccess) {
+        set_error("pinned allocation failed");
+        s = MTS_ERR_OOM;
+    }
+    if (s != MTS_OK) {
+        body_free(b);
+        return s;
+    }
+    cudaStream_t st = ctx->stream;
+    cudaMemsetAsync(b->ctrl, 0, sizeof(Control), st);
+    k_init_state<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b->u, b->uf, b->v, b->acc, b->cp, b->c,
+                                                               b->c_held, b->flags, b->u_unit, n, pad,
+                                                               (int)R);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        body_free(b);
+        return cuda_fail(e, "k_init_state");
+    }
+    s = build_body(b, desc->X);
+    if (s != MTS_OK) {
+        cudaStreamSynchronize(st);
+        body_free(b);
+        return s;
+    }
+    b->h_flags.assign(n, 0);
+    *out = b;
+    return MTS_OK;
+}
+
+void mts_body_destroy(mts_body *body) {
+    if (!body) return;
+    cudaStreamSynchronize(body->ctx->stream);
+    body_free(body);
+}
+
+mts_status mts_body_permutation(const mts_body *b, int64_t *perm) {
+    if (!b || !perm) {
+        set_error("mts_body_permutation: NULL argument");
+        return MTS_ERR_INVALID_ARG;
+    }
+    MTS_CUDA(cudaMemcpyAsync(perm, b->perm, b->n * 8, cudaMemcpyDeviceToHost, b->ctx->stream));
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    return MTS_OK;
+}
+
+mts_status mts_body_neighbors(const mts_body *b, int64_t *nnz, int64_t *offsets, int32_t *idx) {
+    if (!b || !nnz) {
+        set_error("mts_body_neighbors: NULL argument");
+        return MTS_ERR_INVALID_ARG;
+    }
+    *nnz = b->nnz;
+    cudaStream_t st = b->ctx->stream;
+    if (offsets) MTS_CUDA(cudaMemcpyAsync(offsets, b->nb_off, (b->n + 1) * 8, cudaMemcpyDeviceToHost, st));
+    if (idx) MTS_CUDA(cudaMemcpyAsync(idx, b->nb_idx, b->nnz * 4, cudaMemcpyDeviceToHost, st));
+    MTS_CUDA(cudaStreamSynchronize(st));
+    return MTS_OK;
+}
+
+mts_status mts_body_colouring(const mts_body *b, int64_t *npairs, int32_t *pa, int32_t *pb,
+                              int32_t *colour, int64_t *block_key, int32_t *sub) {
+    if (!b || !npairs) {
+        set_error("mts_body_colouring: NULL argument");
+        return MTS_ERR_INVALID_ARG;
+    }
+    *npairs = b->npairs;
+    cudaStream_t st = b->ctx->stream;
+    const size_t m = (size_t)b->npairs;
+    if (pa) MTS_CUDA(cudaMemcpyAsync(pa, b->pair_a, m * 4, cudaMemcpyDeviceToHost, st));
+    if (pb) MTS_CUDA(cudaMemcpyAsync(pb, b->pair_b, m * 4, cudaMemcpyDeviceToHost, st));
+    if (colour) MTS_CUDA(cudaMemcpyAsync(colour, b->pair_col, m * 4, cudaMemcpyDeviceToHost, st));
+    if (block_key) MTS_CUDA(cudaMemcpyAsync(block_key, b->pair_key, m * 8, cudaMemcpyDeviceToHost, st));
+    if (sub) MTS_CUDA(cudaMemcpyAsync(sub, b->pair_sub, m * 4, cudaMemcpyDeviceToHost, st));
+    MTS_CUDA(cudaStreamSynchronize(st));
+    return MTS_OK;
+}
+
+mts_status mts_set_material(mts_body *b, mts_material_model model, double rho0, double E, double nu,
+                            double sigma0, double sigma_inf, double delta, double H) {
+    if (!b || (model != MTS_ELASTIC_SVK && model != MTS_NEOHOOKE_J2) || !(rho0 > 0) || !(E > 0) ||
+        !(nu > -1.0) || !(nu < 0.5) || !std::isfinite(rho0) || !std::isfinite(E)) {
+        set_error("mts_set_material: invalid parameters");
+        return MTS_ERR_INVALID_ARG;
+    }
+    if (model == MTS_NEOHOOKE_J2 && (!(sigma0 > 0) || !std::isfinite(sigma_inf) ||
+                                     !(delta >= 0) || !std::isfinite(H))) {
+        set_error("mts_set_material: invalid hardening parameters");
+        return MTS_ERR_INVALID_ARG;
+    }
+    b->has_material = true;
+    b->model = model;
+    b->rho0 = rho0;
+    b->E = E;
+    b->nu = nu;
+    b->mu = E / (2.0 * (1.0 + nu));
+    b->K = E / (3.0 * (1.0 - 2.0 * nu));
+    b->lambda = b->K - 2.0 * b->mu / 3.0;
+    b->s0 = sigma0;
+    b->sinf = sigma_inf;
+    b->delta = delta;
+    b->Hlin = H;
+    b->graph_dirty = true;
+    return MTS_OK;
+}
+
+mts_status mts_set_damping(mts_body *b, double eta) {
+    if (!b || !(eta >= 0) || !std::isfinite(eta)) {
+        set_error("mts_set_damping: eta must be finite and >= 0");
+        return MTS_ERR_INVALID_ARG;
+    }
+    b->eta = eta;
+    b->graph_dirty = true;
+    return MTS_OK;
+}
+
+mts_status mts_set_diffusion(mts_body *b, double D, double beta, double c0) {
+    if (!b || !(D >= 0) || !std::isfinite(D) || !std::isfinite(beta) || !std::isfinite(c0)) {
+        set_error("mts_set_diffusion: invalid parameters");
+        return MTS_ERR_INVALID_ARG;
+    }
+    b->has_diff = true;
+    b->D = D;
+    b->beta = beta;
+    b->c0 = c0;
+    b->graph_dirty = true;
+    k_set_c<<<(unsigned)((b->n + 255) / 256), 256, 0, b->ctx->stream>>>(b->c, b->c_held, b->flags, b->n,
+                                                                        c0, (int)b->rsize, 0);
+    MTS_CUDA(cudaGetLastError());
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    return MTS_OK;
+}
+
+mts_status mts_set_bc_displacement(mts_body *b, int64_t count, const int64_t *ids, uint32_t mask,
+                                   const double *u_unit, int32_t report_force) {
+    if (!b || count < 0 || (count > 0 && !ids)) {
+        set_error("mts_set_bc_displacement: invalid arguments");
+        return MTS_ERR_INVALID_ARG;
+    }
+    std::vector<long long> rank;
+    MTS_TRY(get_rank_host(b, rank));
+    const int pad = b->dim == 2 ? 2 : 4;
+    std::vector<double> uu((size_t)b->n * pad);
+    MTS_CUDA(cudaMemcpyAsync(uu.data(), b->u_unit, uu.size() * 8, cudaMemcpyDeviceToHost, b->ctx->stream));
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    const uint32_t m = mask & ((1u << b->dim) - 1);
+    for (int64_t t = 0; t < count; ++t) {
+        if (ids[t] < 0 || ids[t] >= b->n) {
+            set_error("mts_set_bc_displacement: id %lld out of range", (long long)ids[t]);
+            return MTS_ERR_INVALID_ARG;
+        }
+        const long long s = rank[ids[t]];
+        b->h_flags[s] |= (uint8_t)m;
+        for (int k = 0; k < b->dim; ++k)
+            if (m & (1u << k)) {
+                double val = u_unit ? u_unit[t * b->dim + k] : 0.0;
+                if (!std::isfinite(val)) {
+                    set_error("mts_set_bc_displacement: non-finite u_unit");
+                    return MTS_ERR_INVALID_ARG;
+                }
+                uu[s * pad + k] = val;
+            }
+        if (report_force) b->h_flags[s] |= kForceBit;
+    }
+    b->graph_dirty = true;
+    return upload_bc(b, uu);
+}
+
+mts_status mts_set_bc_concentration(mts_body *b, int64_t count, const int64_t *ids, double value) {
+    if (!b || count < 0 || (count > 0 && !ids) || !std::isfinite(value)) {
+        set_error("mts_set_bc_concentration: invalid arguments");
+        return MTS_ERR_INVALID_ARG;
+    }
+    std::vector<long long> rank;
+    MTS_TRY(get_rank_host(b, rank));
+    std::vector<char> held((size_t)b->n * b->rsize);
+    MTS_CUDA(cudaMemcpyAsync(held.data(), b->c_held, held.size(), cudaMemcpyDeviceToHost, b->ctx->stream));
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    for (int64_t t = 0; t < count; ++t) {
+        if (ids[t] < 0 || ids[t] >= b->n) {
+            set_error("mts_set_bc_concentration: id %lld out of range", (long long)ids[t]);
+            return MTS_ERR_INVALID_ARG;
+        }
+        const long long s = rank[ids[t]];
+        b->h_flags[s] |= kCHeldBit;
+        if (b->rsize == 4)
+            reinterpret_cast<float *>(held.data())[s] = (float)value;
+        else
+            reinterpret_cast<double *>(held.data())[s] = value;
+    }
+    cudaStream_t st = b->ctx->stream;
+    MTS_CUDA(cudaMemcpyAsync(b->c_held, held.data(), held.size(), cudaMemcpyHostToDevice, st));
+    MTS_TRY(upload_bc(b, {}));
+    k_set_c<<<(unsigned)((b->n + 255) / 256), 256, 0, st>>>(b->c, b->c_held, b->flags, b->n, 0.0,
+                                                            (int)b->rsize, 1);
+    MTS_CUDA(cudaGetLastError());
+    MTS_CUDA(cudaStreamSynchronize(st));
+    return MTS_OK;
+}
+
+mts_status mts_set_tip(mts_body *b, int64_t count, const int64_t *ids) {
+    if (!b || count < 0 || (count > 0 && !ids)) {
+        set_error("mts_set_tip: invalid arguments");
+        return MTS_ERR_INVALID_ARG;
+    }
+    std::vector<long long> rank;
+    MTS_TRY(get_rank_host(b, rank));
+    for (auto &f : b->h_flags) f &= (uint8_t)~kTipBit;
+    for (int64_t t = 0; t < count; ++t) {
+        if (ids[t] < 0 || ids[t] >= b->n) {
+            set_error("mts_set_tip: id %lld out of range", (long long)ids[t]);
+            return MTS_ERR_INVALID_ARG;
+        }
+        b->h_flags[rank[ids[t]]] |= kTipBit;
+    }
+    b->tip_count = (int)count;
+    return upload_bc(b, {});
+}
+
+mts_status mts_diffusion_dt(mts_body *b, double *dt_paper, double *dt_stable) {
+    if (!b || !dt_paper || !dt_stable) {
+        set_error("mts_diffusion_dt: NULL argument");
+        return MTS_ERR_INVALID_ARG;
+    }
+    if (!b->has_diff) {
+        set_error("mts_diffusion_dt: no diffusion set");
+        return MTS_ERR_STATE;
+    }
+    double amax = 0;
+    MTS_TRY(diffusion_bound(b, &amax));
+    *dt_paper = b->D > 0 ? 0.5 * b->h * b->h / b->D : INFINITY;
+    *dt_stable = amax > 0 ? 0.9 / amax : INFINITY;
+    return MTS_OK;
+}
+
+mts_status mts_advance_slow_step(mts_body *b, const mts_step_params *p, mts_step_report *rep) {
+    if (!b || !p || !rep) {
+        set_error("mts_advance_slow_step: NULL argument");
+        return MTS_ERR_INVALID_ARG;
+    }
+    memset(rep, 0, sizeof(*rep));
+    if (!b->has_material) {
+        set_error("mts_advance_slow_step: no material set");
+        return MTS_ERR_STATE;
+    }
+    if (p->max_substeps < 1 || !std::isfinite(p->ramp_value) || !(p->dt_slow >= 0) ||
+        !std::isfinite(p->dt_slow) || !(p->dt_sub_override >= 0) || !std::isfinite(p->ke_ref) ||
+        !std::isfinite(p->ke_tol) || (p->ke_mode != 0 && p->ke_mode != 1)) {
+        set_error("mts_advance_slow_step: invalid step parameters");
+        return MTS_ERR_INVALID_ARG;
+    }
+    MTS_CUDA(cudaSetDevice(b->ctx->device));
+    cudaStream_t st = b->ctx->stream;
+    if (p->dt_slow > 0) {
+        if (!b->has_diff) {
+            set_error("mts_advance_slow_step: dt_slow > 0 without diffusion");
+            return MTS_ERR_STATE;
+        }
+        double dtp, dts;
+        MTS_TRY(mts_diffusion_dt(b, &dtp, &dts));
+        if (p->dt_slow > dts * (1.0 + 1e-12) && !p->force_dt) {
+            set_error("diffusion step %g above the stable limit %g (paper's 0.5 h^2/D = %g)",
+                      p->dt_slow, dts, dtp);
+            return MTS_ERR_UNSTABLE_DT;
+        }
+    }
+    const double cs = std::sqrt(b->K / b->rho0);
+    const double dt0 = p->dt_sub_override > 0 ? p->dt_sub_override : 0.6 * b->h / cs;
+    const int use_tol = p->ke_tol >= 0 ? 1 : 0;
+    MTS_TRY(launch_reset_ctrl(b, dt0, p->dt_sub_override, p->ramp_value, p->max_substeps,
+                              p->ke_tol * p->ke_ref, p->ke_mode, use_tol));
+    MTS_TRY(launch_slow_begin(b));
+    long long launches = 2;
+    if (p->dt_slow > 0) {
+        MTS_TRY(launch_diffusion(b, p->dt_slow));
+        launches += 2;
+    }
+    const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 32, 4096));
+    MTS_TRY(capture_chunk(b, chunk));
+    long long done_before = 0;
+    double prof_ms = 0.0;
+    long long prof_n = 0;
+    for (;;) {
+        MTS_CUDA(cudaGraphLaunch(b->graph, st));
+        launches += chunk * b->launches_per_substep;
+        MTS_CUDA(cudaMemcpyAsync(b->h_ctrl, b->ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+        MTS_CUDA(cudaStreamSynchronize(st));
+        if (b->graph_prof_stage > 0) {
+            const long long ran = std::min<long long>(b->h_ctrl->nsub - done_before, chunk);
+            for (long long k = 0; k < ran; ++k) {
+                float ms = 0.f;
+                MTS_CUDA(cudaEventElapsedTime(&ms, b->prof_ev[2 * k], b->prof_ev[2 * k + 1]));
+                prof_ms += ms;
+            }
+            prof_n += ran;
+        }
+        done_before = b->h_ctrl->nsub;
+        if (b->h_ctrl->done) break;
+    }
+    rep->prof_ms = prof_ms;
+    rep->prof_count = prof_n;
+    const Control &C = *b->h_ctrl;
+    rep->substeps = C.nsub;
+    rep->converged = C.converged;
+    rep->status = C.status;
+    rep->ke_final = C.ke;
+    rep->max_v = C.vmax;
+    rep->max_a = C.amax;
+    rep->dt_last = C.dt_last;
+    for (int k = 0; k < 3; ++k) rep->end_force[k] = k < b->dim ? C.end_force[k] : 0.0;
+    double tip[3] = {0, 0, 0};
+    if (b->tip_count > 0) {
+        MTS_TRY(launch_tip(b, tip));
+        launches += 2;
+    }
+    rep->kernel_launches = launches;
+    for (int k = 0; k < 3; ++k) rep->tip_deflection[k] = tip[k];
+    if (C.status != MTS_OK) {
+        set_error("non-finite kinetic energy after substep %lld", (long long)C.nsub);
+        return (mts_status)C.status;
+    }
+    return MTS_OK;
+}
+
+mts_status mts_set_profiling(mts_body *b, int32_t stage) {
+    if (!b || stage < 0 || stage > 4) {
+        set_error("mts_set_profiling: stage must be 0..4");
+        return MTS_ERR_INVALID_ARG;
+    }
+    b->prof_stage = stage;
+    return MTS_OK;
+}
+
+mts_status mts_substep_partial(mts_body *b, double dt, double ramp, int32_t upto) {
+    if (!b || !(dt > 0) || !std::isfinite(dt) || !std::isfinite(ramp) || upto < 1 || upto > 4) {
+        set_error("mts_substep_partial: invalid arguments");
+        return MTS_ERR_INVALID_ARG;
+    }
+    if (!b->has_material) {
+        set_error("mts_substep_partial: no material set");
+        return MTS_ERR_STATE;
+    }
+    MTS_CUDA(cudaSetDevice(b->ctx->device));
+    MTS_TRY(prepare_kernels(b));
+    MTS_TRY(launch_reset_ctrl(b, dt, dt, ramp, 1LL << 62, 0.0, 0, 0));
+    MTS_TRY(launch_stress(b));
+    if (upto >= 2) MTS_TRY(launch_force(b));
+    if (upto >= 3) MTS_TRY(launch_damping(b));
+    if (upto >= 4) MTS_TRY(launch_drift(b));
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    return MTS_OK;
+}
+
+mts_status mts_read_field(mts_body *b, int32_t field, double *out, int64_t len) {
+    if (!b || !out || !valid_field(field)) {
+        set_error("mts_read_field: invalid arguments");
+        return MTS_ERR_INVALID_ARG;
+    }
+    const int w = field_width(b, field);
+    if (len != b->n * w) {
+        set_error("mts_read_field: len %lld, expected %lld", (long long)len, (long long)(b->n * w));
+        return MTS_ERR_INVALID_ARG;
+    }
+    MTS_CUDA(cudaSetDevice(b->ctx->device));
+    MTS_TRY(field_to_scratch(b, field));
+    MTS_CUDA(cudaMemcpyAsync(out, b->scratch, len * 8, cudaMemcpyDeviceToHost, b->ctx->stream));
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    return MTS_OK;
+}
+
+mts_status mts_write_field(mts_body *b, int32_t field, const double *in, int64_t len) {
+    if (!b || !in || !(field == MTS_F_U || field == MTS_F_V || field == MTS_F_C ||
+                       field == MTS_F_ALPHA || field == MTS_F_CPINV)) {
+        set_error("mts_write_field: invalid arguments (writable: U, V, C, ALPHA, CPINV)");
+        return MTS_ERR_INVALID_ARG;
+    }
+    const int w = field_width(b, field);
+    if (len != b->n * w) {
+        set_error("mts_write_field: len %lld, expected %lld", (long long)len, (long long)(b->n * w));
+        return MTS_ERR_INVALID_ARG;
+    }
+    for (int64_t t = 0; t < len; ++t)
+        if (!std::isfinite(in[t])) {
+            set_error("mts_write_field: non-finite value at %lld", (long long)t);
+            return MTS_ERR_NONFINITE;
+        }
+    MTS_CUDA(cudaSetDevice(b->ctx->device));
+    MTS_CUDA(cudaMemcpyAsync(b->scratch, in, len * 8, cudaMemcpyHostToDevice, b->ctx->stream));
+    MTS_TRY(scratch_to_field(b, field));
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    return MTS_OK;
+}
+
+}  // extern "C"

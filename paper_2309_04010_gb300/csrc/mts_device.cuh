@@ -1,0 +1,292 @@
+// mts_device.cuh -- device helpers: vector loads, 3x3 algebra, constitutive laws.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace mts {
+
+template <int D> struct Pad { static constexpr int v = (D == 2) ? 2 : 4; };
+template <int D> struct MatS { static constexpr int v = (D == 2) ? 4 : 12; };
+
+// ------------------------------------------------------------------ loads
+template <class R> struct Vec2;
+template <> struct Vec2<float> { using T = float2; };
+template <> struct Vec2<double> { using T = double2; };
+
+// read-only vector load of N consecutive reals (N = 2 or 4), 8/16-byte aligned
+template <class R, int N>
+__device__ __forceinline__ void ldg_vec(R (&o)[N], const R *p) {
+    if constexpr (sizeof(R) == 4 && N == 4) {
+        float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else if constexpr (sizeof(R) == 4 && N == 2) {
+        float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        o[0] = t.x; o[1] = t.y;
+    } else if constexpr (sizeof(R) == 8 && N == 2) {
+        double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        o[0] = t.x; o[1] = t.y;
+    } else {
+        static_assert(sizeof(R) == 8 && N == 4, "unsupported vector load");
+        double2 t0 = __ldg(reinterpret_cast<const double2 *>(p));
+        double2 t1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
+    }
+}
+
+template <class R, int N>
+__device__ __forceinline__ void ld_vec(R (&o)[N], const R *p) {
+    if constexpr (sizeof(R) == 4 && N == 4) {
+        float4 t = *reinterpret_cast<const float4 *>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else if constexpr (sizeof(R) == 4 && N == 2) {
+        float2 t = *reinterpret_cast<const float2 *>(p);
+        o[0] = t.x; o[1] = t.y;
+    } else if constexpr (sizeof(R) == 8 && N == 2) {
+        double2 t = *reinterpret_cast<const double2 *>(p);
+        o[0] = t.x; o[1] = t.y;
+    } else {
+        double2 t0 = reinterpret_cast<const double2 *>(p)[0];
+        double2 t1 = reinterpret_cast<const double2 *>(p)[1];
+        o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
+    }
+}
+
+template <class R, int N>
+__device__ __forceinline__ void st_vec(R *p, const R (&o)[N]) {
+    if constexpr (sizeof(R) == 4 && N == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (sizeof(R) == 4 && N == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(o[0], o[1]);
+    } else if constexpr (sizeof(R) == 8 && N == 2) {
+        *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
+    } else {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(o[0], o[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(o[2], o[3]);
+    }
+}
+
+// load a D x D matrix stored with rows padded to Pad<D>
+template <class R, int D>
+__device__ __forceinline__ void ldg_mat(R (&M)[D][D], const R *p) {
+    if constexpr (D == 2) {
+        R t[4];
+        ldg_vec<R, 4>(t, p);
+        M[0][0] = t[0]; M[0][1] = t[1]; M[1][0] = t[2]; M[1][1] = t[3];
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            R t[4];
+            ldg_vec<R, 4>(t, p + 4 * r);
+            M[r][0] = t[0]; M[r][1] = t[1]; M[r][2] = t[2];
+        }
+    }
+}
+
+template <class R, int D>
+__device__ __forceinline__ void st_mat(R *p, const R (&M)[D][D]) {
+    if constexpr (D == 2) {
+        R t[4] = {M[0][0], M[0][1], M[1][0], M[1][1]};
+        st_vec<R, 4>(p, t);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            R t[4] = {M[r][0], M[r][1], M[r][2], R(0)};
+            st_vec<R, 4>(p + 4 * r, t);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ math
+__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float dexp(float x) { return expf(x); }
+__device__ __forceinline__ double dexp(double x) { return exp(x); }
+__device__ __forceinline__ float drcbrt(float x) { return rcbrtf(x); }
+__device__ __forceinline__ double drcbrt(double x) { return rcbrt(x); }
+__device__ __forceinline__ float dabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double dabs(double x) { return fabs(x); }
+
+template <class R>
+__device__ __forceinline__ void m3_mul(const R (&A)[3][3], const R (&B)[3][3], R (&C)[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) C[i][j] = A[i][0] * B[0][j] + A[i][1] * B[1][j] + A[i][2] * B[2][j];
+}
+
+// C = A B^T
+template <class R>
+__device__ __forceinline__ void m3_mul_bt(const R (&A)[3][3], const R (&B)[3][3], R (&C)[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) C[i][j] = A[i][0] * B[j][0] + A[i][1] * B[j][1] + A[i][2] * B[j][2];
+}
+
+template <class R>
+__device__ __forceinline__ R m3_det(const R (&A)[3][3]) {
+    return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+           A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+           A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+}
+
+// cofactor matrix: cof(A) = det(A) A^-T
+template <class R>
+__device__ __forceinline__ void m3_cof(const R (&A)[3][3], R (&C)[3][3]) {
+    C[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+    C[0][1] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+    C[0][2] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+    C[1][0] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+    C[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+    C[1][2] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+    C[2][0] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+    C[2][1] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+    C[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+}
+
+// ------------------------------------------------------------------ laws
+struct MatConst;
+
+// St Venant-Kirchhoff (elastic reading of App. B.2): S = lambda tr(E) I + 2 mu E,
+// E = (F^T F - I)/2, P = F S.
+template <class R>
+__device__ __forceinline__ void stress_svk(const R (&F)[3][3], R lambda, R mu, R (&P)[3][3]) {
+    R E[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            E[i][j] = R(0.5) * (F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j]);
+    E[0][0] -= R(0.5); E[1][1] -= R(0.5); E[2][2] -= R(0.5);
+    R tr = E[0][0] + E[1][1] + E[2][2];
+    R S[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) S[i][j] = R(2) * mu * E[i][j];
+    S[0][0] += lambda * tr; S[1][1] += lambda * tr; S[2][2] += lambda * tr;
+    m3_mul(F, S, P);
+}
+
+template <class R>
+__device__ __forceinline__ R hard_k(R al, R s0, R sinf, R delta, R H) {
+    return s0 + (sinf - s0) * (R(1) - dexp(-delta * al)) + H * al;
+}
+template <class R>
+__device__ __forceinline__ R hard_dk(R al, R s0, R sinf, R delta, R H) {
+    return (sinf - s0) * delta * dexp(-delta * al) + H;
+}
+
+// Alg. 1 (App. A.4): J2 return mapping with saturation hardening.  cp holds
+// C_p^-1 as (xx,yy,zz,xy,yz,xz) and alpha; updated in place when plastic.
+template <class R>
+__device__ __forceinline__ void stress_j2(const R (&F)[3][3], R (&cp)[7], R K, R mu, R s0,
+                                          R sinf, R delta, R H, R (&P)[3][3]) {
+    const R r23 = R(0.816496580927726);  // sqrt(2/3)
+    R J = m3_det(F);
+    R sc = drcbrt(J);
+    R Fb[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Fb[i][j] = sc * F[i][j];
+    R Cp[3][3] = {{cp[0], cp[3], cp[5]}, {cp[3], cp[1], cp[4]}, {cp[5], cp[4], cp[2]}};
+    R T[3][3], bpre[3][3];
+    m3_mul(Fb, Cp, T);
+    m3_mul_bt(T, Fb, bpre);
+    R trb = bpre[0][0] + bpre[1][1] + bpre[2][2];
+    R s[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) s[i][j] = mu * bpre[i][j];
+    R m3 = mu * trb / R(3);
+    s[0][0] -= m3; s[1][1] -= m3; s[2][2] -= m3;
+    R sn = R(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) sn += s[i][j] * s[i][j];
+    sn = dsqrt(sn);
+    R al = cp[6];
+    R kal = hard_k(al, s0, sinf, delta, H);
+    R f = sn - r23 * kal;
+    if (f > R(0)) {
+        R mubar = mu * trb / R(3);
+        R dg = R(0);
+        const R tol = (sizeof(R) == 8) ? R(1e-13) : R(1e-6);
+        for (int it = 0; it < 30; ++it) {
+            R g = sn - r23 * hard_k(al + r23 * dg, s0, sinf, delta, H) - R(2) * mubar * dg;
+            if (dabs(g) <= tol * r23 * kal) break;
+            R dgd = -(R(2) / R(3)) * hard_dk(al + r23 * dg, s0, sinf, delta, H) - R(2) * mubar;
+            dg -= g / dgd;
+        }
+        R fac = R(1) - R(2) * mubar * dg / sn;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) s[i][j] *= fac;
+        cp[6] = al + r23 * dg;
+        // b_e = s/mu + tr(b_pre)/3 I;  C_p^-1 = Fb^-1 b_e Fb^-T  (det Fb = 1)
+        R be[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) be[i][j] = s[i][j] / mu;
+        be[0][0] += trb / R(3); be[1][1] += trb / R(3); be[2][2] += trb / R(3);
+        R Ci[3][3], Fi[3][3];
+        m3_cof(Fb, Ci);                 // cof(Fb) = det(Fb) Fb^-T
+        R idet = R(1) / m3_det(Fb);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Fi[i][j] = Ci[j][i] * idet;   // Fb^-1
+        R T2[3][3], Cn[3][3];
+        m3_mul(Fi, be, T2);
+        m3_mul_bt(T2, Fi, Cn);
+        cp[0] = Cn[0][0]; cp[1] = Cn[1][1]; cp[2] = Cn[2][2];
+        cp[3] = R(0.5) * (Cn[0][1] + Cn[1][0]);
+        cp[4] = R(0.5) * (Cn[1][2] + Cn[2][1]);
+        cp[5] = R(0.5) * (Cn[0][2] + Cn[2][0]);
+    }
+    // tau = K/2 (J^2 - 1) I + s;  P = tau F^-T = tau cof(F) / J
+    R pv = R(0.5) * K * (J * J - R(1));
+    s[0][0] += pv; s[1][1] += pv; s[2][2] += pv;
+    R Cf[3][3];
+    m3_cof(F, Cf);
+    R iJ = R(1) / J;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            P[i][j] = (s[i][0] * Cf[0][j] + s[i][1] * Cf[1][j] + s[i][2] * Cf[2][j]) * iJ;
+}
+
+// swelling (App. B.2): P -= p J F^-T = p cof(F)
+template <class R>
+__device__ __forceinline__ void add_swelling(const R (&F)[3][3], R p, R (&P)[3][3]) {
+    R Cf[3][3];
+    m3_cof(F, Cf);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) P[i][j] -= p * Cf[i][j];
+}
+
+// ------------------------------------------------------------------ reductions
+template <class T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+template <class T>
+__device__ __forceinline__ T warp_max(T x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+}  // namespace mts

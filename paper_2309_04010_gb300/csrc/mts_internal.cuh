@@ -1,0 +1,230 @@
+// mts_internal.cuh -- shared declarations of the sm_103a library (not installed).
+//
+// Layout in HBM (all particle arrays in Morton-sorted order):
+//   X    R[PAD]   reference position relative to Xmin (PAD = 2 in 2D, 4 in 3D)
+//   X64  f64[PAD] reference position (setup, reads)
+//   u    f64[PAD] displacement, FP64 accumulator (both precisions)
+//   uf   R[PAD]   gather copy of u for the neighbour loops (aliases u in FP64)
+//   v    R[PAD]   velocity
+//   acc  R[PAD]   internal acceleration of the last force stage
+//   PB   R[MS]    P B0, rows padded to PAD (MS = 4 in 2D, 12 in 3D)
+//   B0   R[MS]    correction matrix, same layout
+//   cp   R[8]     C_p^-1 (xx,yy,zz,xy,yz,xz), alpha, pad (J2 only)
+//   c    R        concentration
+//   flags u8      bits 0-2 fixed axes, 3 force set, 4 tip set, 5 c held
+//   ELL  i32      neighbour indices, slices of 32 particles, neighbour-major
+//                 inside a slice, padded with the particle itself
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mtssph.h"
+
+namespace mts {
+
+constexpr int kFixMask = 7;
+constexpr int kForceBit = 8;
+constexpr int kTipBit = 16;
+constexpr int kCHeldBit = 32;
+constexpr int kBlock = 128;  // threads per block of the per-particle kernels
+constexpr int kDampWarps = 4;  // owner groups (warps) per damping CTA
+
+// ------------------------------------------------------------------ errors
+void set_error(const char *fmt, ...);
+mts_status cuda_fail(cudaError_t e, const char *what);
+#define MTS_CUDA(call)                                        \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call);   \
+    } while (0)
+#define MTS_TRY(call)                                         \
+    do {                                                      \
+        mts_status _s = (call);                               \
+        if (_s != MTS_OK) return _s;                          \
+    } while (0)
+
+// ------------------------------------------------------------------ control
+// Device-resident state of the substep loop.  Kernels read dt, ramp and done
+// from here, so one captured graph serves every slow step.
+struct Control {
+    double dt, ramp, dt_fixed, ke_thr, volume;
+    double ke, vmax, amax, dt_last;
+    double end_force[3];
+    long long nsub, max_sub;
+    int done, converged, status, ke_mode;
+    int use_tol, pad0;
+    unsigned int counter;     // last-block-done counter of the drift kernel
+    unsigned int err;         // setup error bits
+};
+
+constexpr unsigned kErrSingular = 1u;
+constexpr unsigned kErrNonfinite = 2u;
+constexpr unsigned kErrTooMany = 4u;
+
+// ------------------------------------------------------------------ args
+template <class R>
+struct Args {
+    long long n;
+    int dim;
+    // neighbour ELL
+    const int32_t *ell;
+    const long long *slice_off;
+    const int32_t *slice_w;
+    // geometry
+    const R *X;
+    const R *B0;
+    // state
+    double *u;
+    R *uf;
+    R *v;
+    R *acc;
+    R *PB;
+    R *cp;
+    R *c;
+    R *c_tmp;
+    const uint8_t *flags;
+    const double *u_unit;
+    const R *c_held;
+    // constants
+    R inv_h;       // 1/h
+    R kcoef;       // V * (-5 alpha_d / h^2): grad_a W_ab * V = kcoef (1-q/2)^3 (X_a - X_b)
+    R inv_rho0;
+    R lambda, mu, K, s0, sinf, delta, Hlin;
+    R swell;       // 3 K beta
+    R c0;
+    R dcoef;       // 2 D * kcoef (diffusion, includes V)
+    int swelling;
+    double mass, h, cs;
+    // damping
+    R eta;
+    const uint32_t *pair_ab;
+    const R *pair_g;
+    const long long *lvl_pair;   // level -> first pair, total_levels + 1
+    const int32_t *grp_lvl;      // group -> first level, n_groups + 1
+    const int32_t *touch_start;  // group x NB
+    const int32_t *touch_cnt;
+    int mb;                      // max particles per damping block (local stride)
+    // reductions
+    Control *ctrl;
+    double *part_force;          // grid x 4 (amax, m a_x, m a_y, m a_z)
+    double *part_drift;          // grid x 2 (ke, vmax)
+};
+
+// ------------------------------------------------------------------ structs
+struct Alloc {
+    mts_allocator a;
+    bool custom;
+};
+
+}  // namespace mts
+
+struct mts_ctx {
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    mts::Alloc alloc;
+    std::vector<void *> live;
+};
+
+struct mts_body {
+    mts_ctx *ctx;
+    int dim;
+    int precision;
+    long long n;
+    double dx, h, V, cut2;
+    int blk_shift;
+    double Xmin[3];
+    size_t rsize;  // sizeof(R)
+
+    // setup products
+    long long *perm;      // sorted -> original
+    long long *rank;      // original -> sorted
+    double *X64;          // sorted, PAD
+    long long *nb_off;    // CSR
+    int32_t *nb_idx;
+    long long nnz;
+    int32_t *ell;
+    long long *slice_off;
+    int32_t *slice_w;
+    long long n_slices;
+
+    // canonical damping order
+    long long npairs;
+    int32_t *pair_a, *pair_b, *pair_col, *pair_sub;
+    long long *pair_key;
+    uint32_t *pair_ab;
+    void *pair_g;
+    long long *lvl_pair;
+    int32_t *grp_lvl;
+    int32_t *touch_start, *touch_cnt;
+    long long n_groups, n_levels;
+    int col_off[9];
+    int mb;
+
+    // state
+    void *X, *B0, *uf, *v, *acc, *PB, *cp, *c, *c_tmp, *c_held;
+    double *u, *u_unit;
+    uint8_t *flags;
+    std::vector<uint8_t> h_flags;
+
+    // material
+    bool has_material;
+    int model;
+    double rho0, E, nu, K, mu, lambda, s0, sinf, delta, Hlin, eta;
+    bool has_diff;
+    double D, beta, c0;
+
+    // loop machinery
+    mts::Control *ctrl;
+    mts::Control *h_ctrl;   // pinned
+    double *part_force, *part_drift;
+    double *scratch;        // n x 9 doubles for field transfers
+    double *h_stage;        // pinned staging for field transfers (n x 9)
+    cudaGraphExec_t graph;
+    int graph_chunk;
+    bool graph_dirty;
+    int tip_count;
+    int prof_stage;
+    int graph_prof_stage;
+    std::vector<cudaEvent_t> prof_ev;   // 2 per substep of a chunk
+    long long launches_per_substep;
+};
+
+namespace mts {
+// allocation through the context allocator
+void *dalloc(mts_ctx *ctx, size_t bytes);
+void dfree(mts_ctx *ctx, void *p);
+mts_status dalloc_into(mts_ctx *ctx, void **p, size_t bytes);
+template <class T>
+inline mts_status dalloc_t(mts_ctx *ctx, T **p, size_t count) {
+    return dalloc_into(ctx, reinterpret_cast<void **>(p), count * sizeof(T) + 16);
+}
+
+// setup (mts_setup.cu)
+mts_status build_body(mts_body *b, const double *hX);
+
+// substep machinery (mts_substep.cu)
+mts_status launch_stress(mts_body *b);
+mts_status launch_force(mts_body *b);
+mts_status launch_damping(mts_body *b, long long *launches = nullptr);
+mts_status launch_drift(mts_body *b);
+mts_status prepare_kernels(mts_body *b);
+mts_status launch_slow_begin(mts_body *b);
+mts_status launch_diffusion(mts_body *b, double dt);
+mts_status diffusion_bound(mts_body *b, double *amax_sum);
+mts_status launch_defgrad(mts_body *b, double *out_sorted);
+mts_status launch_tip(mts_body *b, double *out3);
+mts_status launch_reset_ctrl(mts_body *b, double dt, double dt_fixed, double ramp,
+                             long long max_sub, double ke_thr, int ke_mode, int use_tol);
+// field transfers in sorted order (device scratch, double)
+mts_status field_to_scratch(mts_body *b, int field);
+mts_status scratch_to_field(mts_body *b, int field);
+int field_width(const mts_body *b, int field);
+
+// kernel-function constants
+double kernel_alpha(int dim, double h);
+}  // namespace mts

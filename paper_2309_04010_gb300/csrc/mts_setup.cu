@@ -1,0 +1,816 @@
+// mts_setup.cu -- one-time body setup on the GPU (Sec. 3.1: the neighbourhood
+// and the correction matrix B0 are fixed in the reference configuration).
+//
+//   1. Morton order: cell = floor((X - Xmin)/dx), key = bit interleave (x lowest),
+//      stable radix sort, so equal keys keep the original index order.
+//   2. Neighbour CSR: all j != i with |X_i - X_j|^2 < (2h)^2, evaluated in FP64
+//      with explicit round-to-nearest multiply/add (no fused multiply-add), over
+//      a dense cell grid; rows sorted ascending with a segmented sort.
+//   3. B0_a = (sum_b V (X_b - X_a) (x) grad_a W_ab)^-1 in FP64.
+//   4. Sliced ELL copy of the CSR for the substep kernels.
+//   5. Canonical order of the pairwise damping (Sec. 4.3): pairs owned by the
+//      componentwise-min block (blocks of 2^s cells, 2^s dx > 2h) of their two
+//      particles; block colour = parity bits; greedy sub-colours in ascending
+//      (a,b) per owner block; then per-block level lists with block-local
+//      particle indices for the shared-memory damping kernel.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "mts_device.cuh"
+#include "mts_internal.cuh"
+
+namespace mts {
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline unsigned grid_for(long long n, int tpb = TPB) {
+    return (unsigned)((n + tpb - 1) / tpb);
+}
+
+__host__ __device__ inline unsigned long long morton(int dim, long long c0, long long c1,
+                                                     long long c2) {
+    unsigned long long key = 0;
+    long long c[3] = {c0, c1, c2};
+    int bits = dim == 2 ? 32 : 21;
+    for (int bit = 0; bit < bits; ++bit)
+        for (int k = 0; k < dim; ++k)
+            key |= (unsigned long long)((c[k] >> bit) & 1) << (bit * dim + k);
+    return key;
+}
+
+// exact FP64 squared distance (explicit rounding, no contraction)
+__device__ inline double dist2_rn(const double *a, const double *b, int dim) {
+    double d0 = __dsub_rn(a[0], b[0]);
+    double d1 = __dsub_rn(a[1], b[1]);
+    double r2 = __dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1));
+    if (dim == 3) {
+        double d2 = __dsub_rn(a[2], b[2]);
+        r2 = __dadd_rn(r2, __dmul_rn(d2, d2));
+    }
+    return r2;
+}
+
+// ---------------------------------------------------------------- extents
+__global__ void k_extent_partial(const double *X, long long n, int dim, double *part) {
+    __shared__ double smin[3][TPB];
+    __shared__ int sbad[TPB];
+    double mn[3] = {INFINITY, INFINITY, INFINITY};
+    int bad = 0;
+    for (long long i = blockIdx.x * (long long)TPB + threadIdx.x; i < n;
+         i += (long long)gridDim.x * TPB)
+        for (int k = 0; k < dim; ++k) {
+            double x = X[i * dim + k];
+            if (!isfinite(x)) bad = 1;
+            mn[k] = fmin(mn[k], x);
+        }
+    for (int k = 0; k < 3; ++k) smin[k][threadIdx.x] = mn[k];
+    sbad[threadIdx.x] = bad;
+    __syncthreads();
+    for (int s = TPB / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            for (int k = 0; k < 3; ++k)
+                smin[k][threadIdx.x] = fmin(smin[k][threadIdx.x], smin[k][threadIdx.x + s]);
+            sbad[threadIdx.x] |= sbad[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) part[blockIdx.x * 4 + k] = smin[k][0];
+        part[blockIdx.x * 4 + 3] = sbad[0];
+    }
+}
+
+__global__ void k_extent_final(const double *part, int nblk, double *out) {
+    if (threadIdx.x != 0) return;
+    double mn[3] = {INFINITY, INFINITY, INFINITY};
+    double bad = 0;
+    for (int b = 0; b < nblk; ++b) {
+        for (int k = 0; k < 3; ++k) mn[k] = fmin(mn[k], part[b * 4 + k]);
+        bad = fmax(bad, part[b * 4 + 3]);
+    }
+    for (int k = 0; k < 3; ++k) out[k] = mn[k];
+    out[3] = bad;
+}
+
+// ---------------------------------------------------------------- Morton keys
+__global__ void k_keys(const double *X, long long n, int dim, double x0, double x1, double x2,
+                       double dx, unsigned long long *keys, long long *vals,
+                       unsigned long long *cmax) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double xm[3] = {x0, x1, x2};
+    long long c[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) {
+        c[k] = (long long)floor(__ddiv_rn(__dsub_rn(X[i * dim + k], xm[k]), dx));
+        atomicMax(cmax + k, (unsigned long long)c[k]);
+    }
+    keys[i] = morton(dim, c[0], c[1], c[2]);
+    vals[i] = i;
+}
+
+template <class R, int D>
+__global__ void k_apply_perm(const double *Xo, const long long *perm, long long n, double x0,
+                             double x1, double x2, double dx, double *X64, R *Xr,
+                             long long *rank, int *cell) {
+    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    constexpr int P = Pad<D>::v;
+    long long i = perm[s];
+    rank[i] = s;
+    double xm[3] = {x0, x1, x2};
+    for (int k = 0; k < P; ++k) {
+        double x = k < D ? Xo[i * D + k] : 0.0;
+        X64[s * P + k] = x;
+        Xr[s * P + k] = k < D ? (R)(x - xm[k]) : R(0);
+    }
+    for (int k = 0; k < 3; ++k)
+        cell[s * 3 + k] = k < D ? (int)floor(__ddiv_rn(__dsub_rn(Xo[i * D + k], xm[k]), dx)) : 0;
+}
+
+// ---------------------------------------------------------------- cell grid
+__global__ void k_cell_ranges(const unsigned long long *keys, const int *cell, long long n,
+                              long long g0, long long g1, int *cstart, int *cend) {
+    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    long long lin = ((long long)cell[s * 3 + 2] * g1 + cell[s * 3 + 1]) * g0 + cell[s * 3 + 0];
+    if (s == 0 || keys[s] != keys[s - 1]) cstart[lin] = (int)s;
+    if (s == n - 1 || keys[s + 1] != keys[s]) cend[lin] = (int)(s + 1);
+}
+
+template <int D, bool FILL>
+__global__ void k_neigh(const double *X64, const int *cell, long long n, long long g0,
+                        long long g1, long long g2, int reach, double cut2, const int *cstart,
+                        const int *cend, long long *cnt, const long long *off, int32_t *out) {
+    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    constexpr int P = Pad<D>::v;
+    const double *xs = X64 + s * P;
+    int cx = cell[s * 3], cy = cell[s * 3 + 1], cz = cell[s * 3 + 2];
+    long long c = 0;
+    long long base = FILL ? off[s] : 0;
+    int zr = D == 3 ? reach : 0;
+    for (int z = cz - zr; z <= cz + zr; ++z) {
+        if (z < 0 || z >= g2) continue;
+        for (int y = cy - reach; y <= cy + reach; ++y) {
+            if (y < 0 || y >= g1) continue;
+            for (int x = cx - reach; x <= cx + reach; ++x) {
+                if (x < 0 || x >= g0) continue;
+                long long lin = ((long long)z * g1 + y) * g0 + x;
+                int a = cstart[lin];
+                if (a < 0) continue;
+                int e = cend[lin];
+                for (int j = a; j < e; ++j) {
+                    if (j == s) continue;
+                    if (dist2_rn(xs, X64 + (long long)j * P, D) < cut2) {
+                        if (FILL) out[base + c] = j;
+                        ++c;
+                    }
+                }
+            }
+        }
+    }
+    if (!FILL) cnt[s] = c;
+}
+
+// ---------------------------------------------------------------- B0
+template <class R, int D>
+__global__ void k_b0(const double *X64, const long long *off, const int32_t *idx, long long n,
+                     double h, double alpha, double V, R *B0, Control *ctrl) {
+    long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    constexpr int P = Pad<D>::v;
+    double S[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const double *xa = X64 + a * P;
+    for (long long p = off[a]; p < off[a + 1]; ++p) {
+        const double *xb = X64 + (long long)idx[p] * P;
+        double d[3] = {0, 0, 0}, r2 = 0;
+        for (int k = 0; k < D; ++k) {
+            d[k] = xa[k] - xb[k];
+            r2 += d[k] * d[k];
+        }
+        double r = sqrt(r2);
+        double q = r / h;
+        double t = 1.0 - 0.5 * q;
+        double dw = -5.0 * alpha * q * t * t * t / h;   // W'(r)
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) S[i][j] += V * (-d[i]) * (dw * d[j] / r);
+    }
+    double nrm = 0;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) nrm += S[i][j] * S[i][j];
+    nrm = sqrt(nrm);
+    R out[D][D];
+    if (D == 2) {
+        double det = S[0][0] * S[1][1] - S[0][1] * S[1][0];
+        if (!(fabs(det) >= 1e-12 * nrm * nrm) || nrm == 0.0) {
+            atomicOr(&ctrl->err, kErrSingular);
+            det = 1.0;
+        }
+        out[0][0] = (R)(S[1][1] / det);
+        out[0][1] = (R)(-S[0][1] / det);
+        out[1][0] = (R)(-S[1][0] / det);
+        out[1][1] = (R)(S[0][0] / det);
+    } else {
+        double det = S[0][0] * (S[1][1] * S[2][2] - S[1][2] * S[2][1]) -
+                     S[0][1] * (S[1][0] * S[2][2] - S[1][2] * S[2][0]) +
+                     S[0][2] * (S[1][0] * S[2][1] - S[1][1] * S[2][0]);
+        if (!(fabs(det) >= 1e-12 * nrm * nrm * nrm) || nrm == 0.0) {
+            atomicOr(&ctrl->err, kErrSingular);
+            det = 1.0;
+        }
+        double C[3][3];
+        C[0][0] = S[1][1] * S[2][2] - S[1][2] * S[2][1];
+        C[0][1] = S[0][2] * S[2][1] - S[0][1] * S[2][2];
+        C[0][2] = S[0][1] * S[1][2] - S[0][2] * S[1][1];
+        C[1][0] = S[1][2] * S[2][0] - S[1][0] * S[2][2];
+        C[1][1] = S[0][0] * S[2][2] - S[0][2] * S[2][0];
+        C[1][2] = S[0][2] * S[1][0] - S[0][0] * S[1][2];
+        C[2][0] = S[1][0] * S[2][1] - S[1][1] * S[2][0];
+        C[2][1] = S[0][1] * S[2][0] - S[0][0] * S[2][1];
+        C[2][2] = S[0][0] * S[1][1] - S[0][1] * S[1][0];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) out[i][j] = (R)(C[i][j] / det);
+    }
+    R *dst = B0 + a * MatS<D>::v;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < P; ++j) dst[i * P + j] = j < D ? out[i][j] : R(0);
+}
+
+// ---------------------------------------------------------------- ELL
+__global__ void k_slice_w(const long long *off, long long n, long long nslices, long long *w) {
+    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= nslices) return;
+    long long m = 0;
+    for (long long i = s * 32; i < min(n, s * 32 + 32); ++i) m = max(m, off[i + 1] - off[i]);
+    w[s] = m * 32;
+}
+
+__global__ void k_fill_ell(const long long *off, const int32_t *idx, long long n,
+                           const long long *soff, int32_t *sw, int32_t *ell) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long s = i >> 5;
+    int lane = (int)(i & 31);
+    long long nslices = (n + 31) / 32;
+    if (s >= nslices) return;
+    long long width = (soff[s + 1] - soff[s]) / 32;
+    if (lane == 0) sw[s] = (int32_t)width;
+    long long deg = i < n ? off[i + 1] - off[i] : 0;
+    for (long long j = 0; j < width; ++j)
+        ell[soff[s] + j * 32 + lane] = (int32_t)(j < deg ? idx[off[i] + j] : (i < n ? i : 0));
+}
+
+// ---------------------------------------------------------------- damping order
+__global__ void k_count_pairs(const long long *off, const int32_t *idx, long long n,
+                              long long *cnt) {
+    long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    long long c = 0;
+    for (long long p = off[a]; p < off[a + 1]; ++p) c += idx[p] > a;
+    cnt[a] = c;
+}
+
+__global__ void k_fill_pairs(const long long *off, const int32_t *idx, const int *cell,
+                             long long n, int dim, int shift, const long long *poff,
+                             int32_t *pa, int32_t *pb, unsigned long long *key) {
+    long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    long long t = poff[a];
+    for (long long p = off[a]; p < off[a + 1]; ++p) {
+        int b = idx[p];
+        if (b <= a) continue;
+        long long ob[3] = {0, 0, 0};
+        int col = 0;
+        for (int k = 0; k < dim; ++k) {
+            long long ba = cell[a * 3 + k] >> shift, bb = cell[(long long)b * 3 + k] >> shift;
+            ob[k] = ba < bb ? ba : bb;
+            col |= (int)(ob[k] & 1) << k;
+        }
+        pa[t] = (int32_t)a;
+        pb[t] = b;
+        key[t] = ((unsigned long long)col << 60) | morton(dim, ob[0], ob[1], ob[2]);
+        ++t;
+    }
+}
+
+template <class T>
+__global__ void k_gather(const T *src, const long long *order, long long m, T *dst) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p < m) dst[p] = src[order[p]];
+}
+
+__global__ void k_iota(long long *v, long long m) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p < m) v[p] = p;
+}
+
+__global__ void k_run_flags(const unsigned long long *key, long long m, long long *flag) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p < m) flag[p] = (p == 0 || key[p] != key[p - 1]) ? 1 : 0;
+}
+
+// after an inclusive scan of the flags: id = scan - 1
+__global__ void k_run_starts(const long long *scan, long long m, long long *start) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    if (p == 0 || scan[p] != scan[p - 1]) start[scan[p] - 1] = p;
+}
+
+__global__ void k_block_keys(const int *cell, long long n, int dim, int shift,
+                             unsigned long long *bkey) {
+    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    bkey[s] = morton(dim, cell[s * 3] >> shift, cell[s * 3 + 1] >> shift,
+                     cell[s * 3 + 2] >> shift);
+}
+
+__global__ void k_block_table(const long long *bstart, long long nb, long long n,
+                              const unsigned long long *bkey_p, unsigned long long *bkey,
+                              int *bcnt, unsigned int *mb) {
+    long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    long long s = bstart[b];
+    long long e = b + 1 < nb ? bstart[b + 1] : n;
+    bkey[b] = bkey_p[s];
+    bcnt[b] = (int)(e - s);
+    atomicMax(mb, (unsigned int)(e - s));
+}
+
+__device__ long long find_key(const unsigned long long *keys, long long m, unsigned long long k) {
+    long long lo = 0, hi = m;
+    while (lo < hi) {
+        long long mid = (lo + hi) >> 1;
+        if (keys[mid] < k) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < m && keys[lo] == k) ? lo : -1;
+}
+
+// per owner group: the 2^d touched blocks (owner + e), their start and count
+__global__ void k_touch(const long long *gstart, long long ng, const int32_t *pa, const int32_t *pb,
+                        const int *cell, int dim, int shift, const unsigned long long *bkey,
+                        const long long *bstart, const int *bcnt, long long nblocks,
+                        int32_t *tstart, int32_t *tcnt, int32_t *gcol, long long *gkey) {
+    long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    long long p = gstart[g];
+    int a = pa[p], b = pb[p];
+    long long ob[3] = {0, 0, 0};
+    int col = 0;
+    for (int k = 0; k < dim; ++k) {
+        long long ba = cell[(long long)a * 3 + k] >> shift, bb = cell[(long long)b * 3 + k] >> shift;
+        ob[k] = ba < bb ? ba : bb;
+        col |= (int)(ob[k] & 1) << k;
+    }
+    gcol[g] = col;
+    gkey[g] = (long long)morton(dim, ob[0], ob[1], ob[2]);
+    int nbk = 1 << dim;
+    for (int e = 0; e < nbk; ++e) {
+        long long c0 = ob[0] + (e & 1), c1 = ob[1] + ((e >> 1) & 1), c2 = dim == 3 ? ob[2] + ((e >> 2) & 1) : 0;
+        long long bi = find_key(bkey, nblocks, morton(dim, c0, c1, c2));
+        tstart[g * nbk + e] = bi >= 0 ? (int32_t)bstart[bi] : 0;
+        tcnt[g * nbk + e] = bi >= 0 ? bcnt[bi] : 0;
+    }
+}
+
+// greedy sub-colouring of one owner group per thread; local particle index =
+// e * mb + (particle - start of block owner + e)
+__global__ void k_greedy(const long long *gstart, long long g0, long long g1, long long ng,
+                         long long m, const int32_t *pa, const int32_t *pb, const int *cell,
+                         int dim, int shift, const int32_t *tstart, int mb,
+                         unsigned long long *used, int32_t *sub, uint32_t *ab, int32_t *nsub,
+                         Control *ctrl) {
+    long long g = g0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g >= g1) return;
+    int nbk = 1 << dim;
+    unsigned long long *U = used + (g - g0) * (long long)nbk * mb * 4;
+    long long p0 = gstart[g], p1 = g + 1 < ng ? gstart[g + 1] : m;
+    long long ob[3] = {0, 0, 0};
+    {
+        int a = pa[p0], b = pb[p0];
+        for (int k = 0; k < dim; ++k) {
+            long long ba = cell[(long long)a * 3 + k] >> shift, bb = cell[(long long)b * 3 + k] >> shift;
+            ob[k] = ba < bb ? ba : bb;
+        }
+    }
+    int maxc = -1;
+    for (long long p = p0; p < p1; ++p) {
+        int loc[2];
+        int pp[2] = {pa[p], pb[p]};
+        for (int t = 0; t < 2; ++t) {
+            int e = 0;
+            for (int k = 0; k < dim; ++k)
+                e |= (int)((cell[(long long)pp[t] * 3 + k] >> shift) - ob[k]) << k;
+            loc[t] = e * mb + (pp[t] - tstart[g * nbk + e]);
+        }
+        unsigned long long *ua = U + (long long)loc[0] * 4, *ub = U + (long long)loc[1] * 4;
+        int c = -1;
+        for (int w = 0; w < 4 && c < 0; ++w) {
+            unsigned long long free_bits = ~(ua[w] | ub[w]);
+            if (free_bits) c = w * 64 + __ffsll((long long)free_bits) - 1;
+        }
+        if (c < 0) {
+            atomicOr(&ctrl->err, kErrTooMany);
+            c = 255;
+        }
+        ua[c >> 6] |= 1ull << (c & 63);
+        ub[c >> 6] |= 1ull << (c & 63);
+        sub[p] = c;
+        ab[p] = (uint32_t)loc[0] | ((uint32_t)loc[1] << 16);
+        maxc = max(maxc, c);
+    }
+    nsub[g] = maxc + 1;
+}
+
+__global__ void k_group_of_pair(const long long *gscan, long long m, const int32_t *sub,
+                                unsigned long long *key2) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p < m) key2[p] = ((unsigned long long)(gscan[p] - 1) << 8) | (unsigned)sub[p];
+}
+
+__global__ void k_levels(const unsigned long long *key2, long long m, const int32_t *grp_lvl,
+                         long long *lvl_pair, long long nlev) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p > m) return;
+    if (p == m) {
+        lvl_pair[nlev] = m;
+        return;
+    }
+    if (p == 0 || key2[p] != key2[p - 1]) {
+        long long g = (long long)(key2[p] >> 8);
+        int s = (int)(key2[p] & 255);
+        lvl_pair[grp_lvl[g] + s] = p;
+    }
+}
+
+template <class R, int D>
+__global__ void k_pair_coef(const int32_t *pa, const int32_t *pb, long long m, const double *X64,
+                            double h, double alpha, double V, R *g) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    constexpr int P = Pad<D>::v;
+    const double *xa = X64 + (long long)pa[p] * P, *xb = X64 + (long long)pb[p] * P;
+    double r2 = 0;
+    for (int k = 0; k < D; ++k) {
+        double d = xa[k] - xb[k];
+        r2 += d * d;
+    }
+    double r = sqrt(r2);
+    double q = r / h, t = 1.0 - 0.5 * q;
+    double dw = -5.0 * alpha * q * t * t * t / h;
+    g[p] = (R)(-2.0 * V * V * dw / r);   // B_ab / eta
+}
+
+__global__ void k_col_off(const int32_t *gcol, long long ng, int ncol, int *col_off) {
+    long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g > ng) return;
+    int cprev = g == 0 ? -1 : gcol[g - 1];
+    int cnow = g == ng ? ncol : gcol[g];
+    for (int c = cprev + 1; c <= cnow; ++c) col_off[c] = (int)g;
+}
+
+__global__ void k_minus_one(const long long *in, long long m, long long *out) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p < m) out[p] = in[p] - 1;
+}
+
+// ---------------------------------------------------------------- helpers
+struct Tmp {
+    mts_ctx *ctx;
+    std::vector<void *> ptrs;
+    ~Tmp() {
+        for (void *p : ptrs) dfree(ctx, p);
+    }
+    template <class T>
+    T *get(size_t count) {
+        void *p = dalloc(ctx, count * sizeof(T) + 16);
+        if (p) ptrs.push_back(p);
+        return (T *)p;
+    }
+};
+
+#define NEED(p)                                                  \
+    do {                                                         \
+        if (!(p)) {                                              \
+            set_error("device allocation failed (%s)", #p);      \
+            return MTS_ERR_OOM;                                  \
+        }                                                        \
+    } while (0)
+
+template <class T>
+mts_status cub_excl_sum(Tmp &tmp, const T *in, T *out, long long m, cudaStream_t st) {
+    size_t bytes = 0;
+    MTS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, m, st));
+    void *t = tmp.get<char>(bytes);
+    NEED(t);
+    MTS_CUDA(cub::DeviceScan::ExclusiveSum(t, bytes, in, out, m, st));
+    return MTS_OK;
+}
+
+template <class T>
+mts_status cub_incl_sum(Tmp &tmp, const T *in, T *out, long long m, cudaStream_t st) {
+    size_t bytes = 0;
+    MTS_CUDA(cub::DeviceScan::InclusiveSum(nullptr, bytes, in, out, m, st));
+    void *t = tmp.get<char>(bytes);
+    NEED(t);
+    MTS_CUDA(cub::DeviceScan::InclusiveSum(t, bytes, in, out, m, st));
+    return MTS_OK;
+}
+
+mts_status cub_sort_pairs(Tmp &tmp, const unsigned long long *kin, unsigned long long *kout,
+                          const long long *vin, long long *vout, long long m, int end_bit,
+                          cudaStream_t st) {
+    size_t bytes = 0;
+    MTS_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kin, kout, vin, vout, m, 0, end_bit, st));
+    void *t = tmp.get<char>(bytes);
+    NEED(t);
+    MTS_CUDA(cub::DeviceRadixSort::SortPairs(t, bytes, kin, kout, vin, vout, m, 0, end_bit, st));
+    return MTS_OK;
+}
+
+template <class T>
+mts_status to_host(T *h, const T *d, size_t count, cudaStream_t st) {
+    MTS_CUDA(cudaMemcpyAsync(h, d, count * sizeof(T), cudaMemcpyDeviceToHost, st));
+    MTS_CUDA(cudaStreamSynchronize(st));
+    return MTS_OK;
+}
+
+template <class R, int D>
+mts_status build_typed(mts_body *b, const double *hX) {
+    mts_ctx *ctx = b->ctx;
+    cudaStream_t st = ctx->stream;
+    const long long n = b->n;
+    constexpr int P = Pad<D>::v;
+    Tmp tmp{ctx, {}};
+
+    // -- reference positions to the device, extent and finiteness
+    double *Xo = tmp.get<double>(n * D);
+    NEED(Xo);
+    MTS_CUDA(cudaMemcpyAsync(Xo, hX, n * D * sizeof(double), cudaMemcpyHostToDevice, st));
+    int nb = (int)std::min<long long>(grid_for(n), 1024);
+    double *part = tmp.get<double>(nb * 4 + 4);
+    NEED(part);
+    k_extent_partial<<<nb, TPB, 0, st>>>(Xo, n, D, part);
+    k_extent_final<<<1, 32, 0, st>>>(part, nb, part + nb * 4);
+    double ext[4];
+    MTS_TRY(to_host(ext, part + nb * 4, 4, st));
+    if (ext[3] != 0.0) {
+        set_error("reference positions contain NaN or Inf");
+        return MTS_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < 3; ++k) b->Xmin[k] = k < D ? ext[k] : 0.0;
+
+    // -- Morton keys and stable sort
+    unsigned long long *keys = tmp.get<unsigned long long>(n), *keys_s = tmp.get<unsigned long long>(n);
+    long long *vals = tmp.get<long long>(n);
+    unsigned long long *cmax = tmp.get<unsigned long long>(4);
+    NEED(keys); NEED(keys_s); NEED(vals); NEED(cmax);
+    MTS_CUDA(cudaMemsetAsync(cmax, 0, 4 * sizeof(unsigned long long), st));
+    k_keys<<<grid_for(n), TPB, 0, st>>>(Xo, n, D, b->Xmin[0], b->Xmin[1], b->Xmin[2], b->dx, keys,
+                                          vals, cmax);
+    unsigned long long hcmax[4];
+    MTS_TRY(to_host(hcmax, cmax, 4, st));
+    long long g0 = (long long)hcmax[0] + 1, g1 = (long long)hcmax[1] + 1,
+              g2 = D == 3 ? (long long)hcmax[2] + 1 : 1;
+    long long bits = D == 2 ? 31 : 21;
+    if (g0 >= (1LL << bits) || g1 >= (1LL << bits) || g2 >= (1LL << bits)) {
+        set_error("body extent too large for the Morton key (%lld x %lld x %lld cells)", g0, g1, g2);
+        return MTS_ERR_INVALID_ARG;
+    }
+    long long ncell = g0 * g1 * g2;
+    if (ncell > std::max<long long>(64 * n, 1LL << 22)) {
+        set_error("body too sparse for the dense cell grid (%lld cells for %lld particles)", ncell, n);
+        return MTS_ERR_INVALID_ARG;
+    }
+    MTS_TRY(cub_sort_pairs(tmp, keys, keys_s, vals, b->perm, n, D * (int)bits + 1 > 64 ? 64 : D * (int)bits, st));
+
+    int *cell = tmp.get<int>(n * 3);
+    NEED(cell);
+    k_apply_perm<R, D><<<grid_for(n), TPB, 0, st>>>(Xo, b->perm, n, b->Xmin[0], b->Xmin[1],
+                                                    b->Xmin[2], b->dx, b->X64, (R *)b->X,
+                                                    b->rank, cell);
+
+    // -- neighbours
+    int *cstart = tmp.get<int>(ncell), *cend = tmp.get<int>(ncell);
+    NEED(cstart); NEED(cend);
+    MTS_CUDA(cudaMemsetAsync(cstart, 0xff, ncell * sizeof(int), st));
+    MTS_CUDA(cudaMemsetAsync(cend, 0xff, ncell * sizeof(int), st));
+    k_cell_ranges<<<grid_for(n), TPB, 0, st>>>(keys_s, cell, n, g0, g1, cstart, cend);
+    int reach = (int)std::floor(2.0 * b->h / b->dx) + 1;
+    long long *deg = tmp.get<long long>(n + 1);
+    NEED(deg);
+    k_neigh<D, false><<<grid_for(n), TPB, 0, st>>>(b->X64, cell, n, g0, g1, g2, reach, b->cut2,
+                                                     cstart, cend, deg, nullptr, nullptr);
+    MTS_CUDA(cudaMemsetAsync(deg + n, 0, sizeof(long long), st));
+    MTS_TRY(dalloc_t(ctx, &b->nb_off, n + 1));
+    MTS_TRY(cub_excl_sum(tmp, deg, b->nb_off, n + 1, st));
+    MTS_TRY(to_host(&b->nnz, b->nb_off + n, 1, st));
+    if (b->nnz == 0) {
+        set_error("no particle has a neighbour within 2h: every correction matrix is singular");
+        return MTS_ERR_SINGULAR_B;
+    }
+    int32_t *idx_u = tmp.get<int32_t>(std::max(b->nnz, 1LL));
+    NEED(idx_u);
+    MTS_TRY(dalloc_t(ctx, &b->nb_idx, std::max(b->nnz, 1LL)));
+    k_neigh<D, true><<<grid_for(n), TPB, 0, st>>>(b->X64, cell, n, g0, g1, g2, reach, b->cut2,
+                                                    cstart, cend, nullptr, b->nb_off, idx_u);
+    if (b->nnz > 0) {
+        size_t bytes = 0;
+        MTS_CUDA(cub::DeviceSegmentedSort::SortKeys(nullptr, bytes, idx_u, b->nb_idx, b->nnz, n,
+                                                    b->nb_off, b->nb_off + 1, st));
+        void *t = tmp.get<char>(bytes);
+        NEED(t);
+        MTS_CUDA(cub::DeviceSegmentedSort::SortKeys(t, bytes, idx_u, b->nb_idx, b->nnz, n,
+                                                    b->nb_off, b->nb_off + 1, st));
+    }
+
+    // -- B0
+    double alpha = kernel_alpha(D, b->h);
+    MTS_CUDA(cudaMemsetAsync(&b->ctrl->err, 0, sizeof(unsigned), st));
+    k_b0<R, D><<<grid_for(n), TPB, 0, st>>>(b->X64, b->nb_off, b->nb_idx, n, b->h, alpha, b->V,
+                                             (R *)b->B0, b->ctrl);
+
+    // -- sliced ELL
+    b->n_slices = (n + 31) / 32;
+    long long *sw = tmp.get<long long>(b->n_slices + 1);
+    NEED(sw);
+    MTS_TRY(dalloc_t(ctx, &b->slice_off, b->n_slices + 1));
+    MTS_TRY(dalloc_t(ctx, &b->slice_w, b->n_slices + 1));
+    k_slice_w<<<grid_for(b->n_slices), TPB, 0, st>>>(b->nb_off, n, b->n_slices, sw);
+    MTS_CUDA(cudaMemsetAsync(sw + b->n_slices, 0, sizeof(long long), st));
+    MTS_TRY(cub_excl_sum(tmp, sw, b->slice_off, b->n_slices + 1, st));
+    long long ell_len = 0;
+    MTS_TRY(to_host(&ell_len, b->slice_off + b->n_slices, 1, st));
+    MTS_TRY(dalloc_t(ctx, &b->ell, std::max(ell_len, 1LL)));
+    k_fill_ell<<<grid_for(b->n_slices * 32), TPB, 0, st>>>(b->nb_off, b->nb_idx, n, b->slice_off,
+                                                             b->slice_w, b->ell);
+
+    // -- damping order: owned pairs
+    long long *pcnt = tmp.get<long long>(n + 1), *poff = tmp.get<long long>(n + 1);
+    NEED(pcnt); NEED(poff);
+    k_count_pairs<<<grid_for(n), TPB, 0, st>>>(b->nb_off, b->nb_idx, n, pcnt);
+    MTS_CUDA(cudaMemsetAsync(pcnt + n, 0, sizeof(long long), st));
+    MTS_TRY(cub_excl_sum(tmp, pcnt, poff, n + 1, st));
+    long long m = 0;
+    MTS_TRY(to_host(&m, poff + n, 1, st));
+    b->npairs = m;
+    if (m * 2 != b->nnz) {
+        set_error("neighbour lists are not symmetric (%lld pairs, %lld entries)", m, b->nnz);
+        return MTS_ERR_STATE;
+    }
+    const long long mm = std::max(m, 1LL);
+    int32_t *pa0 = tmp.get<int32_t>(mm), *pb0 = tmp.get<int32_t>(mm);
+    unsigned long long *pk0 = tmp.get<unsigned long long>(mm), *pk1 = tmp.get<unsigned long long>(mm);
+    long long *ord = tmp.get<long long>(mm), *ord1 = tmp.get<long long>(mm);
+    NEED(pa0); NEED(pb0); NEED(pk0); NEED(pk1); NEED(ord); NEED(ord1);
+    k_fill_pairs<<<grid_for(n), TPB, 0, st>>>(b->nb_off, b->nb_idx, cell, n, D, b->blk_shift, poff,
+                                              pa0, pb0, pk0);
+    k_iota<<<grid_for(m), TPB, 0, st>>>(ord, m);
+    MTS_TRY(cub_sort_pairs(tmp, pk0, pk1, ord, ord1, m, 63, st));
+    int32_t *pa1 = tmp.get<int32_t>(mm), *pb1 = tmp.get<int32_t>(mm);
+    NEED(pa1); NEED(pb1);
+    k_gather<<<grid_for(m), TPB, 0, st>>>(pa0, ord1, m, pa1);
+    k_gather<<<grid_for(m), TPB, 0, st>>>(pb0, ord1, m, pb1);
+
+    // owner groups
+    long long *flag = tmp.get<long long>(mm), *gscan = tmp.get<long long>(mm);
+    NEED(flag); NEED(gscan);
+    k_run_flags<<<grid_for(m), TPB, 0, st>>>(pk1, m, flag);
+    MTS_TRY(cub_incl_sum(tmp, flag, gscan, m, st));
+    long long ng = 0;
+    if (m > 0) MTS_TRY(to_host(&ng, gscan + m - 1, 1, st));
+    b->n_groups = ng;
+    const long long ngg = std::max(ng, 1LL);
+    long long *gstart = tmp.get<long long>(ngg + 1);
+    NEED(gstart);
+    k_run_starts<<<grid_for(m), TPB, 0, st>>>(gscan, m, gstart);
+
+    // block table (particles are contiguous per block in Morton order)
+    unsigned long long *bkp = tmp.get<unsigned long long>(n);
+    long long *bflag = tmp.get<long long>(n), *bscan = tmp.get<long long>(n);
+    NEED(bkp); NEED(bflag); NEED(bscan);
+    k_block_keys<<<grid_for(n), TPB, 0, st>>>(cell, n, D, b->blk_shift, bkp);
+    k_run_flags<<<grid_for(n), TPB, 0, st>>>(bkp, n, bflag);
+    MTS_TRY(cub_incl_sum(tmp, bflag, bscan, n, st));
+    long long nblocks = 0;
+    MTS_TRY(to_host(&nblocks, bscan + n - 1, 1, st));
+    long long *bstart = tmp.get<long long>(nblocks + 1);
+    unsigned long long *bkey = tmp.get<unsigned long long>(nblocks + 1);
+    int *bcnt = tmp.get<int>(nblocks + 1);
+    unsigned int *dmb = tmp.get<unsigned int>(1);
+    NEED(bstart); NEED(bkey); NEED(bcnt); NEED(dmb);
+    k_run_starts<<<grid_for(n), TPB, 0, st>>>(bscan, n, bstart);
+    MTS_CUDA(cudaMemsetAsync(dmb, 0, sizeof(unsigned), st));
+    k_block_table<<<grid_for(nblocks), TPB, 0, st>>>(bstart, nblocks, n, bkp, bkey, bcnt, dmb);
+    unsigned int hmb = 0;
+    MTS_TRY(to_host(&hmb, dmb, 1, st));
+    const int nbk = 1 << D;
+    if ((long long)hmb * nbk > 65535) {
+        set_error("damping block holds %u particles; at most %d fit the 16-bit local index",
+                  hmb, 65535 / nbk);
+        return MTS_ERR_INVALID_ARG;
+    }
+    b->mb = (int)hmb;
+
+    int32_t *gcol = tmp.get<int32_t>(ngg);
+    long long *gkey = tmp.get<long long>(ngg);
+    NEED(gcol); NEED(gkey);
+    MTS_TRY(dalloc_t(ctx, &b->touch_start, ngg * nbk));
+    MTS_TRY(dalloc_t(ctx, &b->touch_cnt, ngg * nbk));
+    k_touch<<<grid_for(ng), TPB, 0, st>>>(gstart, ng, pa1, pb1, cell, D, b->blk_shift, bkey, bstart,
+                                           bcnt, nblocks, b->touch_start, b->touch_cnt, gcol, gkey);
+
+    // greedy sub-colours, in batches of groups to bound the bitmask scratch
+    int32_t *sub0 = tmp.get<int32_t>(mm), *nsub = tmp.get<int32_t>(ngg + 1);
+    uint32_t *ab0 = tmp.get<uint32_t>(mm);
+    NEED(sub0); NEED(nsub); NEED(ab0);
+    long long per_group = (long long)nbk * b->mb * 4;   // 64-bit words
+    long long batch = std::max(1LL, std::min(ng, (1LL << 25) / std::max(per_group, 1LL)));
+    unsigned long long *used = tmp.get<unsigned long long>(batch * per_group + 1);
+    NEED(used);
+    for (long long gs = 0; gs < ng; gs += batch) {
+        long long ge = std::min(ng, gs + batch);
+        MTS_CUDA(cudaMemsetAsync(used, 0, (ge - gs) * per_group * sizeof(unsigned long long), st));
+        k_greedy<<<grid_for(ge - gs, 64), 64, 0, st>>>(gstart, gs, ge, ng, m, pa1, pb1, cell, D,
+                                                         b->blk_shift, b->touch_start, b->mb, used,
+                                                         sub0, ab0, nsub, b->ctrl);
+    }
+
+    // final canonical order: (group, sub-colour), stable
+    unsigned long long *k2 = tmp.get<unsigned long long>(mm), *k2s = tmp.get<unsigned long long>(mm);
+    NEED(k2); NEED(k2s);
+    k_group_of_pair<<<grid_for(m), TPB, 0, st>>>(gscan, m, sub0, k2);
+    k_iota<<<grid_for(m), TPB, 0, st>>>(ord, m);
+    int gbits = 1;
+    while ((1LL << gbits) <= ng) ++gbits;
+    MTS_TRY(cub_sort_pairs(tmp, k2, k2s, ord, ord1, m, std::min(64, gbits + 8), st));
+    MTS_TRY(dalloc_t(ctx, &b->pair_a, mm));
+    MTS_TRY(dalloc_t(ctx, &b->pair_b, mm));
+    MTS_TRY(dalloc_t(ctx, &b->pair_sub, mm));
+    MTS_TRY(dalloc_t(ctx, &b->pair_col, mm));
+    MTS_TRY(dalloc_t(ctx, &b->pair_key, mm));
+    MTS_TRY(dalloc_t(ctx, &b->pair_ab, mm));
+    MTS_TRY(dalloc_into(ctx, &b->pair_g, mm * sizeof(R) + 16));
+    k_gather<<<grid_for(m), TPB, 0, st>>>(pa1, ord1, m, b->pair_a);
+    k_gather<<<grid_for(m), TPB, 0, st>>>(pb1, ord1, m, b->pair_b);
+    k_gather<<<grid_for(m), TPB, 0, st>>>(sub0, ord1, m, b->pair_sub);
+    k_gather<<<grid_for(m), TPB, 0, st>>>(ab0, ord1, m, b->pair_ab);
+    // per-pair colour and owner key from the group of each final pair
+    {
+        long long *gid = tmp.get<long long>(mm), *g0i = tmp.get<long long>(mm);
+        NEED(gid); NEED(g0i);
+        k_gather<<<grid_for(m), TPB, 0, st>>>(gscan, ord1, m, gid);   // 1-based group ids
+        k_minus_one<<<grid_for(m), TPB, 0, st>>>(gid, m, g0i);
+        k_gather<<<grid_for(m), TPB, 0, st>>>(gcol, g0i, m, b->pair_col);
+        k_gather<<<grid_for(m), TPB, 0, st>>>(gkey, g0i, m, b->pair_key);
+    }
+
+    // levels
+    MTS_TRY(dalloc_t(ctx, &b->grp_lvl, ngg + 1));
+    MTS_CUDA(cudaMemsetAsync(nsub + ng, 0, sizeof(int32_t), st));
+    MTS_TRY(cub_excl_sum(tmp, nsub, b->grp_lvl, ng + 1, st));
+    int nlev = 0;
+    MTS_TRY(to_host(&nlev, b->grp_lvl + ng, 1, st));
+    b->n_levels = nlev;
+    MTS_TRY(dalloc_t(ctx, &b->lvl_pair, (long long)nlev + 1));
+    k_levels<<<grid_for(m + 1), TPB, 0, st>>>(k2s, m, b->grp_lvl, b->lvl_pair, nlev);
+    k_pair_coef<R, D><<<grid_for(m), TPB, 0, st>>>(b->pair_a, b->pair_b, m, b->X64, b->h, alpha,
+                                                    b->V, (R *)b->pair_g);
+    int *dcol = tmp.get<int>(16);
+    NEED(dcol);
+    k_col_off<<<grid_for(ng + 1), TPB, 0, st>>>(gcol, ng, nbk, dcol);
+    MTS_TRY(to_host(b->col_off, dcol, nbk + 1, st));
+
+    // -- setup errors
+    unsigned err = 0;
+    MTS_TRY(to_host(&err, &b->ctrl->err, 1, st));
+    if (err & kErrSingular) {
+        set_error("singular correction-matrix sum (a particle without enough neighbours)");
+        return MTS_ERR_SINGULAR_B;
+    }
+    if (err & kErrTooMany) {
+        set_error("damping sub-colouring needs more than 256 colours");
+        return MTS_ERR_STATE;
+    }
+    MTS_CUDA(cudaStreamSynchronize(st));
+    return MTS_OK;
+}
+
+}  // namespace
+
+double kernel_alpha(int dim, double h) {
+    if (dim == 2) return 7.0 / (4.0 * M_PI * h * h);
+    return 21.0 / (16.0 * M_PI * h * h * h);
+}
+
+mts_status build_body(mts_body *b, const double *hX) {
+    if (b->precision == MTS_FP64)
+        return b->dim == 2 ? build_typed<double, 2>(b, hX) : build_typed<double, 3>(b, hX);
+    return b->dim == 2 ? build_typed<float, 2>(b, hX) : build_typed<float, 3>(b, hX);
+}
+
+}  // namespace mts

@@ -1,0 +1,306 @@
+"""Thin Python binding of libmtssph.so (include/mtssph.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Device memory comes from PyTorch's caching allocator through the library's
+allocator hook, and the library's work is ordered on a PyTorch CUDA stream.
+The names follow the C calls (mts_body_create -> Body(...),
+mts_advance_slow_step -> Body.advance_slow_step, ...).  There is no CPU
+fallback: without the built library or without a CUDA device every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+OK = 0
+ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_SINGULAR_B, ERR_NONFINITE, ERR_TIMEOUT, \
+    ERR_UNSTABLE_DT, ERR_STATE = range(1, 9)
+FP64, MIXED = 0, 1
+ELASTIC_SVK, NEOHOOKE_J2 = 0, 1
+F_U, F_X, F_V, F_DEFGRAD, F_PB, F_C, F_ALPHA, F_CPINV, F_ACC = range(9)
+
+_lib = None
+
+
+class MtsError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where} failed (status {status}): {msg}")
+        self.status = status
+
+
+class Allocator(C.Structure):
+    ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+    RELEASE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+    _fields_ = [("alloc", ALLOC), ("release", RELEASE), ("user", C.c_void_p)]
+
+
+class BodyDesc(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("precision", C.c_int32), ("n", C.c_int64),
+                ("X", C.c_void_p), ("dx", C.c_double), ("h_over_dx", C.c_double)]
+
+
+class StepParams(C.Structure):
+    _fields_ = [("dt_slow", C.c_double), ("ramp_value", C.c_double),
+                ("dt_sub_override", C.c_double), ("ke_tol", C.c_double),
+                ("ke_ref", C.c_double), ("max_substeps", C.c_int64),
+                ("ke_mode", C.c_int32), ("check_every", C.c_int32),
+                ("force_dt", C.c_int32), ("reserved", C.c_int32)]
+
+
+class StepReport(C.Structure):
+    _fields_ = [("substeps", C.c_int64), ("converged", C.c_int32), ("status", C.c_int32),
+                ("ke_final", C.c_double), ("max_v", C.c_double), ("max_a", C.c_double),
+                ("dt_last", C.c_double), ("end_force", C.c_double * 3),
+                ("tip_deflection", C.c_double * 3), ("kernel_launches", C.c_int64),
+                ("prof_count", C.c_int64), ("prof_ms", C.c_double)]
+
+
+def header_functions() -> list:
+    """Names of every function declared in include/mtssph.h."""
+    text = open(_build.HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mts_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """Load (building first if stale) libmtssph.so and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    L = C.CDLL(path)
+    vp, d, i32, i64 = C.c_void_p, C.c_double, C.c_int32, C.c_int64
+    sig = {
+        "mts_ctx_create": [C.c_int, vp, C.POINTER(Allocator), C.POINTER(vp)],
+        "mts_ctx_destroy": [vp],
+        "mts_last_error": [],
+        "mts_version": [],
+        "mts_body_create": [vp, C.POINTER(BodyDesc), C.POINTER(vp)],
+        "mts_body_destroy": [vp],
+        "mts_body_permutation": [vp, vp],
+        "mts_body_neighbors": [vp, C.POINTER(i64), vp, vp],
+        "mts_body_colouring": [vp, C.POINTER(i64), vp, vp, vp, vp, vp],
+        "mts_set_material": [vp, C.c_int, d, d, d, d, d, d, d],
+        "mts_set_damping": [vp, d],
+        "mts_set_diffusion": [vp, d, d, d],
+        "mts_set_bc_displacement": [vp, i64, vp, C.c_uint32, vp, i32],
+        "mts_set_bc_concentration": [vp, i64, vp, d],
+        "mts_set_tip": [vp, i64, vp],
+        "mts_diffusion_dt": [vp, C.POINTER(d), C.POINTER(d)],
+        "mts_advance_slow_step": [vp, C.POINTER(StepParams), C.POINTER(StepReport)],
+        "mts_substep_partial": [vp, d, d, i32],
+        "mts_set_profiling": [vp, i32],
+        "mts_read_field": [vp, i32, vp, i64],
+        "mts_write_field": [vp, i32, vp, i64],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.mts_ctx_destroy.restype = None
+    L.mts_body_destroy.restype = None
+    L.mts_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(st: int, where: str):
+    if st != OK:
+        raise MtsError(st, where, lib().mts_last_error().decode(errors="replace"))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Context:
+    """mts_ctx on one CUDA device with a PyTorch stream and allocator."""
+
+    def __init__(self, device: int = 0, torch_allocator: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("mtssph needs a CUDA device; there is no CPU fallback")
+        self.device = device
+        self._torch = torch
+        self.stream = torch.cuda.Stream(device=device)
+        alloc_p = None
+        if torch_allocator:
+            stream = self.stream
+
+            def _alloc(nbytes, user):
+                try:
+                    with torch.cuda.device(device):
+                        return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream)
+                except Exception:
+                    return None
+
+            def _release(ptr, nbytes, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cb = (Allocator.ALLOC(_alloc), Allocator.RELEASE(_release))
+            self._alloc = Allocator(self._cb[0], self._cb[1], None)
+            alloc_p = C.byref(self._alloc)
+        h = C.c_void_p()
+        _check(lib().mts_ctx_create(device, C.c_void_p(self.stream.cuda_stream), alloc_p,
+                                    C.byref(h)), "mts_ctx_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mts_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Body:
+    """mts_body: a particle body with its fixed neighbourhood on the GPU."""
+
+    def __init__(self, ctx: Context, X: np.ndarray, dx: float, h_over_dx: float = 1.3,
+                 precision: int = FP64):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        self.n, self.dim = X.shape
+        self.ctx = ctx
+        self.precision = precision
+        desc = BodyDesc(self.dim, precision, self.n, X.ctypes.data, dx, h_over_dx)
+        h = C.c_void_p()
+        _check(lib().mts_body_create(ctx.handle, C.byref(desc), C.byref(h)), "mts_body_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mts_body_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- setup products
+    def permutation(self) -> np.ndarray:
+        p = np.zeros(self.n, np.int64)
+        _check(lib().mts_body_permutation(self._h, _ptr(p)), "mts_body_permutation")
+        return p
+
+    def neighbors(self):
+        nnz = C.c_int64()
+        _check(lib().mts_body_neighbors(self._h, C.byref(nnz), None, None), "mts_body_neighbors")
+        off = np.zeros(self.n + 1, np.int64)
+        idx = np.zeros(max(nnz.value, 1), np.int32)
+        _check(lib().mts_body_neighbors(self._h, C.byref(nnz), _ptr(off), _ptr(idx)),
+               "mts_body_neighbors")
+        return off, idx[:nnz.value]
+
+    def colouring(self):
+        m = C.c_int64()
+        _check(lib().mts_body_colouring(self._h, C.byref(m), None, None, None, None, None),
+               "mts_body_colouring")
+        k = max(m.value, 1)
+        pa, pb, col, sub = (np.zeros(k, np.int32) for _ in range(4))
+        key = np.zeros(k, np.int64)
+        _check(lib().mts_body_colouring(self._h, C.byref(m), _ptr(pa), _ptr(pb), _ptr(col),
+                                        _ptr(key), _ptr(sub)), "mts_body_colouring")
+        mm = m.value
+        return pa[:mm], pb[:mm], col[:mm], key[:mm], sub[:mm]
+
+    # -- configuration
+    def set_material(self, model: int, rho0: float, E: float, nu: float, sigma0: float = 0.0,
+                     sigma_inf: float = 0.0, delta: float = 0.0, H: float = 0.0):
+        _check(lib().mts_set_material(self._h, model, rho0, E, nu, sigma0, sigma_inf, delta, H),
+               "mts_set_material")
+
+    def set_damping(self, eta: float):
+        _check(lib().mts_set_damping(self._h, eta), "mts_set_damping")
+
+    def set_diffusion(self, D: float, beta: float, c0: float):
+        _check(lib().mts_set_diffusion(self._h, D, beta, c0), "mts_set_diffusion")
+
+    def set_bc_displacement(self, ids, axis_mask: int, u_unit=None, report_force: bool = False):
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        uu = None if u_unit is None else np.ascontiguousarray(u_unit, dtype=np.float64)
+        _check(lib().mts_set_bc_displacement(self._h, ids.size, _ptr(ids), axis_mask,
+                                             None if uu is None else _ptr(uu), int(report_force)),
+               "mts_set_bc_displacement")
+
+    def set_bc_concentration(self, ids, value: float):
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        _check(lib().mts_set_bc_concentration(self._h, ids.size, _ptr(ids), value),
+               "mts_set_bc_concentration")
+
+    def set_tip(self, ids):
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        _check(lib().mts_set_tip(self._h, ids.size, _ptr(ids)), "mts_set_tip")
+
+    def diffusion_dt(self):
+        a, b = C.c_double(), C.c_double()
+        _check(lib().mts_diffusion_dt(self._h, C.byref(a), C.byref(b)), "mts_diffusion_dt")
+        return a.value, b.value
+
+    # -- stepping
+    def advance_slow_step(self, dt_slow: float = 0.0, ramp: float = 0.0, ke_tol: float = -1.0,
+                          ke_ref: float = 1.0, ke_mode: int = 0, max_substeps: int = 1,
+                          dt_sub: float = 0.0, check_every: int = 32,
+                          force_dt: bool = False) -> StepReport:
+        p = StepParams(dt_slow, ramp, dt_sub, ke_tol, ke_ref, max_substeps, ke_mode,
+                       check_every, int(force_dt), 0)
+        r = StepReport()
+        _check(lib().mts_advance_slow_step(self._h, C.byref(p), C.byref(r)),
+               "mts_advance_slow_step")
+        return r
+
+    def set_profiling(self, stage: int):
+        _check(lib().mts_set_profiling(self._h, stage), "mts_set_profiling")
+
+    def substep_partial(self, dt: float, upto: int, ramp: float = 0.0):
+        _check(lib().mts_substep_partial(self._h, dt, ramp, upto), "mts_substep_partial")
+
+    # -- fields
+    def _width(self, field: int) -> int:
+        return {F_U: self.dim, F_X: self.dim, F_V: self.dim, F_ACC: self.dim, F_DEFGRAD: 9,
+                F_PB: self.dim * self.dim, F_C: 1, F_ALPHA: 1, F_CPINV: 6}[field]
+
+    def read(self, field: int) -> np.ndarray:
+        w = self._width(field)
+        out = np.zeros(self.n * w)
+        _check(lib().mts_read_field(self._h, field, _ptr(out), out.size), "mts_read_field")
+        return out.reshape(self.n, w) if w > 1 else out
+
+    def write(self, field: int, values):
+        w = self._width(field)
+        a = np.ascontiguousarray(values, dtype=np.float64).reshape(self.n * w)
+        _check(lib().mts_write_field(self._h, field, _ptr(a), a.size), "mts_write_field")
+
+
+def body_from_case(ctx: Context, case, precision: int = FP64) -> Body:
+    """Body with the material, damping, diffusion and BCs of a synth Case."""
+    b = Body(ctx, case.X, case.dx, case.h_over_dx, precision)
+    m = case.material
+    b.set_material(ELASTIC_SVK if m.model == "svk" else NEOHOOKE_J2, m.rho0, m.E, m.nu,
+                   m.sigma0, m.sigma_inf, m.delta, m.H)
+    b.set_damping(case.eta)
+    for bc in case.disp_bcs:
+        b.set_bc_displacement(bc.ids, bc.axis_mask, bc.u_unit, bc.report_force)
+    if case.diffusion is not None:
+        b.set_diffusion(*case.diffusion)
+    for cb in case.conc_bcs:
+        b.set_bc_concentration(cb.ids, cb.value)
+    if case.tip_ids is not None and len(case.tip_ids):
+        b.set_tip(case.tip_ids)
+    return b

@@ -1,0 +1,273 @@
+"""GPU (CUDA library, through the C ABI) versus the FP64 CPU oracle.
+
+Tolerances (normwise: max |gpu - oracle| / max |oracle| per field):
+  * setup products (Morton order, CSR, damping colouring): bit-exact;
+  * FP64 single substep, every stage: <= 1e-12;
+  * FP64 multi-substep slow steps at equal substep counts: <= 1e-9;
+  * mixed precision (FP32 per-particle arithmetic, FP64 displacement and
+    reductions): displacement <= 1e-4, concentration <= 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2309_04010_gb300 import mtssph as M
+from synth import bodies as B
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return M.Context(0)
+
+
+def rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    den = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (den if den > 0 else 1.0))
+
+
+def small_cylinder(**kw):
+    return B.cylinder3d(L=5e-3, R=1.25e-3, dx=0.25e-3, n_slow=20, **kw)
+
+
+def small_strip(nx=120, ny=20):
+    c = B.strip2d(nx=nx, ny=ny)
+    c.eta = 1.0
+    return c
+
+
+def pair(ctx, case, precision=M.FP64):
+    return O.body_from_case(case), M.body_from_case(ctx, case, precision)
+
+
+CASES = {
+    "bar2d": lambda: B.bar2d(),
+    "cyl3d": small_cylinder,
+    "strip2d": small_strip,
+    "box3d_irregular": lambda: _irregular3d(),
+}
+
+
+def _irregular3d():
+    X, idx, _ = B.box_body((9, 8, 7), 1e-4, seed=77, jitter=0.3)
+    c = B.bar2d(nx=10, ny=4)
+    c.dim, c.X, c.dx = 3, X, 1e-4
+    c.disp_bcs = [B.DispBC(B.layer_ids(idx, 0, 0, 2), 0b111, np.zeros((int((idx[:, 0] < 2).sum()), 3)))]
+    c.tip_ids = B.layer_ids(idx, 0, 8, 1)
+    return c
+
+
+# ---------------------------------------------------------------- setup
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("precision", [M.FP64, M.MIXED])
+def test_setup_products_bit_exact(ctx, name, precision):
+    case = CASES[name]()
+    ob = O.OracleBody(case.X, case.dx, case.h_over_dx)
+    gb = M.Body(ctx, case.X, case.dx, case.h_over_dx, precision)
+    assert np.array_equal(gb.permutation(), ob.perm())
+    go, gi = gb.neighbors()
+    oo, oi = ob.neighbors()
+    assert np.array_equal(go, oo) and np.array_equal(gi, oi)
+    for g, o in zip(gb.colouring(), ob.colouring()):
+        assert np.array_equal(g, o)
+
+
+def test_setup_rejects_bad_bodies(ctx):
+    with pytest.raises(M.MtsError) as e:
+        M.Body(ctx, np.array([[0.0, 0.0], [1.0, 0.0]]), 1.0)
+    assert e.value.status == M.ERR_SINGULAR_B
+    X = np.zeros((10, 2))
+    X[:, 0] = np.arange(10)
+    X[3, 1] = np.nan
+    with pytest.raises(M.MtsError) as e:
+        M.Body(ctx, X, 1.0)
+    assert e.value.status == M.ERR_INVALID_ARG
+    with pytest.raises(M.MtsError) as e:
+        M.Body(ctx, np.zeros((1, 3)), 1.0)
+    assert e.value.status == M.ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------- one substep
+def _state(case, seed, ustrain):
+    n, d = case.X.shape
+    U = B.random_field(n, d, ustrain * case.dx, seed)
+    V = B.random_field(n, d, 0.05, seed + 1)
+    return U, V
+
+
+@pytest.mark.parametrize("name,ustrain", [("bar2d", 1e-3), ("cyl3d", 2e-2), ("strip2d", 1e-3),
+                                          ("box3d_irregular", 1e-3)])
+def test_fp64_single_substep_every_stage(ctx, name, ustrain):
+    case = CASES[name]()
+    U, V = _state(case, 5, ustrain)
+    dt = 0.6 * case.h_over_dx * case.dx / math.sqrt(
+        case.material.E / (3 * (1 - 2 * case.material.nu)) / case.material.rho0)
+    rng = np.random.default_rng(3)
+    C0 = rng.uniform(0, 1, case.n) if case.diffusion else None
+    for upto in (1, 2, 3, 4):
+        ob, gb = pair(ctx, case)
+        for b in (ob, gb):
+            b.write(M.F_U, U)
+            b.write(M.F_V, V)
+            if C0 is not None:
+                b.write(M.F_C, C0)
+        ob.substep_partial(dt, upto, ramp=0.5)
+        gb.substep_partial(dt, upto, ramp=0.5)
+        assert rel(gb.read(M.F_PB), ob.read(O.F_PB)) < 1e-12
+        if case.material.model == "j2":
+            assert rel(gb.read(M.F_ALPHA), ob.read(O.F_ALPHA)) < 1e-12
+            assert ob.read(O.F_ALPHA).max() > 0      # the state is plastic somewhere
+            assert rel(gb.read(M.F_CPINV), ob.read(O.F_CPINV)) < 1e-12
+        if upto >= 2:
+            assert rel(gb.read(M.F_ACC), ob.read(O.F_ACC)) < 1e-12
+        assert rel(gb.read(M.F_V), ob.read(O.F_V)) < 1e-12
+        assert rel(gb.read(M.F_U), ob.read(O.F_U)) < 1e-12
+        assert rel(gb.read(M.F_DEFGRAD), ob.read(O.F_DEFGRAD)) < 1e-12
+
+
+def test_affine_field_exact_F(ctx):
+    for case in (B.bar2d(nx=20, ny=9), small_cylinder()):
+        d = case.X.shape[1]
+        G = np.random.default_rng(1).uniform(-0.05, 0.05, (d, d))
+        want = np.eye(3)
+        want[:d, :d] += G
+        for prec, tol in ((M.FP64, 1e-13), (M.MIXED, 2e-6)):
+            gb = M.Body(ctx, case.X, case.dx, case.h_over_dx, prec)
+            gb.write(M.F_U, case.X @ G.T)
+            F = gb.read(M.F_DEFGRAD).reshape(-1, 3, 3)
+            assert np.max(np.abs(F - want)) < tol
+
+
+# ---------------------------------------------------------------- slow steps
+def _run_both(ctx, case, nslow, nsub, precision=M.FP64, ke_tol=-1.0, dt_slow=0.0):
+    ob, gb = pair(ctx, case, precision)
+    reps = []
+    for l in range(1, nslow + 1):
+        ramp = l / max(case.plan.n_ramp, 1)
+        rg = gb.advance_slow_step(dt_slow=dt_slow, ramp=ramp, ke_tol=ke_tol, ke_ref=case.plan.ke_ref,
+                                  ke_mode=case.plan.ke_mode, max_substeps=nsub, check_every=16)
+        ro = ob.advance(dt_slow=dt_slow, ramp=ramp, ke_tol=-1.0, ke_ref=case.plan.ke_ref,
+                        ke_mode=case.plan.ke_mode, max_substeps=rg.substeps)
+        reps.append((rg, ro))
+    return ob, gb, reps
+
+
+def test_fp64_slow_steps_bar2d(ctx):
+    ob, gb, reps = _run_both(ctx, B.bar2d(), 3, 300)
+    assert rel(gb.read(M.F_U), ob.read(O.F_U)) < 1e-9
+    assert rel(gb.read(M.F_V), ob.read(O.F_V)) < 1e-9
+    for rg, ro in reps:
+        assert rg.substeps == ro.substeps == 300
+        assert abs(rg.ke_final - ro.ke_final) < 1e-9 * ro.ke_final
+        assert abs(rg.end_force[0] - ro.end_force[0]) < 1e-9 * abs(ro.end_force[0])
+        assert abs(rg.tip_deflection[0] - ro.tip_deflection[0]) < 1e-9 * abs(ro.tip_deflection[0])
+        assert abs(rg.dt_last - ro.dt_last) < 1e-12 * ro.dt_last
+
+
+def test_fp64_slow_steps_j2_cylinder(ctx):
+    case = small_cylinder()
+    ob, gb, reps = _run_both(ctx, case, 4, 150)
+    assert ob.read(O.F_ALPHA).max() > 0
+    assert rel(gb.read(M.F_U), ob.read(O.F_U)) < 1e-9
+    assert rel(gb.read(M.F_ALPHA), ob.read(O.F_ALPHA)) < 1e-9
+
+
+def test_kinetic_energy_stop_matches_oracle(ctx):
+    case = B.bar2d(nx=40, ny=10)
+    ob, gb = pair(ctx, case)
+    for l in (1, 2):
+        rg = gb.advance_slow_step(ramp=l / 20, ke_tol=1e-4, ke_ref=case.plan.ke_ref,
+                                  max_substeps=100000, check_every=64)
+        ro = ob.advance(ramp=l / 20, ke_tol=1e-4, ke_ref=case.plan.ke_ref, max_substeps=100000)
+        assert rg.converged == ro.converged == 1
+        assert rg.substeps == ro.substeps
+        assert rg.ke_final <= 1e-4 * case.plan.ke_ref
+    assert rel(gb.read(M.F_U), ob.read(O.F_U)) < 1e-9
+
+
+def test_diffusion_and_swelling_fp64(ctx):
+    case = small_strip()
+    ob, gb = pair(ctx, case)
+    dtp_o, dts_o = ob.diffusion_dt()
+    dtp_g, dts_g = gb.diffusion_dt()
+    assert abs(dtp_g - dtp_o) < 1e-14 * dtp_o and abs(dts_g - dts_o) < 1e-12 * dts_o
+    for _ in range(3):
+        rg = gb.advance_slow_step(dt_slow=dts_o, ke_tol=-1, max_substeps=50, check_every=16)
+        ob.advance(dt_slow=dts_o, ke_tol=-1, max_substeps=rg.substeps)
+    assert rel(gb.read(M.F_C), ob.read(O.F_C)) < 1e-12
+    assert rel(gb.read(M.F_U), ob.read(O.F_U)) < 1e-9
+    with pytest.raises(M.MtsError) as e:
+        gb.advance_slow_step(dt_slow=1.5 * dts_g, max_substeps=1)
+    assert e.value.status == M.ERR_UNSTABLE_DT
+
+
+# ---------------------------------------------------------------- mixed precision
+def test_mixed_precision_bar2d_displacement(ctx):
+    case = B.bar2d()
+    ob, gb, reps = _run_both(ctx, case, 2, 2000, precision=M.MIXED)
+    e = rel(gb.read(M.F_U), ob.read(O.F_U))
+    assert e < 1e-4, e
+
+
+def test_mixed_precision_concentration(ctx):
+    case = small_strip()
+    ob, gb = pair(ctx, case, M.MIXED)
+    _, dts = ob.diffusion_dt()
+    for _ in range(20):
+        rg = gb.advance_slow_step(dt_slow=dts, ke_tol=-1, max_substeps=5, check_every=8)
+        ob.advance(dt_slow=dts, ke_tol=-1, max_substeps=rg.substeps)
+    assert rel(gb.read(M.F_C), ob.read(O.F_C)) < 1e-5
+
+
+def test_mixed_precision_j2_cylinder(ctx):
+    case = small_cylinder()
+    ob, gb, reps = _run_both(ctx, case, 3, 300, precision=M.MIXED)
+    assert rel(gb.read(M.F_U), ob.read(O.F_U)) < 1e-4
+
+
+# ---------------------------------------------------------------- full size
+@pytest.mark.parametrize("precision,tol", [(M.FP64, 1e-12), (M.MIXED, 1e-4)])
+def test_full_size_cylinder_first_substeps(ctx, precision, tol):
+    """The benchmark workload (3D J2 cylinder, 252,800 particles) at full size:
+    setup products bit-exact, then two substeps after the first load jump."""
+    case = B.cylinder3d()
+    ob, gb = pair(ctx, case, precision)
+    off_g, idx_g = gb.neighbors()
+    off_o, idx_o = ob.neighbors()
+    assert np.array_equal(off_g, off_o) and np.array_equal(idx_g, idx_o)
+    for g, o in zip(gb.colouring(), ob.colouring()):
+        assert np.array_equal(g, o)
+    ramp = 1.0 / case.plan.n_ramp
+    rg = gb.advance_slow_step(ramp=ramp, ke_tol=-1, max_substeps=2, check_every=2)
+    ro = ob.advance(ramp=ramp, ke_tol=-1, max_substeps=2)
+    assert rel(gb.read(M.F_U), ob.read(O.F_U)) < tol
+    assert rel(gb.read(M.F_V), ob.read(O.F_V)) < max(tol, 1e-12) * (1 if precision == M.FP64 else 10)
+    assert abs(rg.ke_final - ro.ke_final) < (1e-12 if precision == M.FP64 else 1e-3) * ro.ke_final
+
+
+# ---------------------------------------------------------------- errors
+def test_api_errors(ctx):
+    case = B.bar2d(nx=20, ny=6)
+    gb = M.Body(ctx, case.X, case.dx)
+    with pytest.raises(M.MtsError) as e:
+        gb.advance_slow_step(max_substeps=1)
+    assert e.value.status == M.ERR_STATE
+    gb.set_material(M.ELASTIC_SVK, 7850, 210e9, 0.3)
+    with pytest.raises(M.MtsError) as e:
+        gb.write(M.F_U, np.full((case.n, 2), np.nan))
+    assert e.value.status == M.ERR_NONFINITE
+    with pytest.raises(M.MtsError) as e:
+        gb.set_bc_displacement([case.n + 5], 1)
+    assert e.value.status == M.ERR_INVALID_ARG
+    with pytest.raises(M.MtsError):
+        gb.advance_slow_step(max_substeps=0)
+    with pytest.raises(M.MtsError) as e:
+        gb.advance_slow_step(dt_slow=1.0, max_substeps=1)
+    assert e.value.status == M.ERR_STATE
+    gb.set_bc_displacement(np.zeros(0, np.int64), 1)      # empty set is fine
+    r = gb.advance_slow_step(max_substeps=1)
+    assert r.substeps == 1 and r.converged == 0
