@@ -65,6 +65,7 @@ typedef struct {
  * cudaStream_t is used and stays owned by the caller. */
 mts_status mts_ctx_create(int device, void *cuda_stream, const mts_allocator *alloc,
                           mts_ctx **out);
+/* Destroy every body of the context first: a body keeps a pointer to it. */
 void mts_ctx_destroy(mts_ctx *ctx);
 /* Message for the last failing call on this thread ("" if none). */
 const char *mts_last_error(void);

@@ -79,8 +79,7 @@ void body_free(mts_body *b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (cudaEvent_t e : b->prof_ev) cudaEventDestroy(e);
     void **ptrs[] = {(void **)&b->perm, (void **)&b->rank, (void **)&b->X64, (void **)&b->nb_off,
-                     (void **)&b->nb_idx, (void **)&b->ell, (void **)&b->slice_off,
-                     (void **)&b->slice_w, (void **)&b->pair_a, (void **)&b->pair_b,
+                     (void **)&b->nb_idx, (void **)&b->pair_a, (void **)&b->pair_b,
                      (void **)&b->pair_col, (void **)&b->pair_sub, (void **)&b->pair_key,
                      (void **)&b->pair_ab, (void **)&b->pair_g, (void **)&b->lvl_pair,
                      (void **)&b->grp_lvl, (void **)&b->touch_start, (void **)&b->touch_cnt,
@@ -88,7 +87,9 @@ void body_free(mts_body *b) {
                      (void **)&b->acc, (void **)&b->PB, (void **)&b->cp, (void **)&b->c,
                      (void **)&b->c_tmp, (void **)&b->c_held, (void **)&b->u, (void **)&b->u_unit,
                      (void **)&b->flags, (void **)&b->ctrl, (void **)&b->part_force,
-                     (void **)&b->part_drift, (void **)&b->scratch};
+                     (void **)&b->part_drift, (void **)&b->scratch, (void **)&b->halo_off,
+                     (void **)&b->halo_idx, (void **)&b->lself, (void **)&b->lell,
+                     (void **)&b->lell_off, (void **)&b->tile_w};
     for (void **pp : ptrs) {
         dfree(b->ctx, *pp);
         *pp = nullptr;

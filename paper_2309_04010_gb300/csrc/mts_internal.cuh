@@ -12,8 +12,10 @@
 //   cp   R[8]     C_p^-1 (xx,yy,zz,xy,yz,xz), alpha, pad (J2 only)
 //   c    R        concentration
 //   flags u8      bits 0-2 fixed axes, 3 force set, 4 tip set, 5 c held
-//   ELL  i32      neighbour indices, slices of 32 particles, neighbour-major
-//                 inside a slice, padded with the particle itself
+//   halo i32      per Morton tile of T particles: the sorted union of the tile
+//                 and its neighbours, staged in shared memory by the kernels
+//   lell u16      per tile, neighbour-major local slots into the tile's halo,
+//                 padded with the particle's own slot
 #pragma once
 
 #include <cuda_runtime.h>
@@ -70,10 +72,6 @@ template <class R>
 struct Args {
     long long n;
     int dim;
-    // neighbour ELL
-    const int32_t *ell;
-    const long long *slice_off;
-    const int32_t *slice_w;
     // geometry
     const R *X;
     const R *B0;
@@ -108,6 +106,17 @@ struct Args {
     const int32_t *touch_start;  // group x NB
     const int32_t *touch_cnt;
     int mb;                      // max particles per damping block (local stride)
+    int max_group_pairs;         // largest pair list of one owner group
+    int max_group_levels;
+    // Morton tiles of T particles with their neighbour halo (shared-memory staging)
+    int T;                       // particles per tile = threads per CTA
+    int max_halo;                // largest halo (tile + neighbours)
+    const long long *halo_off;   // tile -> first halo entry, ntiles + 1
+    const int32_t *halo_idx;     // halo particle indices, ascending per tile
+    const uint16_t *lself;       // particle -> its slot in its tile's halo
+    const uint16_t *lell;        // local neighbour slots, neighbour-major per tile
+    const long long *lell_off;   // tile -> first local ELL entry
+    const int32_t *tile_w;       // tile -> ELL width
     // reductions
     Control *ctrl;
     double *part_force;          // grid x 4 (amax, m a_x, m a_y, m a_z)
@@ -147,10 +156,6 @@ struct mts_body {
     long long *nb_off;    // CSR
     int32_t *nb_idx;
     long long nnz;
-    int32_t *ell;
-    long long *slice_off;
-    int32_t *slice_w;
-    long long n_slices;
 
     // canonical damping order
     long long npairs;
@@ -164,6 +169,18 @@ struct mts_body {
     long long n_groups, n_levels;
     int col_off[9];
     int mb;
+    int max_group_pairs, max_group_levels;
+
+    // Morton tiles with neighbour halos
+    int T;
+    long long ntiles;
+    int max_halo;
+    long long *halo_off;
+    int32_t *halo_idx;
+    uint16_t *lself;
+    uint16_t *lell;
+    long long *lell_off;
+    int32_t *tile_w;
 
     // state
     void *X, *B0, *uf, *v, *acc, *PB, *cp, *c, *c_tmp, *c_held;

@@ -7,7 +7,8 @@
 //      with explicit round-to-nearest multiply/add (no fused multiply-add), over
 //      a dense cell grid; rows sorted ascending with a segmented sort.
 //   3. B0_a = (sum_b V (X_b - X_a) (x) grad_a W_ab)^-1 in FP64.
-//   4. Sliced ELL copy of the CSR for the substep kernels.
+//   4. Morton tiles of T particles with their neighbour halos and 16-bit local
+//      neighbour slots (shared-memory staging in the substep kernels).
 //   5. Canonical order of the pairwise damping (Sec. 4.3): pairs owned by the
 //      componentwise-min block (blocks of 2^s cells, 2^s dx > 2h) of their two
 //      particles; block colour = parity bits; greedy sub-colours in ascending
@@ -241,29 +242,6 @@ __global__ void k_b0(const double *X64, const long long *off, const int32_t *idx
         for (int j = 0; j < P; ++j) dst[i * P + j] = j < D ? out[i][j] : R(0);
 }
 
-// ---------------------------------------------------------------- ELL
-__global__ void k_slice_w(const long long *off, long long n, long long nslices, long long *w) {
-    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= nslices) return;
-    long long m = 0;
-    for (long long i = s * 32; i < min(n, s * 32 + 32); ++i) m = max(m, off[i + 1] - off[i]);
-    w[s] = m * 32;
-}
-
-__global__ void k_fill_ell(const long long *off, const int32_t *idx, long long n,
-                           const long long *soff, int32_t *sw, int32_t *ell) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long s = i >> 5;
-    int lane = (int)(i & 31);
-    long long nslices = (n + 31) / 32;
-    if (s >= nslices) return;
-    long long width = (soff[s + 1] - soff[s]) / 32;
-    if (lane == 0) sw[s] = (int32_t)width;
-    long long deg = i < n ? off[i + 1] - off[i] : 0;
-    for (long long j = 0; j < width; ++j)
-        ell[soff[s] + j * 32 + lane] = (int32_t)(j < deg ? idx[off[i] + j] : (i < n ? i : 0));
-}
-
 // ---------------------------------------------------------------- damping order
 __global__ void k_count_pairs(const long long *off, const int32_t *idx, long long n,
                               long long *cnt) {
@@ -465,6 +443,100 @@ __global__ void k_pair_coef(const int32_t *pa, const int32_t *pb, long long m, c
     g[p] = (R)(-2.0 * V * V * dw / r);   // B_ab / eta
 }
 
+// ---------------------------------------------------------------- tiles
+// entries of tile t: its own particles and all their CSR neighbours
+__global__ void k_tile_entries(const long long *off, const int32_t *idx, long long n, int32_t *vals) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    long long dst = off[i] + i;
+    vals[dst] = (int32_t)i;
+    for (long long p = off[i]; p < off[i + 1]; ++p) vals[++dst] = idx[p];
+}
+
+__global__ void k_tile_seg(const long long *off, long long n, int T, long long ntiles,
+                           long long *seg) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    long long i = t * T < n ? t * T : n;
+    seg[t] = off[i] + i;
+}
+
+__global__ void k_uniq_flags(const int32_t *v, long long m, long long *flag) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k < m) flag[k] = (k == 0 || v[k] != v[k - 1]) ? 1 : 0;
+}
+
+__global__ void k_seg_start_flags(const long long *seg, long long ntiles, long long *flag) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < ntiles) flag[seg[t]] = 1;
+}
+
+__global__ void k_halo_compact(const int32_t *v, const long long *flag, const long long *scan,
+                               long long m, int32_t *halo) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k < m && flag[k]) halo[scan[k] - 1] = v[k];
+}
+
+__global__ void k_halo_off(const long long *seg, const long long *scan, long long ntiles,
+                           long long total, long long *hoff, unsigned int *hmax) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    hoff[t] = t == ntiles ? total : scan[seg[t]] - 1;
+    if (t < ntiles) {
+        long long e = t + 1 == ntiles ? total : scan[seg[t + 1]] - 1;
+        atomicMax(hmax, (unsigned int)(e - (scan[seg[t]] - 1)));
+    }
+}
+
+__global__ void k_tile_w(const long long *off, long long n, int T, long long ntiles, long long *w) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    long long m = 0;
+    for (long long i = t * T; i < min(n, (t + 1) * T); ++i) m = max(m, off[i + 1] - off[i]);
+    w[t] = m * T;
+}
+
+__device__ int find_slot(const int32_t *h, long long len, int32_t key) {
+    long long lo = 0, hi = len;
+    while (lo < hi) {
+        long long mid = (lo + hi) >> 1;
+        if (h[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (int)lo;
+}
+
+__global__ void k_local_ell(const long long *off, const int32_t *idx, long long n, int T,
+                            long long ntiles, const long long *hoff, const int32_t *halo,
+                            const long long *loff, int32_t *tw, uint16_t *lell, uint16_t *lself) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long t = i / T;
+    if (t >= ntiles) return;
+    int lane = (int)(i - t * T);
+    long long width = (loff[t + 1] - loff[t]) / T;
+    if (lane == 0) tw[t] = (int32_t)width;
+    const int32_t *h = halo + hoff[t];
+    long long hl = hoff[t + 1] - hoff[t];
+    if (i >= n) {
+        for (long long j = 0; j < width; ++j) lell[loff[t] + j * T + lane] = 0;
+        return;
+    }
+    int self = find_slot(h, hl, (int32_t)i);
+    lself[i] = (uint16_t)self;
+    long long deg = off[i + 1] - off[i];
+    for (long long j = 0; j < width; ++j)
+        lell[loff[t] + j * T + lane] =
+            (uint16_t)(j < deg ? find_slot(h, hl, idx[off[i] + j]) : self);
+}
+
+__global__ void k_group_max(const long long *lvl_pair, const int32_t *grp_lvl, long long ng,
+                            unsigned int *mx) {
+    long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    atomicMax(mx, (unsigned int)(lvl_pair[grp_lvl[g + 1]] - lvl_pair[grp_lvl[g]]));
+    atomicMax(mx + 1, (unsigned int)(grp_lvl[g + 1] - grp_lvl[g]));
+}
+
 __global__ void k_col_off(const int32_t *gcol, long long ng, int ncol, int *col_off) {
     long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (g > ng) return;
@@ -536,6 +608,62 @@ template <class T>
 mts_status to_host(T *h, const T *d, size_t count, cudaStream_t st) {
     MTS_CUDA(cudaMemcpyAsync(h, d, count * sizeof(T), cudaMemcpyDeviceToHost, st));
     MTS_CUDA(cudaStreamSynchronize(st));
+    return MTS_OK;
+}
+
+mts_status build_tiles(mts_body *b, Tmp &tmp, cudaStream_t st, int T) {
+    mts_ctx *ctx = b->ctx;
+    const long long n = b->n;
+    const long long ntiles = (n + T - 1) / T;
+    const long long m = b->nnz + n;
+    int32_t *vals = tmp.get<int32_t>(m), *vs = tmp.get<int32_t>(m);
+    long long *seg = tmp.get<long long>(ntiles + 1);
+    long long *flag = tmp.get<long long>(m), *scan = tmp.get<long long>(m);
+    NEED(vals); NEED(vs); NEED(seg); NEED(flag); NEED(scan);
+    k_tile_entries<<<grid_for(n), TPB, 0, st>>>(b->nb_off, b->nb_idx, n, vals);
+    k_tile_seg<<<grid_for(ntiles + 1), TPB, 0, st>>>(b->nb_off, n, T, ntiles, seg);
+    {
+        size_t bytes = 0;
+        MTS_CUDA(cub::DeviceSegmentedSort::SortKeys(nullptr, bytes, vals, vs, m, ntiles, seg, seg + 1, st));
+        void *t = tmp.get<char>(bytes);
+        NEED(t);
+        MTS_CUDA(cub::DeviceSegmentedSort::SortKeys(t, bytes, vals, vs, m, ntiles, seg, seg + 1, st));
+    }
+    k_uniq_flags<<<grid_for(m), TPB, 0, st>>>(vs, m, flag);
+    k_seg_start_flags<<<grid_for(ntiles), TPB, 0, st>>>(seg, ntiles, flag);
+    MTS_TRY(cub_incl_sum(tmp, flag, scan, m, st));
+    long long total = 0;
+    MTS_TRY(to_host(&total, scan + m - 1, 1, st));
+    MTS_TRY(dalloc_t(ctx, &b->halo_idx, total));
+    MTS_TRY(dalloc_t(ctx, &b->halo_off, ntiles + 1));
+    k_halo_compact<<<grid_for(m), TPB, 0, st>>>(vs, flag, scan, m, b->halo_idx);
+    unsigned int *hmax = tmp.get<unsigned int>(1);
+    NEED(hmax);
+    MTS_CUDA(cudaMemsetAsync(hmax, 0, sizeof(unsigned), st));
+    k_halo_off<<<grid_for(ntiles + 1), TPB, 0, st>>>(seg, scan, ntiles, total, b->halo_off, hmax);
+    unsigned int hm = 0;
+    MTS_TRY(to_host(&hm, hmax, 1, st));
+    if (hm > 65535) {
+        set_error("tile halo of %u particles exceeds the 16-bit local index", hm);
+        return MTS_ERR_INVALID_ARG;
+    }
+    b->max_halo = (int)hm;
+    long long *w = tmp.get<long long>(ntiles + 1);
+    NEED(w);
+    MTS_TRY(dalloc_t(ctx, &b->lell_off, ntiles + 1));
+    MTS_TRY(dalloc_t(ctx, &b->tile_w, ntiles + 1));
+    k_tile_w<<<grid_for(ntiles), TPB, 0, st>>>(b->nb_off, n, T, ntiles, w);
+    MTS_CUDA(cudaMemsetAsync(w + ntiles, 0, sizeof(long long), st));
+    MTS_TRY(cub_excl_sum(tmp, w, b->lell_off, ntiles + 1, st));
+    long long len = 0;
+    MTS_TRY(to_host(&len, b->lell_off + ntiles, 1, st));
+    MTS_TRY(dalloc_t(ctx, &b->lell, std::max(len, 1LL)));
+    MTS_TRY(dalloc_t(ctx, &b->lself, n));
+    k_local_ell<<<grid_for(ntiles * T), TPB, 0, st>>>(b->nb_off, b->nb_idx, n, T, ntiles,
+                                                        b->halo_off, b->halo_idx, b->lell_off,
+                                                        b->tile_w, b->lell, b->lself);
+    b->T = T;
+    b->ntiles = ntiles;
     return MTS_OK;
 }
 
@@ -633,21 +761,6 @@ mts_status build_typed(mts_body *b, const double *hX) {
     MTS_CUDA(cudaMemsetAsync(&b->ctrl->err, 0, sizeof(unsigned), st));
     k_b0<R, D><<<grid_for(n), TPB, 0, st>>>(b->X64, b->nb_off, b->nb_idx, n, b->h, alpha, b->V,
                                              (R *)b->B0, b->ctrl);
-
-    // -- sliced ELL
-    b->n_slices = (n + 31) / 32;
-    long long *sw = tmp.get<long long>(b->n_slices + 1);
-    NEED(sw);
-    MTS_TRY(dalloc_t(ctx, &b->slice_off, b->n_slices + 1));
-    MTS_TRY(dalloc_t(ctx, &b->slice_w, b->n_slices + 1));
-    k_slice_w<<<grid_for(b->n_slices), TPB, 0, st>>>(b->nb_off, n, b->n_slices, sw);
-    MTS_CUDA(cudaMemsetAsync(sw + b->n_slices, 0, sizeof(long long), st));
-    MTS_TRY(cub_excl_sum(tmp, sw, b->slice_off, b->n_slices + 1, st));
-    long long ell_len = 0;
-    MTS_TRY(to_host(&ell_len, b->slice_off + b->n_slices, 1, st));
-    MTS_TRY(dalloc_t(ctx, &b->ell, std::max(ell_len, 1LL)));
-    k_fill_ell<<<grid_for(b->n_slices * 32), TPB, 0, st>>>(b->nb_off, b->nb_idx, n, b->slice_off,
-                                                             b->slice_w, b->ell);
 
     // -- damping order: owned pairs
     long long *pcnt = tmp.get<long long>(n + 1), *poff = tmp.get<long long>(n + 1);
@@ -784,6 +897,20 @@ mts_status build_typed(mts_body *b, const double *hX) {
     NEED(dcol);
     k_col_off<<<grid_for(ng + 1), TPB, 0, st>>>(gcol, ng, nbk, dcol);
     MTS_TRY(to_host(b->col_off, dcol, nbk + 1, st));
+
+    {
+        unsigned int *mx = tmp.get<unsigned int>(2);
+        NEED(mx);
+        MTS_CUDA(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned), st));
+        k_group_max<<<grid_for(ng), TPB, 0, st>>>(b->lvl_pair, b->grp_lvl, ng, mx);
+        unsigned int hm[2];
+        MTS_TRY(to_host(hm, mx, 2, st));
+        b->max_group_pairs = (int)hm[0];
+        b->max_group_levels = (int)hm[1];
+    }
+
+    // -- Morton tiles and their halos (particles + neighbours), local ELL
+    MTS_TRY(build_tiles(b, tmp, st, sizeof(R) == 4 ? 256 : 128));
 
     // -- setup errors
     unsigned err = 0;

@@ -28,35 +28,73 @@ namespace {
 
 inline unsigned grid_of(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
-// --------------------------------------------------------------------- F
-// F_a = I + (sum_b V (u_b - u_a) (x) grad_a W_ab) B0_a, 3x3 with F_zz = 1 in 2D.
+// --------------------------------------------------------------------- tiles
+// A CTA owns one Morton tile of T = blockDim.x consecutive particles.  It
+// stages the reference positions and one more per-particle array of the tile's
+// halo (the tile and all its neighbours) in shared memory, then every
+// neighbour access reads shared memory through a 16-bit local slot.
+template <class R, int P, int NY>
+__device__ __forceinline__ int stage_halo(const Args<R> &A, R *sX, R *sY, const R *Y) {
+    const long long t = blockIdx.x;
+    const long long h0 = A.halo_off[t];
+    const int nh = (int)(A.halo_off[t + 1] - h0);
+    for (int k = threadIdx.x; k < nh; k += blockDim.x) {
+        const long long g = __ldg(A.halo_idx + h0 + k);
+        R x[P];
+        ldg_vec<R, P>(x, A.X + g * P);
+        st_vec<R, P>(sX + k * P, x);
+        if (sY) {
+            if constexpr (NY == 12) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    R y[4];
+                    ldg_vec<R, 4>(y, Y + g * 12 + 4 * r);
+                    st_vec<R, 4>(sY + k * 12 + 4 * r, y);
+                }
+            } else {
+                R y[NY];
+                ldg_vec<R, NY>(y, Y + g * NY);
+                st_vec<R, NY>(sY + k * NY, y);
+            }
+        }
+    }
+    __syncthreads();
+    return nh;
+}
+
+// F_a = I + (sum_b V (u_b - u_a) (x) grad_a W_ab) B0_a, 3x3 with F_zz = 1 in 2D;
+// X and u of the halo are in shared memory.
 template <class R, int D>
-__device__ __forceinline__ void compute_F(const Args<R> &A, long long i, R (&F)[3][3]) {
+__device__ __forceinline__ void compute_F(const Args<R> &A, const R *sX, const R *sU, long long i,
+                                          R (&F)[3][3]) {
     constexpr int P = Pad<D>::v;
+    const long long t = blockIdx.x;
+    const int li = A.lself[i];
     R xa[P], ua[P];
-    ldg_vec<R, P>(xa, A.X + i * P);
-    ldg_vec<R, P>(ua, A.uf + i * P);
+    ld_vec<R, P>(xa, sX + li * P);
+    ld_vec<R, P>(ua, sU + li * P);
     R G[D][D];
 #pragma unroll
     for (int r = 0; r < D; ++r)
 #pragma unroll
         for (int c = 0; c < D; ++c) G[r][c] = R(0);
-    const long long s = i >> 5;
-    const int32_t *row = A.ell + A.slice_off[s] + (i & 31);
-    const int w = A.slice_w[s];
+    const int T = A.T;
+    const uint16_t *row = A.lell + A.lell_off[t] + threadIdx.x;
+    const int w = A.tile_w[t];
+#pragma unroll 4
     for (int j = 0; j < w; ++j) {
-        const int b = __ldg(row + 32 * j);
+        const int l = __ldg(row + j * T);
         R xb[P], ub[P];
-        ldg_vec<R, P>(xb, A.X + (long long)b * P);
-        ldg_vec<R, P>(ub, A.uf + (long long)b * P);
+        ld_vec<R, P>(xb, sX + l * P);
+        ld_vec<R, P>(ub, sU + l * P);
         R d[D], r2 = R(0);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             d[k] = xa[k] - xb[k];
             r2 += d[k] * d[k];
         }
-        const R t = R(1) - R(0.5) * dsqrt(r2) * A.inv_h;
-        const R f = A.kcoef * t * t * t;   // V W'(r)/r
+        const R tt = R(1) - R(0.5) * dsqrt(r2) * A.inv_h;
+        const R f = A.kcoef * tt * tt * tt;   // V W'(r)/r
 #pragma unroll
         for (int r = 0; r < D; ++r) {
             const R du = (ub[r] - ua[r]) * f;
@@ -83,21 +121,26 @@ __device__ __forceinline__ void compute_F(const Args<R> &A, long long i, R (&F)[
 
 // --------------------------------------------------------------------- K_A
 template <class R, int D, int MAT>
-__global__ void __launch_bounds__(kBlock) k_stress(Args<R> A) {
+__global__ void __launch_bounds__(256) k_stress(Args<R> A) {
     if (A.ctrl->done) return;
-    const long long i = blockIdx.x * (long long)kBlock + threadIdx.x;
+    constexpr int P = Pad<D>::v;
+    extern __shared__ __align__(16) unsigned char smem[];
+    R *sX = reinterpret_cast<R *>(smem);
+    R *sU = sX + (size_t)A.max_halo * P;
+    stage_halo<R, P, P>(A, sX, sU, A.uf);
+    const long long i = blockIdx.x * (long long)A.T + threadIdx.x;
     if (i >= A.n) return;
     R F[3][3];
-    compute_F<R, D>(A, i, F);
-    R P[3][3];
+    compute_F<R, D>(A, sX, sU, i, F);
+    R P3[3][3];
     if constexpr (MAT == MTS_ELASTIC_SVK) {
-        stress_svk<R>(F, A.lambda, A.mu, P);
+        stress_svk<R>(F, A.lambda, A.mu, P3);
     } else {
         R cp[8];
         ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(cp), A.cp + i * 8);
         ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(cp + 4), A.cp + i * 8 + 4);
         R c7[7] = {cp[0], cp[1], cp[2], cp[3], cp[4], cp[5], cp[6]};
-        stress_j2<R>(F, c7, A.K, A.mu, A.s0, A.sinf, A.delta, A.Hlin, P);
+        stress_j2<R>(F, c7, A.K, A.mu, A.s0, A.sinf, A.delta, A.Hlin, P3);
         if (c7[6] != cp[6]) {
             R o0[4] = {c7[0], c7[1], c7[2], c7[3]};
             R o1[4] = {c7[4], c7[5], c7[6], R(0)};
@@ -105,7 +148,7 @@ __global__ void __launch_bounds__(kBlock) k_stress(Args<R> A) {
             st_vec<R, 4>(A.cp + i * 8 + 4, o1);
         }
     }
-    if (A.swelling) add_swelling<R>(F, A.swell * (A.c[i] - A.c0), P);
+    if (A.swelling) add_swelling<R>(F, A.swell * (A.c[i] - A.c0), P3);
     R B[D][D];
     ldg_mat<R, D>(B, A.B0 + i * MatS<D>::v);
     R PB[D][D];
@@ -115,7 +158,7 @@ __global__ void __launch_bounds__(kBlock) k_stress(Args<R> A) {
         for (int c = 0; c < D; ++c) {
             R acc = R(0);
 #pragma unroll
-            for (int k = 0; k < D; ++k) acc += P[r][k] * B[k][c];
+            for (int k = 0; k < D; ++k) acc += P3[r][k] * B[k][c];
             PB[r][c] = acc;
         }
     st_mat<R, D>(A.PB + i * MatS<D>::v, PB);
@@ -123,42 +166,66 @@ __global__ void __launch_bounds__(kBlock) k_stress(Args<R> A) {
 
 // --------------------------------------------------------------------- K_B
 template <class R, int D>
-__global__ void __launch_bounds__(kBlock) k_force(Args<R> A) {
+__global__ void __launch_bounds__(256) k_force(Args<R> A) {
     if (A.ctrl->done) return;
     constexpr int P = Pad<D>::v;
-    const long long i = blockIdx.x * (long long)kBlock + threadIdx.x;
+    constexpr int MS = MatS<D>::v;
+    extern __shared__ __align__(16) unsigned char smem[];
+    R *sX = reinterpret_cast<R *>(smem);
+    R *sP = sX + (size_t)A.max_halo * P;
+    stage_halo<R, P, MS>(A, sX, sP, A.PB);
+    const long long t = blockIdx.x;
+    const long long i = t * A.T + threadIdx.x;
     double amax = 0.0, fm[3] = {0.0, 0.0, 0.0};
     if (i < A.n) {
+        const int li = A.lself[i];
         R xa[P];
-        ldg_vec<R, P>(xa, A.X + i * P);
+        ld_vec<R, P>(xa, sX + li * P);
         R Pa[D][D];
-        ldg_mat<R, D>(Pa, A.PB + i * MatS<D>::v);
+        if constexpr (D == 2) {
+            R q[4];
+            ld_vec<R, 4>(q, sP + li * 4);
+            Pa[0][0] = q[0]; Pa[0][1] = q[1]; Pa[1][0] = q[2]; Pa[1][1] = q[3];
+        } else {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                R q[4];
+                ld_vec<R, 4>(q, sP + li * 12 + 4 * r);
+                Pa[r][0] = q[0]; Pa[r][1] = q[1]; Pa[r][2] = q[2];
+            }
+        }
         R acc[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) acc[k] = R(0);
-        const long long s = i >> 5;
-        const int32_t *row = A.ell + A.slice_off[s] + (i & 31);
-        const int w = A.slice_w[s];
+        const int T = A.T;
+        const uint16_t *row = A.lell + A.lell_off[t] + threadIdx.x;
+        const int w = A.tile_w[t];
+#pragma unroll 4
         for (int j = 0; j < w; ++j) {
-            const int b = __ldg(row + 32 * j);
+            const int l = __ldg(row + j * T);
             R xb[P];
-            ldg_vec<R, P>(xb, A.X + (long long)b * P);
-            R Pb[D][D];
-            ldg_mat<R, D>(Pb, A.PB + (long long)b * MatS<D>::v);
+            ld_vec<R, P>(xb, sX + l * P);
             R d[D], r2 = R(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 d[k] = xa[k] - xb[k];
                 r2 += d[k] * d[k];
             }
-            const R t = R(1) - R(0.5) * dsqrt(r2) * A.inv_h;
-            const R f = A.kcoef * t * t * t;
+            const R tt = R(1) - R(0.5) * dsqrt(r2) * A.inv_h;
+            const R f = A.kcoef * tt * tt * tt;
+            if constexpr (D == 2) {
+                R q[4];
+                ld_vec<R, 4>(q, sP + l * 4);
+                acc[0] += ((Pa[0][0] + q[0]) * d[0] + (Pa[0][1] + q[1]) * d[1]) * f;
+                acc[1] += ((Pa[1][0] + q[2]) * d[0] + (Pa[1][1] + q[3]) * d[1]) * f;
+            } else {
 #pragma unroll
-            for (int r = 0; r < D; ++r) {
-                R sr = R(0);
-#pragma unroll
-                for (int c = 0; c < D; ++c) sr += (Pa[r][c] + Pb[r][c]) * d[c];
-                acc[r] += sr * f;
+                for (int r = 0; r < 3; ++r) {
+                    R q[4];
+                    ld_vec<R, 4>(q, sP + l * 12 + 4 * r);
+                    acc[r] += ((Pa[r][0] + q[0]) * d[0] + (Pa[r][1] + q[1]) * d[1] +
+                               (Pa[r][2] + q[2]) * d[2]) * f;
+                }
             }
         }
         const uint8_t fx = A.flags[i];
@@ -183,7 +250,7 @@ __global__ void __launch_bounds__(kBlock) k_force(Args<R> A) {
         amax = sqrt(a2);
     }
     // block partials (fixed tree order: deterministic)
-    __shared__ double sh[4][kBlock / 32];
+    __shared__ double sh[4][8];
     amax = warp_max(amax);
     double f0 = warp_sum(fm[0]), f1 = warp_sum(fm[1]), f2 = warp_sum(fm[2]);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -193,7 +260,7 @@ __global__ void __launch_bounds__(kBlock) k_force(Args<R> A) {
     __syncthreads();
     if (threadIdx.x == 0) {
         double m = 0, s0 = 0, s1 = 0, s2 = 0;
-        for (int q = 0; q < kBlock / 32; ++q) {
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
             m = fmax(m, sh[0][q]); s0 += sh[1][q]; s1 += sh[2][q]; s2 += sh[3][q];
         }
         double *o = A.part_force + blockIdx.x * 4;
@@ -202,40 +269,55 @@ __global__ void __launch_bounds__(kBlock) k_force(Args<R> A) {
 }
 
 // --------------------------------------------------------------------- K_C
+// shared-memory layout of one damping warp: velocities of the 2^d touched
+// blocks, the owner group's pair coefficients and packed local indices, its
+// level table, the touched particles' flags
 template <class R, int D>
-__device__ __forceinline__ void damp_pair(const Args<R> &A, long long p, R *sv, const uint8_t *sf,
-                                          R hdt, R im) {
+struct DampSmem {
+    __host__ __device__ static size_t bytes(int mb, int maxp, int maxl) {
+        size_t b = (size_t)(1 << D) * mb * Pad<D>::v * sizeof(R) + (size_t)maxp * sizeof(R) +
+                   (size_t)maxp * 4 + (size_t)(maxl + 1) * 4 + (size_t)(1 << D) * mb;
+        return (b + 15) & ~size_t(15);
+    }
+};
+
+template <class R, int D>
+__device__ __forceinline__ void damp_pair(const R *sg, const uint32_t *sab, int k, R *sv,
+                                          const uint8_t *sf, R hc, R im) {
     constexpr int P = Pad<D>::v;
-    const uint32_t ab = __ldg(A.pair_ab + p);
+    const uint32_t ab = sab[k];
     const int la = (int)(ab & 0xffffu), lb = (int)(ab >> 16);
-    const R c = A.eta * __ldg(A.pair_g + p) * hdt;
+    const R c = hc * sg[k];
     const uint8_t fa = sf[la], fb = sf[lb];
     R *va = sv + la * P, *vb = sv + lb * P;
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-        const R ia = ((fa >> k) & 1) ? R(0) : im;
-        const R ib = ((fb >> k) & 1) ? R(0) : im;
-        const R wn = (va[k] - vb[k]) / (R(1) + c * (ia + ib));
-        va[k] -= c * wn * ia;
-        vb[k] += c * wn * ib;
+    for (int q = 0; q < D; ++q) {
+        const R ia = ((fa >> q) & 1) ? R(0) : im;
+        const R ib = ((fb >> q) & 1) ? R(0) : im;
+        const R wn = (va[q] - vb[q]) / (R(1) + c * (ia + ib));
+        va[q] -= c * wn * ia;
+        vb[q] += c * wn * ib;
     }
 }
 
 template <class R, int D>
-__global__ void __launch_bounds__(kDampWarps * 32) k_damp(Args<R> A, long long g_begin,
-                                                         long long g_end, int mode) {
+__global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long long g_end,
+                                             int mode) {
     if (A.ctrl->done) return;
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int P = Pad<D>::v;
     constexpr int NB = 1 << D;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long g = g_begin + (long long)blockIdx.x * kDampWarps + warp;
+    const long long g = g_begin + (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     if (g >= g_end) return;
     const int mb = A.mb;
-    R *sv = reinterpret_cast<R *>(smem) + (size_t)warp * NB * mb * P;
-    uint8_t *sf = reinterpret_cast<uint8_t *>(reinterpret_cast<R *>(smem) +
-                                              (size_t)kDampWarps * NB * mb * P) +
-                  (size_t)warp * NB * mb;
+    unsigned char *base = smem + (size_t)warp * DampSmem<R, D>::bytes(mb, A.max_group_pairs,
+                                                                         A.max_group_levels);
+    R *sv = reinterpret_cast<R *>(base);
+    R *sg = sv + (size_t)NB * mb * P;
+    uint32_t *sab = reinterpret_cast<uint32_t *>(sg + A.max_group_pairs);
+    int *slv = reinterpret_cast<int *>(sab + A.max_group_pairs);
+    uint8_t *sf = reinterpret_cast<uint8_t *>(slv + A.max_group_levels + 1);
     int ts[NB], tc[NB];
 #pragma unroll
     for (int e = 0; e < NB; ++e) {
@@ -250,23 +332,29 @@ __global__ void __launch_bounds__(kDampWarps * 32) k_damp(Args<R> A, long long g
             st_vec<R, P>(sv + (e * mb + t) * P, vv);
             sf[e * mb + t] = A.flags[ts[e] + t];
         }
-    __syncwarp();
-    const R hdt = (R)(0.5 * A.ctrl->dt);
-    const R im = (R)(1.0 / A.mass);
     const int l0 = __ldg(A.grp_lvl + g), l1 = __ldg(A.grp_lvl + g + 1);
+    const long long p0 = __ldg(A.lvl_pair + l0);
+    const int np = (int)(__ldg(A.lvl_pair + l1) - p0);
+    for (int k = lane; k < np; k += 32) {
+        sg[k] = __ldg(A.pair_g + p0 + k);
+        sab[k] = __ldg(A.pair_ab + p0 + k);
+    }
+    for (int l = lane; l <= l1 - l0; l += 32) slv[l] = (int)(__ldg(A.lvl_pair + l0 + l) - p0);
+    __syncwarp();
+    const R hc = (R)(0.5 * A.ctrl->dt) * A.eta;   // dt/2 * eta
+    const R im = (R)(1.0 / A.mass);
+    const int nl = l1 - l0;
     if (mode & 1) {
-        for (int l = l0; l < l1; ++l) {
-            const long long p1 = __ldg(A.lvl_pair + l + 1);
-            for (long long p = __ldg(A.lvl_pair + l) + lane; p < p1; p += 32)
-                damp_pair<R, D>(A, p, sv, sf, hdt, im);
+        for (int l = 0; l < nl; ++l) {
+            const int e = slv[l + 1];
+            for (int k = slv[l] + lane; k < e; k += 32) damp_pair<R, D>(sg, sab, k, sv, sf, hc, im);
             __syncwarp();
         }
     }
     if (mode & 2) {
-        for (int l = l1 - 1; l >= l0; --l) {
-            const long long p1 = __ldg(A.lvl_pair + l + 1);
-            for (long long p = __ldg(A.lvl_pair + l) + lane; p < p1; p += 32)
-                damp_pair<R, D>(A, p, sv, sf, hdt, im);
+        for (int l = nl - 1; l >= 0; --l) {
+            const int e = slv[l + 1];
+            for (int k = slv[l] + lane; k < e; k += 32) damp_pair<R, D>(sg, sab, k, sv, sf, hc, im);
             __syncwarp();
         }
     }
@@ -425,33 +513,47 @@ __global__ void k_load(Args<R> A) {
 
 // explicit diffusion (Sec. 2.2 Fick's law as a scalar; Jacobi update)
 template <class R, int D>
-__global__ void __launch_bounds__(kBlock) k_diffuse(Args<R> A, R dt) {
+__global__ void __launch_bounds__(256) k_diffuse(Args<R> A, R dt) {
     constexpr int P = Pad<D>::v;
-    const long long i = blockIdx.x * (long long)kBlock + threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smem[];
+    R *sX = reinterpret_cast<R *>(smem);
+    R *sC = sX + (size_t)A.max_halo * P;
+    const long long t = blockIdx.x;
+    const long long h0 = A.halo_off[t];
+    const int nh = (int)(A.halo_off[t + 1] - h0);
+    for (int k = threadIdx.x; k < nh; k += blockDim.x) {
+        const long long g = __ldg(A.halo_idx + h0 + k);
+        R x[P];
+        ldg_vec<R, P>(x, A.X + g * P);
+        st_vec<R, P>(sX + k * P, x);
+        sC[k] = A.c[g];
+    }
+    __syncthreads();
+    const long long i = t * A.T + threadIdx.x;
     if (i >= A.n) return;
     if (A.flags[i] & kCHeldBit) {
         A.c_tmp[i] = A.c_held[i];
         return;
     }
+    const int li = A.lself[i];
     R xa[P];
-    ldg_vec<R, P>(xa, A.X + i * P);
-    const R ca = A.c[i];
+    ld_vec<R, P>(xa, sX + li * P);
+    const R ca = sC[li];
     R s = R(0);
-    const long long sl = i >> 5;
-    const int32_t *row = A.ell + A.slice_off[sl] + (i & 31);
-    const int w = A.slice_w[sl];
+    const uint16_t *row = A.lell + A.lell_off[t] + threadIdx.x;
+    const int w = A.tile_w[t];
     for (int j = 0; j < w; ++j) {
-        const int b = __ldg(row + 32 * j);
+        const int l = __ldg(row + j * A.T);
         R xb[P];
-        ldg_vec<R, P>(xb, A.X + (long long)b * P);
+        ld_vec<R, P>(xb, sX + l * P);
         R r2 = R(0);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             const R d = xa[k] - xb[k];
             r2 += d * d;
         }
-        const R t = R(1) - R(0.5) * dsqrt(r2) * A.inv_h;
-        s += (ca - A.c[b]) * t * t * t;
+        const R tt = R(1) - R(0.5) * dsqrt(r2) * A.inv_h;
+        s += (ca - sC[l]) * tt * tt * tt;
     }
     A.c_tmp[i] = ca + dt * A.dcoef * s;
 }
@@ -494,11 +596,16 @@ __global__ void k_diff_bound(const double *X64, const long long *off, const int3
 
 // --------------------------------------------------------------------- reads
 template <class R, int D>
-__global__ void k_defgrad(Args<R> A, double *out) {
-    const long long i = blockIdx.x * (long long)kBlock + threadIdx.x;
+__global__ void __launch_bounds__(256) k_defgrad(Args<R> A, double *out) {
+    constexpr int P = Pad<D>::v;
+    extern __shared__ __align__(16) unsigned char smem[];
+    R *sX = reinterpret_cast<R *>(smem);
+    R *sU = sX + (size_t)A.max_halo * P;
+    stage_halo<R, P, P>(A, sX, sU, A.uf);
+    const long long i = blockIdx.x * (long long)A.T + threadIdx.x;
     if (i >= A.n) return;
     R F[3][3];
-    compute_F<R, D>(A, i, F);
+    compute_F<R, D>(A, sX, sU, i, F);
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) out[i * 9 + r * 3 + c] = (double)F[r][c];
 }
@@ -596,9 +703,16 @@ Args<R> make_args(mts_body *b) {
     Args<R> A{};
     A.n = b->n;
     A.dim = b->dim;
-    A.ell = b->ell;
-    A.slice_off = b->slice_off;
-    A.slice_w = b->slice_w;
+    A.T = b->T;
+    A.max_halo = b->max_halo;
+    A.halo_off = b->halo_off;
+    A.halo_idx = b->halo_idx;
+    A.lself = b->lself;
+    A.lell = b->lell;
+    A.lell_off = b->lell_off;
+    A.tile_w = b->tile_w;
+    A.max_group_pairs = b->max_group_pairs;
+    A.max_group_levels = b->max_group_levels;
     A.X = (const R *)b->X;
     A.B0 = (const R *)b->B0;
     A.u = b->u;
@@ -639,27 +753,42 @@ Args<R> make_args(mts_body *b) {
     return A;
 }
 
+template <class R, int D> size_t smem_stress(const mts_body *b) {
+    return (size_t)b->max_halo * Pad<D>::v * 2 * sizeof(R);
+}
+template <class R, int D> size_t smem_force(const mts_body *b) {
+    return (size_t)b->max_halo * (Pad<D>::v + MatS<D>::v) * sizeof(R);
+}
+template <class R, int D> size_t smem_diffuse(const mts_body *b) {
+    return (size_t)b->max_halo * (Pad<D>::v + 1) * sizeof(R);
+}
+template <class R, int D> int damp_warps(const mts_body *b) {
+    const size_t per = DampSmem<R, D>::bytes(b->mb, b->max_group_pairs, b->max_group_levels);
+    int w = 4;
+    while (w > 1 && per * w > 200 * 1024) w >>= 1;
+    return w;
+}
+template <class R, int D> size_t smem_damp(const mts_body *b) {
+    return DampSmem<R, D>::bytes(b->mb, b->max_group_pairs, b->max_group_levels) * damp_warps<R, D>(b);
+}
+
 template <class R, int D>
 mts_status stress_t(mts_body *b) {
     Args<R> A = make_args<R>(b);
+    const size_t sm = smem_stress<R, D>(b);
     if (b->model == MTS_NEOHOOKE_J2)
-        k_stress<R, D, MTS_NEOHOOKE_J2><<<grid_of(b->n), kBlock, 0, b->ctx->stream>>>(A);
+        k_stress<R, D, MTS_NEOHOOKE_J2><<<(unsigned)b->ntiles, b->T, sm, b->ctx->stream>>>(A);
     else
-        k_stress<R, D, MTS_ELASTIC_SVK><<<grid_of(b->n), kBlock, 0, b->ctx->stream>>>(A);
+        k_stress<R, D, MTS_ELASTIC_SVK><<<(unsigned)b->ntiles, b->T, sm, b->ctx->stream>>>(A);
     MTS_CUDA(cudaGetLastError());
     return MTS_OK;
 }
 
 template <class R, int D>
 mts_status force_t(mts_body *b) {
-    k_force<R, D><<<grid_of(b->n), kBlock, 0, b->ctx->stream>>>(make_args<R>(b));
+    k_force<R, D><<<(unsigned)b->ntiles, b->T, smem_force<R, D>(b), b->ctx->stream>>>(make_args<R>(b));
     MTS_CUDA(cudaGetLastError());
     return MTS_OK;
-}
-
-template <class R, int D>
-size_t damp_smem(const mts_body *b) {
-    return (size_t)kDampWarps * (1 << D) * b->mb * (Pad<D>::v * sizeof(R) + 1) + 16;
 }
 
 template <class R, int D>
@@ -667,13 +796,14 @@ mts_status damping_t(mts_body *b, long long *nlaunch) {
     if (nlaunch) *nlaunch = 0;
     if (b->eta == 0.0 || b->npairs == 0) return MTS_OK;
     Args<R> A = make_args<R>(b);
-    const size_t smem = damp_smem<R, D>(b);
+    const size_t smem = smem_damp<R, D>(b);
+    const int W = damp_warps<R, D>(b);
     const int ncol = 1 << D;
     auto launch = [&](int c, int mode) -> mts_status {
         const long long g0 = b->col_off[c], g1 = b->col_off[c + 1];
         if (g1 <= g0) return MTS_OK;
-        const unsigned grid = (unsigned)((g1 - g0 + kDampWarps - 1) / kDampWarps);
-        k_damp<R, D><<<grid, kDampWarps * 32, smem, b->ctx->stream>>>(A, g0, g1, mode);
+        const unsigned grid = (unsigned)((g1 - g0 + W - 1) / W);
+        k_damp<R, D><<<grid, W * 32, smem, b->ctx->stream>>>(A, g0, g1, mode);
         MTS_CUDA(cudaGetLastError());
         if (nlaunch) ++*nlaunch;
         return MTS_OK;
@@ -689,13 +819,24 @@ mts_status damping_t(mts_body *b, long long *nlaunch) {
 // stream capture)
 template <class R, int D>
 mts_status prepare_t(mts_body *b) {
-    const size_t smem = damp_smem<R, D>(b);
-    if (smem > 227 * 1024) {
-        set_error("damping blocks hold too many particles (%d) for shared memory", b->mb);
+    const size_t lim = 227 * 1024;
+    const size_t sd = smem_damp<R, D>(b), sa = smem_stress<R, D>(b), sf = smem_force<R, D>(b),
+                 sc = smem_diffuse<R, D>(b);
+    if (sd > lim || sa > lim || sf > lim || sc > lim) {
+        set_error("shared-memory staging too large (damping %zu, stress %zu, force %zu bytes; "
+                  "halo %d particles, damping block %d particles)", sd, sa, sf, b->max_halo, b->mb);
         return MTS_ERR_INVALID_ARG;
     }
-    MTS_CUDA(cudaFuncSetAttribute(k_damp<R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)std::max<size_t>(smem, 48 * 1024)));
+    auto attr = [](const void *fn, size_t bytes) {
+        return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)std::max<size_t>(bytes, 48 * 1024));
+    };
+    MTS_CUDA(attr((const void *)k_damp<R, D>, sd));
+    MTS_CUDA(attr((const void *)k_stress<R, D, MTS_ELASTIC_SVK>, sa));
+    MTS_CUDA(attr((const void *)k_stress<R, D, MTS_NEOHOOKE_J2>, sa));
+    MTS_CUDA(attr((const void *)k_defgrad<R, D>, sa));
+    MTS_CUDA(attr((const void *)k_force<R, D>, sf));
+    MTS_CUDA(attr((const void *)k_diffuse<R, D>, sc));
     return MTS_OK;
 }
 
@@ -716,7 +857,8 @@ mts_status load_t(mts_body *b) {
 template <class R, int D>
 mts_status diffuse_t(mts_body *b, double dt) {
     Args<R> A = make_args<R>(b);
-    k_diffuse<R, D><<<grid_of(b->n), kBlock, 0, b->ctx->stream>>>(A, (R)dt);
+    MTS_TRY((prepare_t<R, D>(b)));
+    k_diffuse<R, D><<<(unsigned)b->ntiles, b->T, smem_diffuse<R, D>(b), b->ctx->stream>>>(A, (R)dt);
     k_copy<R><<<grid_of(b->n), kBlock, 0, b->ctx->stream>>>((const R *)b->c_tmp, (R *)b->c, b->n);
     MTS_CUDA(cudaGetLastError());
     return MTS_OK;
@@ -724,7 +866,9 @@ mts_status diffuse_t(mts_body *b, double dt) {
 
 template <class R, int D>
 mts_status defgrad_t(mts_body *b, double *out_sorted) {
-    k_defgrad<R, D><<<grid_of(b->n), kBlock, 0, b->ctx->stream>>>(make_args<R>(b), out_sorted);
+    MTS_TRY((prepare_t<R, D>(b)));
+    k_defgrad<R, D><<<(unsigned)b->ntiles, b->T, smem_stress<R, D>(b), b->ctx->stream>>>(
+        make_args<R>(b), out_sorted);
     MTS_CUDA(cudaGetLastError());
     return MTS_OK;
 }
@@ -733,7 +877,7 @@ template <class R, int D>
 mts_status field_out_t(mts_body *b, int field) {
     if (field == MTS_F_DEFGRAD) {
         double *tmp = b->scratch + (size_t)b->n * 9;
-        k_defgrad<R, D><<<grid_of(b->n), kBlock, 0, b->ctx->stream>>>(make_args<R>(b), tmp);
+        MTS_TRY((defgrad_t<R, D>(b, tmp)));
         k_perm_rows<<<grid_of(b->n), kBlock, 0, b->ctx->stream>>>(tmp, b->perm, b->n, 9, b->scratch);
     } else {
         k_field_out<R, D><<<grid_of(b->n), kBlock, 0, b->ctx->stream>>>(make_args<R>(b), field,

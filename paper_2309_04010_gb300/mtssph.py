@@ -10,9 +10,12 @@ raises.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
 import re
+import sys
+import weakref
 from typing import Optional
 
 import numpy as np
@@ -27,6 +30,20 @@ ELASTIC_SVK, NEOHOOKE_J2 = 0, 1
 F_U, F_X, F_V, F_DEFGRAD, F_PB, F_C, F_ALPHA, F_CPINV, F_ACC = range(9)
 
 _lib = None
+_live_contexts: "weakref.WeakSet" = weakref.WeakSet()
+
+
+def _shutdown():
+    """Release every body and context while PyTorch (whose allocator frees the
+    device memory) is still alive; interpreter teardown order is arbitrary."""
+    for ctx in list(_live_contexts):
+        try:
+            ctx.close()
+        except Exception:
+            pass
+
+
+atexit.register(_shutdown)
 
 
 class MtsError(RuntimeError):
@@ -151,17 +168,27 @@ class Context:
         _check(lib().mts_ctx_create(device, C.c_void_p(self.stream.cuda_stream), alloc_p,
                                     C.byref(h)), "mts_ctx_create")
         self._h = h
+        self._bodies: "weakref.WeakSet" = weakref.WeakSet()
+        _live_contexts.add(self)
 
     @property
     def handle(self):
+        if not getattr(self, "_h", None):
+            raise RuntimeError("context is closed")
         return self._h
 
     def close(self):
+        """Destroy the context after every body created on it."""
         if getattr(self, "_h", None):
+            for b in list(self._bodies):
+                b.close()
+            self.stream.synchronize()
             lib().mts_ctx_destroy(self._h)
             self._h = None
 
     def __del__(self):
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -181,6 +208,7 @@ class Body:
         h = C.c_void_p()
         _check(lib().mts_body_create(ctx.handle, C.byref(desc), C.byref(h)), "mts_body_create")
         self._h = h
+        ctx._bodies.add(self)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -188,6 +216,8 @@ class Body:
             self._h = None
 
     def __del__(self):
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:

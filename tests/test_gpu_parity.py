@@ -21,7 +21,9 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def ctx():
-    return M.Context(0)
+    c = M.Context(0)
+    yield c
+    c.close()
 
 
 def rel(a, b):
