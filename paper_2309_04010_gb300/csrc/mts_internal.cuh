@@ -110,6 +110,7 @@ struct Args {
     int max_group_levels;
     // Morton tiles of T particles with their neighbour halo (shared-memory staging)
     int T;                       // particles per tile = threads per CTA
+    long long ntiles;            // CTAs of the tiled kernels (= force partials)
     int max_halo;                // largest halo (tile + neighbours)
     const long long *halo_off;   // tile -> first halo entry, ntiles + 1
     const int32_t *halo_idx;     // halo particle indices, ascending per tile

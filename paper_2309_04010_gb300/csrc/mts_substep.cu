@@ -28,6 +28,13 @@ namespace {
 
 inline unsigned grid_of(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
+// byte offset of the second staged array: rounded up to 16 bytes so that
+// 16-byte vector loads from it stay aligned for any halo size
+template <class R, int P>
+__host__ __device__ __forceinline__ size_t second_off(int max_halo) {
+    return ((size_t)max_halo * P * sizeof(R) + 15) & ~size_t(15);
+}
+
 // --------------------------------------------------------------------- tiles
 // A CTA owns one Morton tile of T = blockDim.x consecutive particles.  It
 // stages the reference positions and one more per-particle array of the tile's
@@ -126,7 +133,7 @@ __global__ void __launch_bounds__(256) k_stress(Args<R> A) {
     constexpr int P = Pad<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
     R *sX = reinterpret_cast<R *>(smem);
-    R *sU = sX + (size_t)A.max_halo * P;
+    R *sU = reinterpret_cast<R *>(smem + second_off<R, P>(A.max_halo));
     stage_halo<R, P, P>(A, sX, sU, A.uf);
     const long long i = blockIdx.x * (long long)A.T + threadIdx.x;
     if (i >= A.n) return;
@@ -172,7 +179,7 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
     constexpr int MS = MatS<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
     R *sX = reinterpret_cast<R *>(smem);
-    R *sP = sX + (size_t)A.max_halo * P;
+    R *sP = reinterpret_cast<R *>(smem + second_off<R, P>(A.max_halo));
     stage_halo<R, P, MS>(A, sX, sP, A.PB);
     const long long t = blockIdx.x;
     const long long i = t * A.T + threadIdx.x;
@@ -433,6 +440,8 @@ __global__ void __launch_bounds__(kBlock) k_drift(Args<R> A) {
     for (unsigned q = threadIdx.x; q < gridDim.x; q += kBlock) {
         s_ke += __ldcg(A.part_drift + q * 2);
         s_v = fmax(s_v, __ldcg(A.part_drift + q * 2 + 1));
+    }
+    for (long long q = threadIdx.x; q < A.ntiles; q += kBlock) {   // one partial per force CTA
         s_a = fmax(s_a, __ldcg(A.part_force + q * 4));
         for (int k = 0; k < 3; ++k) s_f[k] += __ldcg(A.part_force + q * 4 + 1 + k);
     }
@@ -517,7 +526,7 @@ __global__ void __launch_bounds__(256) k_diffuse(Args<R> A, R dt) {
     constexpr int P = Pad<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
     R *sX = reinterpret_cast<R *>(smem);
-    R *sC = sX + (size_t)A.max_halo * P;
+    R *sC = reinterpret_cast<R *>(smem + second_off<R, P>(A.max_halo));
     const long long t = blockIdx.x;
     const long long h0 = A.halo_off[t];
     const int nh = (int)(A.halo_off[t + 1] - h0);
@@ -600,7 +609,7 @@ __global__ void __launch_bounds__(256) k_defgrad(Args<R> A, double *out) {
     constexpr int P = Pad<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
     R *sX = reinterpret_cast<R *>(smem);
-    R *sU = sX + (size_t)A.max_halo * P;
+    R *sU = reinterpret_cast<R *>(smem + second_off<R, P>(A.max_halo));
     stage_halo<R, P, P>(A, sX, sU, A.uf);
     const long long i = blockIdx.x * (long long)A.T + threadIdx.x;
     if (i >= A.n) return;
@@ -704,6 +713,7 @@ Args<R> make_args(mts_body *b) {
     A.n = b->n;
     A.dim = b->dim;
     A.T = b->T;
+    A.ntiles = b->ntiles;
     A.max_halo = b->max_halo;
     A.halo_off = b->halo_off;
     A.halo_idx = b->halo_idx;
@@ -754,13 +764,13 @@ Args<R> make_args(mts_body *b) {
 }
 
 template <class R, int D> size_t smem_stress(const mts_body *b) {
-    return (size_t)b->max_halo * Pad<D>::v * 2 * sizeof(R);
+    return second_off<R, Pad<D>::v>(b->max_halo) + (size_t)b->max_halo * Pad<D>::v * sizeof(R);
 }
 template <class R, int D> size_t smem_force(const mts_body *b) {
-    return (size_t)b->max_halo * (Pad<D>::v + MatS<D>::v) * sizeof(R);
+    return second_off<R, Pad<D>::v>(b->max_halo) + (size_t)b->max_halo * MatS<D>::v * sizeof(R);
 }
 template <class R, int D> size_t smem_diffuse(const mts_body *b) {
-    return (size_t)b->max_halo * (Pad<D>::v + 1) * sizeof(R);
+    return second_off<R, Pad<D>::v>(b->max_halo) + (size_t)b->max_halo * sizeof(R);
 }
 template <class R, int D> int damp_warps(const mts_body *b) {
     const size_t per = DampSmem<R, D>::bytes(b->mb, b->max_group_pairs, b->max_group_levels);
