@@ -383,7 +383,8 @@ static int build_b0(ob_body *b) {
 /*   > 2h); pair (a<b) is owned by the componentwise-min block of its   */
 /*   two particles; block colour = parity bits of the owner block;      */
 /*   inside an owner block its pairs, in ascending (a,b), take the      */
-/*   smallest sub-colour unused at a and at b (greedy).  Sequential     */
+/*   smallest sub-colour unused at a and at b that holds fewer than 32  */
+/*   pairs so far (greedy, capped level size).  Sequential              */
 /*   order: colour, owner block Morton key, sub-colour, a, b.  Pairs of */
 /*   one (colour, sub-colour) touch disjoint particles.                 */
 /* ------------------------------------------------------------------ */
@@ -406,6 +407,7 @@ static int cmp_pair_final(const void *x, const void *y) {
 }
 
 #define OB_MAXSUB 256
+#define OB_LEVEL_CAP 32
 static int build_colouring(ob_body *b) {
     int d = b->dim;
     int64_t np = b->nnz / 2;
@@ -440,12 +442,17 @@ static int build_colouring(ob_body *b) {
     while (s < m) {
         int64_t e = s;
         while (e < m && pr[e].col == pr[s].col && pr[e].key == pr[s].key) e++;
+        int count[OB_MAXSUB];
+        memset(count, 0, sizeof(count));
         for (int64_t t = s; t < e; t++) {
             uint64_t *ua = used + (size_t)pr[t].a * (OB_MAXSUB / 64);
             uint64_t *ub = used + (size_t)pr[t].b * (OB_MAXSUB / 64);
             int c = 0;
-            while (c < OB_MAXSUB && (((ua[c >> 6] | ub[c >> 6]) >> (c & 63)) & 1)) c++;
+            while (c < OB_MAXSUB &&
+                   ((((ua[c >> 6] | ub[c >> 6]) >> (c & 63)) & 1) || count[c] >= OB_LEVEL_CAP))
+                c++;
             if (c >= OB_MAXSUB) { free(used); free(pr); return OB_ERR_STATE; }
+            count[c]++;
             pr[t].sub = c;
             ua[c >> 6] |= 1ull << (c & 63);
             ub[c >> 6] |= 1ull << (c & 63);

@@ -101,6 +101,14 @@ __device__ __forceinline__ void st_mat(R *p, const R (&M)[D][D]) {
 // ------------------------------------------------------------------ math
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+// square root for the neighbour loops: the hardware approximation in FP32
+// (mixed precision), IEEE in FP64; exact 0 for the zero-distance padding
+__device__ __forceinline__ float nsqrt(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double nsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float dexp(float x) { return expf(x); }
 __device__ __forceinline__ double dexp(double x) { return exp(x); }
 __device__ __forceinline__ float drcbrt(float x) { return rcbrtf(x); }

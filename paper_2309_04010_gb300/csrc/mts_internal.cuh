@@ -33,7 +33,7 @@ constexpr int kForceBit = 8;
 constexpr int kTipBit = 16;
 constexpr int kCHeldBit = 32;
 constexpr int kBlock = 128;  // threads per block of the per-particle kernels
-constexpr int kDampWarps = 4;  // owner groups (warps) per damping CTA
+constexpr int kLevelCap = 32;  // pairs per damping level: one warp-wide pass
 
 // ------------------------------------------------------------------ errors
 void set_error(const char *fmt, ...);

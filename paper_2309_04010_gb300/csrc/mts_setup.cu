@@ -12,7 +12,8 @@
 //   5. Canonical order of the pairwise damping (Sec. 4.3): pairs owned by the
 //      componentwise-min block (blocks of 2^s cells, 2^s dx > 2h) of their two
 //      particles; block colour = parity bits; greedy sub-colours in ascending
-//      (a,b) per owner block; then per-block level lists with block-local
+//      (a,b) per owner block, at most 32 pairs per sub-colour; then per-block
+//      level lists with block-local
 //      particle indices for the shared-memory damping kernel.
 #include <cub/cub.cuh>
 
@@ -376,6 +377,8 @@ __global__ void k_greedy(const long long *gstart, long long g0, long long g1, lo
         }
     }
     int maxc = -1;
+    int count[256];
+    for (int c = 0; c < 256; ++c) count[c] = 0;
     for (long long p = p0; p < p1; ++p) {
         int loc[2];
         int pp[2] = {pa[p], pb[p]};
@@ -386,15 +389,25 @@ __global__ void k_greedy(const long long *gstart, long long g0, long long g1, lo
             loc[t] = e * mb + (pp[t] - tstart[g * nbk + e]);
         }
         unsigned long long *ua = U + (long long)loc[0] * 4, *ub = U + (long long)loc[1] * 4;
+        // smallest sub-colour free at both particles that still has room
+        // (at most kLevelCap pairs per level: one warp-wide pass)
         int c = -1;
         for (int w = 0; w < 4 && c < 0; ++w) {
             unsigned long long free_bits = ~(ua[w] | ub[w]);
-            if (free_bits) c = w * 64 + __ffsll((long long)free_bits) - 1;
+            while (free_bits) {
+                const int cand = w * 64 + __ffsll((long long)free_bits) - 1;
+                if (count[cand] < kLevelCap) {
+                    c = cand;
+                    break;
+                }
+                free_bits &= free_bits - 1;
+            }
         }
         if (c < 0) {
             atomicOr(&ctrl->err, kErrTooMany);
             c = 255;
         }
+        ++count[c];
         ua[c >> 6] |= 1ull << (c & 63);
         ub[c >> 6] |= 1ull << (c & 63);
         sub[p] = c;

@@ -100,7 +100,7 @@ __device__ __forceinline__ void compute_F(const Args<R> &A, const R *sX, const R
             d[k] = xa[k] - xb[k];
             r2 += d[k] * d[k];
         }
-        const R tt = R(1) - R(0.5) * dsqrt(r2) * A.inv_h;
+        const R tt = R(1) - R(0.5) * nsqrt(r2) * A.inv_h;
         const R f = A.kcoef * tt * tt * tt;   // V W'(r)/r
 #pragma unroll
         for (int r = 0; r < D; ++r) {
@@ -201,9 +201,10 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
                 Pa[r][0] = q[0]; Pa[r][1] = q[1]; Pa[r][2] = q[2];
             }
         }
-        R acc[D];
+        // a_a = (PB_a sum_b g_ab + sum_b PB_b g_ab) / rho0, g_ab = V grad_a W_ab
+        R acc[D], gs[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) acc[k] = R(0);
+        for (int k = 0; k < D; ++k) acc[k] = gs[k] = R(0);
         const int T = A.T;
         const uint16_t *row = A.lell + A.lell_off[t] + threadIdx.x;
         const int w = A.tile_w[t];
@@ -218,23 +219,31 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
                 d[k] = xa[k] - xb[k];
                 r2 += d[k] * d[k];
             }
-            const R tt = R(1) - R(0.5) * dsqrt(r2) * A.inv_h;
+            const R tt = R(1) - R(0.5) * nsqrt(r2) * A.inv_h;
             const R f = A.kcoef * tt * tt * tt;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                d[k] *= f;
+                gs[k] += d[k];
+            }
             if constexpr (D == 2) {
                 R q[4];
                 ld_vec<R, 4>(q, sP + l * 4);
-                acc[0] += ((Pa[0][0] + q[0]) * d[0] + (Pa[0][1] + q[1]) * d[1]) * f;
-                acc[1] += ((Pa[1][0] + q[2]) * d[0] + (Pa[1][1] + q[3]) * d[1]) * f;
+                acc[0] += q[0] * d[0] + q[1] * d[1];
+                acc[1] += q[2] * d[0] + q[3] * d[1];
             } else {
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
                     R q[4];
                     ld_vec<R, 4>(q, sP + l * 12 + 4 * r);
-                    acc[r] += ((Pa[r][0] + q[0]) * d[0] + (Pa[r][1] + q[1]) * d[1] +
-                               (Pa[r][2] + q[2]) * d[2]) * f;
+                    acc[r] += q[0] * d[0] + q[1] * d[1] + q[2] * d[2];
                 }
             }
         }
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[r] += Pa[r][c] * gs[c];
         const uint8_t fx = A.flags[i];
         const R dt = (R)A.ctrl->dt;
         R v[P];
@@ -288,23 +297,39 @@ struct DampSmem {
     }
 };
 
+// One backward-Euler update of the pair ODE m dv_a/dt = -B (v_a - v_b) with
+// x = (dt/2) B: w' = w / (1 + x (1/m_a + 1/m_b)), v_a -= x w' / m_a, v_b += x w' / m_b.
+// f > 0 is the precomputed factor x/m / (1 + 2 x/m) of a pair whose particles
+// are free on every axis (equal masses); f <= 0 stores -x for pairs with a
+// constrained axis (1/m = 0 on that axis), handled per axis.
 template <class R, int D>
-__device__ __forceinline__ void damp_pair(const R *sg, const uint32_t *sab, int k, R *sv,
-                                          const uint8_t *sf, R hc, R im) {
+__device__ __forceinline__ void damp_pair(uint32_t ab, R f, R *sv, const uint8_t *sf, R im) {
     constexpr int P = Pad<D>::v;
-    const uint32_t ab = sab[k];
     const int la = (int)(ab & 0xffffu), lb = (int)(ab >> 16);
-    const R c = hc * sg[k];
-    const uint8_t fa = sf[la], fb = sf[lb];
-    R *va = sv + la * P, *vb = sv + lb * P;
+    R va[P], vb[P];
+    ld_vec<R, P>(va, sv + la * P);
+    ld_vec<R, P>(vb, sv + lb * P);
+    if (f > R(0)) {
 #pragma unroll
-    for (int q = 0; q < D; ++q) {
-        const R ia = ((fa >> q) & 1) ? R(0) : im;
-        const R ib = ((fb >> q) & 1) ? R(0) : im;
-        const R wn = (va[q] - vb[q]) / (R(1) + c * (ia + ib));
-        va[q] -= c * wn * ia;
-        vb[q] += c * wn * ib;
+        for (int q = 0; q < D; ++q) {
+            const R w = va[q] - vb[q];
+            va[q] -= f * w;
+            vb[q] += f * w;
+        }
+    } else {
+        const R x = -f;
+        const uint8_t fa = sf[la], fb = sf[lb];
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            const R ia = ((fa >> q) & 1) ? R(0) : im;
+            const R ib = ((fb >> q) & 1) ? R(0) : im;
+            const R wn = (va[q] - vb[q]) / (R(1) + x * (ia + ib));
+            va[q] -= x * wn * ia;
+            vb[q] += x * wn * ib;
+        }
     }
+    st_vec<R, P>(sv + la * P, va);
+    st_vec<R, P>(sv + lb * P, vb);
 }
 
 template <class R, int D>
@@ -321,8 +346,8 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     unsigned char *base = smem + (size_t)warp * DampSmem<R, D>::bytes(mb, A.max_group_pairs,
                                                                          A.max_group_levels);
     R *sv = reinterpret_cast<R *>(base);
-    R *sg = sv + (size_t)NB * mb * P;
-    uint32_t *sab = reinterpret_cast<uint32_t *>(sg + A.max_group_pairs);
+    R *sfac = sv + (size_t)NB * mb * P;
+    uint32_t *sab = reinterpret_cast<uint32_t *>(sfac + A.max_group_pairs);
     int *slv = reinterpret_cast<int *>(sab + A.max_group_pairs);
     uint8_t *sf = reinterpret_cast<uint8_t *>(slv + A.max_group_levels + 1);
     int ts[NB], tc[NB];
@@ -342,26 +367,31 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     const int l0 = __ldg(A.grp_lvl + g), l1 = __ldg(A.grp_lvl + g + 1);
     const long long p0 = __ldg(A.lvl_pair + l0);
     const int np = (int)(__ldg(A.lvl_pair + l1) - p0);
-    for (int k = lane; k < np; k += 32) {
-        sg[k] = __ldg(A.pair_g + p0 + k);
-        sab[k] = __ldg(A.pair_ab + p0 + k);
-    }
     for (int l = lane; l <= l1 - l0; l += 32) slv[l] = (int)(__ldg(A.lvl_pair + l0 + l) - p0);
     __syncwarp();
     const R hc = (R)(0.5 * A.ctrl->dt) * A.eta;   // dt/2 * eta
     const R im = (R)(1.0 / A.mass);
+    const uint8_t fixmask = (uint8_t)((1 << D) - 1);
+    for (int k = lane; k < np; k += 32) {
+        const uint32_t ab = __ldg(A.pair_ab + p0 + k);
+        const R x = hc * __ldg(A.pair_g + p0 + k);
+        const bool free2 = !((sf[ab & 0xffffu] | sf[ab >> 16]) & fixmask);
+        sab[k] = ab;
+        sfac[k] = free2 ? x * im / (R(1) + R(2) * x * im) : -x;
+    }
+    __syncwarp();
     const int nl = l1 - l0;
     if (mode & 1) {
         for (int l = 0; l < nl; ++l) {
-            const int e = slv[l + 1];
-            for (int k = slv[l] + lane; k < e; k += 32) damp_pair<R, D>(sg, sab, k, sv, sf, hc, im);
+            const int k = slv[l] + lane;
+            if (k < slv[l + 1]) damp_pair<R, D>(sab[k], sfac[k], sv, sf, im);
             __syncwarp();
         }
     }
     if (mode & 2) {
         for (int l = nl - 1; l >= 0; --l) {
-            const int e = slv[l + 1];
-            for (int k = slv[l] + lane; k < e; k += 32) damp_pair<R, D>(sg, sab, k, sv, sf, hc, im);
+            const int k = slv[l] + lane;
+            if (k < slv[l + 1]) damp_pair<R, D>(sab[k], sfac[k], sv, sf, im);
             __syncwarp();
         }
     }
@@ -561,7 +591,7 @@ __global__ void __launch_bounds__(256) k_diffuse(Args<R> A, R dt) {
             const R d = xa[k] - xb[k];
             r2 += d * d;
         }
-        const R tt = R(1) - R(0.5) * dsqrt(r2) * A.inv_h;
+        const R tt = R(1) - R(0.5) * nsqrt(r2) * A.inv_h;
         s += (ca - sC[l]) * tt * tt * tt;
     }
     A.c_tmp[i] = ca + dt * A.dcoef * s;

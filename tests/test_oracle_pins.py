@@ -129,6 +129,9 @@ def test_colour_stages_are_matchings(dim, counts):
             sel = (col == c) & (sub == s)
             parts = np.concatenate([pa[sel], pb[sel]])
             assert np.unique(parts).size == parts.size
+    # one owner block's level holds at most 32 pairs (one warp-wide pass)
+    _, counts = np.unique(np.stack([col, key, sub]), axis=1, return_counts=True)
+    assert counts.max() <= 32
     assert len(np.unique(col)) <= 2 ** dim
 
 
@@ -693,16 +696,18 @@ def test_colouring_matches_independent_greedy(dim, counts):
                 recs.append([col, mkey(owner), a, int(b)])
     recs.sort()
     used = {}
+    count = {}
     subs = []
     for i, (col, key, a, b) in enumerate(recs):
         if i == 0 or (col, key) != (recs[i - 1][0], recs[i - 1][1]):
-            used = {}
+            used, count = {}, {}
         ua, ub = used.setdefault(a, set()), used.setdefault(b, set())
         c = 0
-        while c in ua or c in ub:
+        while c in ua or c in ub or count.get(c, 0) >= 32:   # at most 32 pairs per level
             c += 1
         ua.add(c)
         ub.add(c)
+        count[c] = count.get(c, 0) + 1
         subs.append(c)
     want = sorted((r[0], r[1], s, r[2], r[3]) for r, s in zip(recs, subs))
     pa, pb, col, key, sub = ob.colouring()
