@@ -146,6 +146,7 @@ mts_status upload_bc(mts_body *b, const std::vector<double> &u_unit_sorted) {
     if (!u_unit_sorted.empty())
         MTS_CUDA(cudaMemcpyAsync(b->u_unit, u_unit_sorted.data(),
                                  u_unit_sorted.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    MTS_TRY(update_pair_fixbits(b));
     MTS_CUDA(cudaStreamSynchronize(st));
     return MTS_OK;
 }

@@ -98,6 +98,31 @@ __device__ __forceinline__ void st_mat(R *p, const R (&M)[D][D]) {
     }
 }
 
+// ------------------------------------------------------------------ async copies
+// cp.async global -> shared (non-blocking; completion by cp_async_wait_all)
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if (bytes == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+    else if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+// copy N reals (N * sizeof(R) a multiple of 8, both ends aligned to min(16, N*sizeof(R)))
+template <class R, int N>
+__device__ __forceinline__ void cp_async_reals(R *smem, const R *gmem) {
+    constexpr int B = N * (int)sizeof(R);
+    if constexpr (B <= 16) {
+        cp_async(smem, gmem, B);
+    } else {
+#pragma unroll
+        for (int o = 0; o < B / 16; ++o)
+            cp_async(reinterpret_cast<char *>(smem) + 16 * o, reinterpret_cast<const char *>(gmem) + 16 * o, 16);
+    }
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ------------------------------------------------------------------ math
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }

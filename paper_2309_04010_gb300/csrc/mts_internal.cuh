@@ -231,6 +231,7 @@ mts_status launch_force(mts_body *b);
 mts_status launch_damping(mts_body *b, long long *launches = nullptr);
 mts_status launch_drift(mts_body *b);
 mts_status prepare_kernels(mts_body *b);
+mts_status update_pair_fixbits(mts_body *b);
 mts_status launch_slow_begin(mts_body *b);
 mts_status launch_diffusion(mts_body *b, double dt);
 mts_status diffusion_bound(mts_body *b, double *amax_sum);

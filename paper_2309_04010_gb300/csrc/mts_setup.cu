@@ -835,9 +835,9 @@ mts_status build_typed(mts_body *b, const double *hX) {
     unsigned int hmb = 0;
     MTS_TRY(to_host(&hmb, dmb, 1, st));
     const int nbk = 1 << D;
-    if ((long long)hmb * nbk > 65535) {
-        set_error("damping block holds %u particles; at most %d fit the 16-bit local index",
-                  hmb, 65535 / nbk);
+    if ((long long)hmb * nbk > 32767) {
+        set_error("damping block holds %u particles; at most %d fit the 15-bit local index",
+                  hmb, 32767 / nbk);
         return MTS_ERR_INVALID_ARG;
     }
     b->mb = (int)hmb;

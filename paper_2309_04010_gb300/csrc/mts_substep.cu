@@ -45,26 +45,24 @@ __device__ __forceinline__ int stage_halo(const Args<R> &A, R *sX, R *sY, const 
     const long long t = blockIdx.x;
     const long long h0 = A.halo_off[t];
     const int nh = (int)(A.halo_off[t + 1] - h0);
-    for (int k = threadIdx.x; k < nh; k += blockDim.x) {
-        const long long g = __ldg(A.halo_idx + h0 + k);
-        R x[P];
-        ldg_vec<R, P>(x, A.X + g * P);
-        st_vec<R, P>(sX + k * P, x);
-        if (sY) {
-            if constexpr (NY == 12) {
+    // indices first (independent loads), then asynchronous row copies
+    constexpr int U = 4;
+    for (int k0 = threadIdx.x; k0 < nh; k0 += U * blockDim.x) {
+        int g[U];
 #pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    R y[4];
-                    ldg_vec<R, 4>(y, Y + g * 12 + 4 * r);
-                    st_vec<R, 4>(sY + k * 12 + 4 * r, y);
-                }
-            } else {
-                R y[NY];
-                ldg_vec<R, NY>(y, Y + g * NY);
-                st_vec<R, NY>(sY + k * NY, y);
-            }
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * blockDim.x;
+            g[u] = k < nh ? __ldg(A.halo_idx + h0 + k) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * blockDim.x;
+            if (g[u] < 0) continue;
+            cp_async_reals<R, P>(sX + (size_t)k * P, A.X + (size_t)g[u] * P);
+            if (sY) cp_async_reals<R, NY>(sY + (size_t)k * NY, Y + (size_t)g[u] * NY);
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     return nh;
 }
@@ -299,17 +297,24 @@ struct DampSmem {
 
 // One backward-Euler update of the pair ODE m dv_a/dt = -B (v_a - v_b) with
 // x = (dt/2) B: w' = w / (1 + x (1/m_a + 1/m_b)), v_a -= x w' / m_a, v_b += x w' / m_b.
-// f > 0 is the precomputed factor x/m / (1 + 2 x/m) of a pair whose particles
-// are free on every axis (equal masses); f <= 0 stores -x for pairs with a
-// constrained axis (1/m = 0 on that axis), handled per axis.
+// Bit 31 of the packed pair word marks a pair with a constrained axis
+// (1/m = 0 on that axis), handled per axis; all other pairs are free-free
+// with equal masses: v_a -= f w, v_b += f w with f = x/m / (1 + 2 x/m).
+constexpr uint32_t kPairFixBit = 0x80000000u;
+
+template <class R> __device__ __forceinline__ R fast_div(R a, R b) { return a / b; }
+template <> __device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
+
 template <class R, int D>
-__device__ __forceinline__ void damp_pair(uint32_t ab, R f, R *sv, const uint8_t *sf, R im) {
+__device__ __forceinline__ void damp_pair(uint32_t ab, R x, R *sv, const uint8_t *sf, R im) {
     constexpr int P = Pad<D>::v;
-    const int la = (int)(ab & 0xffffu), lb = (int)(ab >> 16);
+    const int la = (int)(ab & 0x7fffu), lb = (int)((ab >> 16) & 0x7fffu);
     R va[P], vb[P];
     ld_vec<R, P>(va, sv + la * P);
     ld_vec<R, P>(vb, sv + lb * P);
-    if (f > R(0)) {
+    if (!(ab & kPairFixBit)) {
+        const R xm = x * im;
+        const R f = fast_div<R>(xm, R(1) + R(2) * xm);
 #pragma unroll
         for (int q = 0; q < D; ++q) {
             const R w = va[q] - vb[q];
@@ -317,7 +322,6 @@ __device__ __forceinline__ void damp_pair(uint32_t ab, R f, R *sv, const uint8_t
             vb[q] += f * w;
         }
     } else {
-        const R x = -f;
         const uint8_t fa = sf[la], fb = sf[lb];
 #pragma unroll
         for (int q = 0; q < D; ++q) {
@@ -346,8 +350,8 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     unsigned char *base = smem + (size_t)warp * DampSmem<R, D>::bytes(mb, A.max_group_pairs,
                                                                          A.max_group_levels);
     R *sv = reinterpret_cast<R *>(base);
-    R *sfac = sv + (size_t)NB * mb * P;
-    uint32_t *sab = reinterpret_cast<uint32_t *>(sfac + A.max_group_pairs);
+    R *sg = sv + (size_t)NB * mb * P;
+    uint32_t *sab = reinterpret_cast<uint32_t *>(sg + A.max_group_pairs);
     int *slv = reinterpret_cast<int *>(sab + A.max_group_pairs);
     uint8_t *sf = reinterpret_cast<uint8_t *>(slv + A.max_group_levels + 1);
     int ts[NB], tc[NB];
@@ -356,42 +360,39 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
         ts[e] = __ldg(A.touch_start + g * NB + e);
         tc[e] = __ldg(A.touch_cnt + g * NB + e);
     }
-#pragma unroll
-    for (int e = 0; e < NB; ++e)
-        for (int t = lane; t < tc[e]; t += 32) {
-            R vv[P];
-            ld_vec<R, P>(vv, A.v + (long long)(ts[e] + t) * P);
-            st_vec<R, P>(sv + (e * mb + t) * P, vv);
-            sf[e * mb + t] = A.flags[ts[e] + t];
-        }
     const int l0 = __ldg(A.grp_lvl + g), l1 = __ldg(A.grp_lvl + g + 1);
     const long long p0 = __ldg(A.lvl_pair + l0);
     const int np = (int)(__ldg(A.lvl_pair + l1) - p0);
+    // asynchronous staging: velocities of the touched blocks, pair words and
+    // coefficients; flags and the level table with plain loads meanwhile
+#pragma unroll
+    for (int e = 0; e < NB; ++e)
+        for (int t = lane; t < tc[e]; t += 32)
+            cp_async_reals<R, P>(sv + (size_t)(e * mb + t) * P, A.v + (size_t)(ts[e] + t) * P);
+    for (int k = lane; k < np; k += 32) {
+        cp_async(sab + k, A.pair_ab + p0 + k, 4);
+        cp_async(sg + k, A.pair_g + p0 + k, (int)sizeof(R));
+    }
+#pragma unroll
+    for (int e = 0; e < NB; ++e)
+        for (int t = lane; t < tc[e]; t += 32) sf[e * mb + t] = A.flags[ts[e] + t];
     for (int l = lane; l <= l1 - l0; l += 32) slv[l] = (int)(__ldg(A.lvl_pair + l0 + l) - p0);
+    cp_async_wait_all();
     __syncwarp();
     const R hc = (R)(0.5 * A.ctrl->dt) * A.eta;   // dt/2 * eta
     const R im = (R)(1.0 / A.mass);
-    const uint8_t fixmask = (uint8_t)((1 << D) - 1);
-    for (int k = lane; k < np; k += 32) {
-        const uint32_t ab = __ldg(A.pair_ab + p0 + k);
-        const R x = hc * __ldg(A.pair_g + p0 + k);
-        const bool free2 = !((sf[ab & 0xffffu] | sf[ab >> 16]) & fixmask);
-        sab[k] = ab;
-        sfac[k] = free2 ? x * im / (R(1) + R(2) * x * im) : -x;
-    }
-    __syncwarp();
     const int nl = l1 - l0;
     if (mode & 1) {
         for (int l = 0; l < nl; ++l) {
             const int k = slv[l] + lane;
-            if (k < slv[l + 1]) damp_pair<R, D>(sab[k], sfac[k], sv, sf, im);
+            if (k < slv[l + 1]) damp_pair<R, D>(sab[k], hc * sg[k], sv, sf, im);
             __syncwarp();
         }
     }
     if (mode & 2) {
         for (int l = nl - 1; l >= 0; --l) {
             const int k = slv[l] + lane;
-            if (k < slv[l + 1]) damp_pair<R, D>(sab[k], sfac[k], sv, sf, im);
+            if (k < slv[l + 1]) damp_pair<R, D>(sab[k], hc * sg[k], sv, sf, im);
             __syncwarp();
         }
     }
@@ -402,6 +403,15 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
             ld_vec<R, P>(vv, sv + (e * mb + t) * P);
             st_vec<R, P>(A.v + (long long)(ts[e] + t) * P, vv);
         }
+}
+
+// pair words: set bit 31 when either particle has a constrained axis
+__global__ void k_pair_fixbits(uint32_t *ab, const int32_t *pa, const int32_t *pb, long long m,
+                               const uint8_t *flags, int fixmask) {
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    const bool fix = (flags[pa[p]] | flags[pb[p]]) & fixmask;
+    ab[p] = fix ? (ab[p] | kPairFixBit) : (ab[p] & ~kPairFixBit);
 }
 
 // --------------------------------------------------------------------- drift
@@ -947,6 +957,14 @@ mts_status launch_force(mts_body *b) { return DISPATCH(force_t, b); }
 mts_status launch_damping(mts_body *b, long long *launches) { return DISPATCH(damping_t, b, launches); }
 mts_status launch_drift(mts_body *b) { return DISPATCH(drift_t, b); }
 mts_status prepare_kernels(mts_body *b) { return DISPATCH(prepare_t, b); }
+
+mts_status update_pair_fixbits(mts_body *b) {
+    if (b->npairs == 0) return MTS_OK;
+    k_pair_fixbits<<<(unsigned)((b->npairs + 255) / 256), 256, 0, b->ctx->stream>>>(
+        b->pair_ab, b->pair_a, b->pair_b, b->npairs, b->flags, (1 << b->dim) - 1);
+    MTS_CUDA(cudaGetLastError());
+    return MTS_OK;
+}
 mts_status launch_slow_begin(mts_body *b) { return DISPATCH(load_t, b); }
 mts_status launch_diffusion(mts_body *b, double dt) { return DISPATCH(diffuse_t, b, dt); }
 mts_status launch_defgrad(mts_body *b, double *out_sorted) { return DISPATCH(defgrad_t, b, out_sorted); }
