@@ -67,6 +67,27 @@ __device__ __forceinline__ int stage_halo(const Args<R> &A, R *sX, R *sY, const 
     return nh;
 }
 
+// Visit the neighbour slots of one particle, reading the index stream 8
+// entries ahead into registers so that each warp keeps several index lines in
+// flight (the loop is unrolled by 8 so every register index is static).
+template <class Body>
+__device__ __forceinline__ void for_each_neighbour(const uint16_t *row, int T, int w, Body body) {
+    constexpr int K = 8;
+    int cur[K], nxt[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) cur[u] = u < w ? (int)__ldg(row + u * T) : 0;
+    for (int j0 = 0; j0 < w; j0 += K) {
+#pragma unroll
+        for (int u = 0; u < K; ++u)
+            nxt[u] = (j0 + K + u < w) ? (int)__ldg(row + (j0 + K + u) * T) : 0;
+#pragma unroll
+        for (int u = 0; u < K; ++u)
+            if (j0 + u < w) body(cur[u]);
+#pragma unroll
+        for (int u = 0; u < K; ++u) cur[u] = nxt[u];
+    }
+}
+
 // F_a = I + (sum_b V (u_b - u_a) (x) grad_a W_ab) B0_a, 3x3 with F_zz = 1 in 2D;
 // X and u of the halo are in shared memory.
 template <class R, int D>
@@ -86,9 +107,8 @@ __device__ __forceinline__ void compute_F(const Args<R> &A, const R *sX, const R
     const int T = A.T;
     const uint16_t *row = A.lell + A.lell_off[t] + threadIdx.x;
     const int w = A.tile_w[t];
-#pragma unroll 4
-    for (int j = 0; j < w; ++j) {
-        const int l = __ldg(row + j * T);
+    const R inv_h = A.inv_h, kcoef = A.kcoef;
+    for_each_neighbour(row, T, w, [&](int l) {
         R xb[P], ub[P];
         ld_vec<R, P>(xb, sX + l * P);
         ld_vec<R, P>(ub, sU + l * P);
@@ -98,15 +118,15 @@ __device__ __forceinline__ void compute_F(const Args<R> &A, const R *sX, const R
             d[k] = xa[k] - xb[k];
             r2 += d[k] * d[k];
         }
-        const R tt = R(1) - R(0.5) * nsqrt(r2) * A.inv_h;
-        const R f = A.kcoef * tt * tt * tt;   // V W'(r)/r
+        const R tt = R(1) - R(0.5) * nsqrt(r2) * inv_h;
+        const R f = kcoef * tt * tt * tt;   // V W'(r)/r
 #pragma unroll
         for (int r = 0; r < D; ++r) {
             const R du = (ub[r] - ua[r]) * f;
 #pragma unroll
             for (int c = 0; c < D; ++c) G[r][c] += du * d[c];
         }
-    }
+    });
     R B[D][D];
     ldg_mat<R, D>(B, A.B0 + i * MatS<D>::v);
 #pragma unroll
@@ -206,9 +226,8 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
         const int T = A.T;
         const uint16_t *row = A.lell + A.lell_off[t] + threadIdx.x;
         const int w = A.tile_w[t];
-#pragma unroll 4
-        for (int j = 0; j < w; ++j) {
-            const int l = __ldg(row + j * T);
+        const R inv_h = A.inv_h, kcoef = A.kcoef;
+        for_each_neighbour(row, T, w, [&](int l) {
             R xb[P];
             ld_vec<R, P>(xb, sX + l * P);
             R d[D], r2 = R(0);
@@ -217,8 +236,8 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
                 d[k] = xa[k] - xb[k];
                 r2 += d[k] * d[k];
             }
-            const R tt = R(1) - R(0.5) * nsqrt(r2) * A.inv_h;
-            const R f = A.kcoef * tt * tt * tt;
+            const R tt = R(1) - R(0.5) * nsqrt(r2) * inv_h;
+            const R f = kcoef * tt * tt * tt;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 d[k] *= f;
@@ -237,7 +256,7 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
                     acc[r] += q[0] * d[0] + q[1] * d[1] + q[2] * d[2];
                 }
             }
-        }
+        });
 #pragma unroll
         for (int r = 0; r < D; ++r)
 #pragma unroll
@@ -312,24 +331,28 @@ __device__ __forceinline__ void damp_pair(uint32_t ab, R x, R *sv, const uint8_t
     R va[P], vb[P];
     ld_vec<R, P>(va, sv + la * P);
     ld_vec<R, P>(vb, sv + lb * P);
+    const R xm = x * im;
+    const R f2 = fast_div<R>(xm, R(1) + R(2) * xm);   // both free
     if (!(ab & kPairFixBit)) {
-        const R xm = x * im;
-        const R f = fast_div<R>(xm, R(1) + R(2) * xm);
 #pragma unroll
         for (int q = 0; q < D; ++q) {
             const R w = va[q] - vb[q];
-            va[q] -= f * w;
-            vb[q] += f * w;
+            va[q] -= f2 * w;
+            vb[q] += f2 * w;
         }
     } else {
+        // on an axis where one particle is constrained (1/m = 0) the update of
+        // the free one is x/m / (1 + x/m) w; a constrained one does not move
+        const R f1 = fast_div<R>(xm, R(1) + xm);
         const uint8_t fa = sf[la], fb = sf[lb];
 #pragma unroll
         for (int q = 0; q < D; ++q) {
-            const R ia = ((fa >> q) & 1) ? R(0) : im;
-            const R ib = ((fb >> q) & 1) ? R(0) : im;
-            const R wn = (va[q] - vb[q]) / (R(1) + x * (ia + ib));
-            va[q] -= x * wn * ia;
-            vb[q] += x * wn * ib;
+            const bool a_free = !((fa >> q) & 1), b_free = !((fb >> q) & 1);
+            const R ca = a_free ? (b_free ? f2 : f1) : R(0);
+            const R cb = b_free ? (a_free ? f2 : f1) : R(0);
+            const R w = va[q] - vb[q];
+            va[q] -= ca * w;
+            vb[q] += cb * w;
         }
     }
     st_vec<R, P>(sv + la * P, va);
