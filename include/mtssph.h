@@ -155,7 +155,9 @@ typedef struct {
     double ke_ref;           /* reference energy (mode 0) or energy density (mode 1)    */
     int64_t max_substeps;    /* cap on substeps (>= 1); reaching it is not an error     */
     int32_t ke_mode;         /* 0: total E_k; 1: E_k per unit volume                    */
-    int32_t check_every;     /* substeps per host check of the stop flag (>= 1)         */
+    int32_t check_every;     /* 0: the loop runs on the device (CUDA graph WHILE node);  */
+                             /* k >= 1: graph chunks of k substeps, stop flag read by   */
+                             /* the host after each chunk                               */
     int32_t force_dt;        /* 1: accept dt_slow above the stable diffusion limit      */
     int32_t reserved;
 } mts_step_params;
@@ -181,8 +183,9 @@ typedef struct {
  * E_k <= ke_tol * ke_ref or max_substeps.  The substep size follows
  * Sec. 4.1: dt0 = 0.6 h / c_s, then 0.6 min(h / (c_s + |v|max),
  * sqrt(h / |dv/dt|max)) with c_s = sqrt(K / rho0).  The stop flag lives on the
- * device; the host checks it every check_every substeps, so the substep count
- * is exact.  Errors: MTS_ERR_UNSTABLE_DT, MTS_ERR_NONFINITE (report.status
+ * device; with check_every = 0 a conditional WHILE graph node runs exactly the
+ * substeps needed, otherwise the host checks the flag every check_every
+ * substeps (kernels after the stop return at once, so the count is exact).  Errors: MTS_ERR_UNSTABLE_DT, MTS_ERR_NONFINITE (report.status
  * says so too), MTS_ERR_STATE (no material set). */
 mts_status mts_advance_slow_step(mts_body *body, const mts_step_params *params,
                                  mts_step_report *report);

@@ -159,8 +159,69 @@ mts_status get_rank_host(mts_body *b, std::vector<long long> &rank) {
     return MTS_OK;
 }
 
+// The inner loop as a conditional WHILE node whose body is one substep; the
+// drift kernel's last block sets the condition to "not done".  No host round
+// trip and no work after the stop.  (Event-record nodes are not allowed in a
+// conditional body, so profiled runs use capture_chunk instead.)
+mts_status capture_loop(mts_body *b) {
+    if (b->graph && !b->graph_dirty && b->graph_is_loop) return MTS_OK;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    MTS_TRY(prepare_kernels(b));
+    cudaStream_t st = b->ctx->stream;
+    cudaGraph_t g = nullptr;
+    MTS_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e, "cudaGraphConditionalHandleCreate");
+    }
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e, "cudaGraphAddNode(conditional)");
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e, "cudaStreamBeginCaptureToGraph");
+    }
+    b->cond = h;
+    b->use_cond = 1;
+    long long ndamp = 0;
+    mts_status s = launch_stress(b);
+    if (s == MTS_OK) s = launch_force(b);
+    if (s == MTS_OK) s = launch_damping(b, &ndamp);
+    if (s == MTS_OK) s = launch_drift(b);
+    b->use_cond = 0;
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(st, &captured);
+    if (s != MTS_OK || e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return s != MTS_OK ? s : cuda_fail(e, "cudaStreamEndCapture");
+    }
+    b->launches_per_substep = 3 + ndamp;
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(loop)");
+    b->graph_is_loop = true;
+    b->graph_prof_stage = 0;
+    b->graph_dirty = false;
+    return MTS_OK;
+}
+
 mts_status capture_chunk(mts_body *b, int chunk) {
-    if (b->graph && !b->graph_dirty && b->graph_chunk == chunk &&
+    if (b->graph && !b->graph_dirty && !b->graph_is_loop && b->graph_chunk == chunk &&
         b->graph_prof_stage == b->prof_stage)
         return MTS_OK;
     if (b->graph) {
@@ -214,6 +275,7 @@ mts_status capture_chunk(mts_body *b, int chunk) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     b->graph_chunk = chunk;
     b->graph_prof_stage = ps;
+    b->graph_is_loop = false;
     b->graph_dirty = false;
     return MTS_OK;
 }
@@ -329,7 +391,8 @@ mts_status mts_body_create(mts_ctx *ctx, const mts_body_desc *desc, mts_body **o
     A((void **)&b->flags, n);
     A((void **)&b->ctrl, sizeof(Control));
     const long long grid = (n + kBlock - 1) / kBlock;
-    A((void **)&b->part_force, grid * 4 * 8);
+    // one force partial per tile: tiles hold at least 64 particles
+    A((void **)&b->part_force, ((n + 63) / 64) * 4 * 8);
     A((void **)&b->part_drift, grid * 2 * 8);
     A((void **)&b->scratch, (size_t)n * 18 * 8);
     if (s == MTS_OK && cudaMallocHost((void **)&b->h_ctrl, sizeof(Control)) != cudaSuccess) {
@@ -607,12 +670,20 @@ mts_status mts_advance_slow_step(mts_body *b, const mts_step_params *p, mts_step
         MTS_TRY(launch_diffusion(b, p->dt_slow));
         launches += 2;
     }
-    const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 32, 4096));
-    MTS_TRY(capture_chunk(b, chunk));
     long long done_before = 0;
     double prof_ms = 0.0;
     long long prof_n = 0;
-    for (;;) {
+    if (b->prof_stage == 0 && p->check_every <= 0) {
+        // device-side loop: one graph launch runs substeps until the stop flag
+        MTS_TRY(capture_loop(b));
+        MTS_CUDA(cudaGraphLaunch(b->graph, st));
+        MTS_CUDA(cudaMemcpyAsync(b->h_ctrl, b->ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+        MTS_CUDA(cudaStreamSynchronize(st));
+        launches += b->h_ctrl->nsub * b->launches_per_substep;
+    }
+    const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 32, 4096));
+    if (b->prof_stage > 0 || p->check_every > 0) MTS_TRY(capture_chunk(b, chunk));
+    for (; b->prof_stage > 0 || p->check_every > 0;) {
         MTS_CUDA(cudaGraphLaunch(b->graph, st));
         launches += chunk * b->launches_per_substep;
         MTS_CUDA(cudaMemcpyAsync(b->h_ctrl, b->ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));

@@ -32,7 +32,7 @@ constexpr int kFixMask = 7;
 constexpr int kForceBit = 8;
 constexpr int kTipBit = 16;
 constexpr int kCHeldBit = 32;
-constexpr int kBlock = 128;  // threads per block of the per-particle kernels
+constexpr int kBlock = 256;  // threads per block of the per-particle kernels
 constexpr int kLevelCap = 32;  // pairs per damping level: one warp-wide pass
 
 // ------------------------------------------------------------------ errors
@@ -118,6 +118,10 @@ struct Args {
     const uint16_t *lell;        // local neighbour slots, neighbour-major per tile
     const long long *lell_off;   // tile -> first local ELL entry
     const int32_t *tile_w;       // tile -> ELL width
+    // device loop control: inside a conditional WHILE graph node the drift
+    // kernel sets the node's condition to "not done"
+    cudaGraphConditionalHandle cond;
+    int use_cond;
     // reductions
     Control *ctrl;
     double *part_force;          // grid x 4 (amax, m a_x, m a_y, m a_z)
@@ -208,6 +212,9 @@ struct mts_body {
     int tip_count;
     int prof_stage;
     int graph_prof_stage;
+    bool graph_is_loop;           // conditional WHILE graph (one substep per iteration)
+    cudaGraphConditionalHandle cond;
+    int use_cond;
     std::vector<cudaEvent_t> prof_ev;   // 2 per substep of a chunk
     long long launches_per_substep;
 };

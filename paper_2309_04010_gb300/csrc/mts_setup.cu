@@ -625,6 +625,10 @@ mts_status to_host(T *h, const T *d, size_t count, cudaStream_t st) {
 }
 
 mts_status build_tiles(mts_body *b, Tmp &tmp, cudaStream_t st, int T) {
+    if (T < 64 || T > 256) {   // the force partials buffer holds one slot per 64 particles
+        set_error("tile size %d outside [64, 256]", T);
+        return MTS_ERR_STATE;
+    }
     mts_ctx *ctx = b->ctx;
     const long long n = b->n;
     const long long ntiles = (n + T - 1) / T;

@@ -441,7 +441,11 @@ __global__ void k_pair_fixbits(uint32_t *ab, const int32_t *pa, const int32_t *p
 template <class R, int D>
 __global__ void __launch_bounds__(kBlock) k_drift(Args<R> A) {
     Control *C = A.ctrl;
-    if (C->done) return;
+    if (C->done) {
+        // defensive: a loop iteration that starts after the stop ends the loop
+        if (A.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(A.cond, 0u);
+        return;
+    }
     constexpr int P = Pad<D>::v;
     const long long i = blockIdx.x * (long long)kBlock + threadIdx.x;
     double ke = 0.0, vmax = 0.0;
@@ -498,15 +502,39 @@ __global__ void __launch_bounds__(kBlock) k_drift(Args<R> A) {
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    // last block: fixed-order reduction of every block's partials
+    // last block: fixed-order reduction of every block's partials (loads
+    // issued four at a time, accumulated in a fixed order)
     double s_ke = 0, s_v = 0, s_a = 0, s_f[3] = {0, 0, 0};
-    for (unsigned q = threadIdx.x; q < gridDim.x; q += kBlock) {
-        s_ke += __ldcg(A.part_drift + q * 2);
-        s_v = fmax(s_v, __ldcg(A.part_drift + q * 2 + 1));
+    for (unsigned q0 = threadIdx.x; q0 < gridDim.x; q0 += 4 * kBlock) {
+        double2 t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned q = q0 + u * kBlock;
+            t[u] = q < gridDim.x ? __ldcg(reinterpret_cast<const double2 *>(A.part_drift) + q)
+                                 : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            s_ke += t[u].x;
+            s_v = fmax(s_v, t[u].y);
+        }
     }
-    for (long long q = threadIdx.x; q < A.ntiles; q += kBlock) {   // one partial per force CTA
-        s_a = fmax(s_a, __ldcg(A.part_force + q * 4));
-        for (int k = 0; k < 3; ++k) s_f[k] += __ldcg(A.part_force + q * 4 + 1 + k);
+    for (long long q0 = threadIdx.x; q0 < A.ntiles; q0 += 4 * kBlock) {   // one partial per force CTA
+        double2 t[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long q = q0 + u * kBlock;
+            const double2 z = make_double2(0.0, 0.0);
+            t[u][0] = q < A.ntiles ? __ldcg(reinterpret_cast<const double2 *>(A.part_force) + 2 * q) : z;
+            t[u][1] = q < A.ntiles ? __ldcg(reinterpret_cast<const double2 *>(A.part_force) + 2 * q + 1) : z;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            s_a = fmax(s_a, t[u][0].x);
+            s_f[0] += t[u][0].y;
+            s_f[1] += t[u][1].x;
+            s_f[2] += t[u][1].y;
+        }
     }
     __shared__ double red[6][kBlock];
     red[0][threadIdx.x] = s_ke; red[1][threadIdx.x] = s_v; red[2][threadIdx.x] = s_a;
@@ -550,6 +578,7 @@ __global__ void __launch_bounds__(kBlock) k_drift(Args<R> A) {
             C->dt = 0.6 * fmin(t1, t2);
         }
         C->counter = 0;
+        if (A.use_cond) cudaGraphSetConditional(A.cond, C->done ? 0u : 1u);
     }
 }
 
@@ -820,6 +849,8 @@ Args<R> make_args(mts_body *b) {
     A.touch_start = b->touch_start;
     A.touch_cnt = b->touch_cnt;
     A.mb = b->mb;
+    A.cond = b->cond;
+    A.use_cond = b->use_cond;
     A.ctrl = b->ctrl;
     A.part_force = b->part_force;
     A.part_drift = b->part_drift;

@@ -286,7 +286,7 @@ class Body:
     # -- stepping
     def advance_slow_step(self, dt_slow: float = 0.0, ramp: float = 0.0, ke_tol: float = -1.0,
                           ke_ref: float = 1.0, ke_mode: int = 0, max_substeps: int = 1,
-                          dt_sub: float = 0.0, check_every: int = 32,
+                          dt_sub: float = 0.0, check_every: int = 0,
                           force_dt: bool = False) -> StepReport:
         p = StepParams(dt_slow, ramp, dt_sub, ke_tol, ke_ref, max_substeps, ke_mode,
                        check_every, int(force_dt), 0)

@@ -158,6 +158,17 @@ def _run_both(ctx, case, nslow, nsub, precision=M.FP64, ke_tol=-1.0, dt_slow=0.0
     return ob, gb, reps
 
 
+def test_device_loop_counts_and_launches(ctx):
+    case = B.bar2d(nx=30, ny=8)
+    gb = M.body_from_case(ctx, case)
+    r = gb.advance_slow_step(ramp=0.05, ke_tol=-1, max_substeps=37)          # device loop
+    assert r.substeps == 37 and r.converged == 0
+    per = (r.kernel_launches - 2 - 2) // 37                 # minus load/reset and tip kernels
+    assert per >= 4 and (r.kernel_launches - 4) % 37 == 0
+    r2 = gb.advance_slow_step(ramp=0.05, ke_tol=-1, max_substeps=37, check_every=8)
+    assert r2.substeps == 37 and r2.kernel_launches == 4 + 40 * per   # 5 chunks of 8
+
+
 def test_fp64_slow_steps_bar2d(ctx):
     ob, gb, reps = _run_both(ctx, B.bar2d(), 3, 300)
     assert rel(gb.read(M.F_U), ob.read(O.F_U)) < 1e-9
@@ -178,12 +189,13 @@ def test_fp64_slow_steps_j2_cylinder(ctx):
     assert rel(gb.read(M.F_ALPHA), ob.read(O.F_ALPHA)) < 1e-9
 
 
-def test_kinetic_energy_stop_matches_oracle(ctx):
+@pytest.mark.parametrize("check_every", [0, 64])    # device WHILE loop / host-checked chunks
+def test_kinetic_energy_stop_matches_oracle(ctx, check_every):
     case = B.bar2d(nx=40, ny=10)
     ob, gb = pair(ctx, case)
     for l in (1, 2):
         rg = gb.advance_slow_step(ramp=l / 20, ke_tol=1e-4, ke_ref=case.plan.ke_ref,
-                                  max_substeps=100000, check_every=64)
+                                  max_substeps=100000, check_every=check_every)
         ro = ob.advance(ramp=l / 20, ke_tol=1e-4, ke_ref=case.plan.ke_ref, max_substeps=100000)
         assert rg.converged == ro.converged == 1
         assert rg.substeps == ro.substeps
