@@ -382,20 +382,38 @@ static int build_b0(ob_body *b) {
 /*   block = cell >> blk_shift per axis (B = 2^blk_shift cells, B*dx    */
 /*   > 2h); pair (a<b) is owned by the componentwise-min block of its   */
 /*   two particles; block colour = parity bits of the owner block;      */
-/*   inside an owner block its pairs, in ascending (a,b), take the      */
+/*   inside an owner block its pairs, visited by offset class (the      */
+/*   sign-folded cell offset) and then ascending (a,b), take the        */
 /*   smallest sub-colour unused at a and at b that holds fewer than 32  */
 /*   pairs so far (greedy, capped level size).  Sequential              */
 /*   order: colour, owner block Morton key, sub-colour, a, b.  Pairs of */
 /*   one (colour, sub-colour) touch disjoint particles.                 */
 /* ------------------------------------------------------------------ */
-typedef struct { int32_t col; int32_t sub; uint64_t key; int32_t a, b; } pair_rec;
+typedef struct { int32_t col; int32_t sub; uint64_t key; int32_t cls; int32_t a, b; } pair_rec;
 
+/* owner block, then offset class, then (a, b): the order the greedy visits */
 static int cmp_pair_owner(const void *x, const void *y) {
     const pair_rec *p = x, *q = y;
     if (p->col != q->col) return p->col < q->col ? -1 : 1;
     if (p->key != q->key) return p->key < q->key ? -1 : 1;
+    if (p->cls != q->cls) return p->cls < q->cls ? -1 : 1;
     if (p->a != q->a) return p->a < q->a ? -1 : 1;
     return (p->b > q->b) - (p->b < q->b);
+}
+
+/* offset class of a pair: the cell offset o = cell(b) - cell(a), sign-folded so
+ * that o and -o fall in one class (first nonzero component positive), encoded
+ * as a base-(2R+1) number with R = floor(2h/dx) + 1 */
+static int32_t offset_class(const ob_body *b, int64_t a, int64_t j) {
+    int64_t o[3] = {0, 0, 0};
+    for (int k = 0; k < b->dim; k++) o[k] = b->cell[3 * j + k] - b->cell[3 * a + k];
+    int sgn = 0;
+    for (int k = b->dim - 1; k >= 0 && sgn == 0; k--)
+        if (o[k] != 0) sgn = o[k] > 0 ? 1 : -1;
+    int64_t R = (int64_t)floor(2.0 * b->h / b->dx) + 1, base = 2 * R + 1;
+    int64_t c = 0;
+    for (int k = b->dim - 1; k >= 0; k--) c = c * base + (sgn * o[k] + R);
+    return (int32_t)c;
 }
 static int cmp_pair_final(const void *x, const void *y) {
     const pair_rec *p = x, *q = y;
@@ -428,6 +446,7 @@ static int build_colouring(ob_body *b) {
             }
             pr[m].col = col;
             pr[m].key = morton_key(d, ob);
+            pr[m].cls = offset_class(b, a, j);
             pr[m].a = (int32_t)a;
             pr[m].b = (int32_t)j;
             pr[m].sub = 0;

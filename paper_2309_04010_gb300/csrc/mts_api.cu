@@ -89,7 +89,8 @@ void body_free(mts_body *b) {
                      (void **)&b->flags, (void **)&b->ctrl, (void **)&b->part_force,
                      (void **)&b->part_drift, (void **)&b->scratch, (void **)&b->halo_off,
                      (void **)&b->halo_idx, (void **)&b->lself, (void **)&b->lell,
-                     (void **)&b->lell_off, (void **)&b->tile_w};
+                     (void **)&b->lell_off, (void **)&b->tile_w, (void **)&b->pair_slot,
+                     (void **)&b->kpad_ab, (void **)&b->kpad_g};
     for (void **pp : ptrs) {
         dfree(b->ctx, *pp);
         *pp = nullptr;

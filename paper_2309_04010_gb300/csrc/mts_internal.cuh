@@ -99,7 +99,7 @@ struct Args {
     double mass, h, cs;
     // damping
     R eta;
-    const uint32_t *pair_ab;
+    const uint32_t *pair_ab;     // padded: level L in slots [32 L, 32 L + 32)
     const R *pair_g;
     const long long *lvl_pair;   // level -> first pair, total_levels + 1
     const int32_t *grp_lvl;      // group -> first level, n_groups + 1
@@ -164,6 +164,9 @@ struct mts_body {
 
     // canonical damping order
     long long npairs;
+    long long *pair_slot;     // slot of each canonical pair in the padded layout
+    uint32_t *kpad_ab;        // padded per-level pair words (32 slots per level)
+    void *kpad_g;             // padded per-level pair coefficients
     int32_t *pair_a, *pair_b, *pair_col, *pair_sub;
     long long *pair_key;
     uint32_t *pair_ab;

@@ -417,6 +417,50 @@ __global__ void k_greedy(const long long *gstart, long long g0, long long g1, lo
     nsub[g] = maxc + 1;
 }
 
+// offset class: cell(b) - cell(a), sign-folded, base (2R+1) digits
+__global__ void k_pair_class(const int32_t *pa, const int32_t *pb, const long long *gscan,
+                             long long m, const int *cell, int dim, int R,
+                             unsigned long long *key) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    long long o[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k)
+        o[k] = (long long)cell[(long long)pb[p] * 3 + k] - cell[(long long)pa[p] * 3 + k];
+    int sg = 0;
+    for (int k = dim - 1; k >= 0 && sg == 0; --k)
+        if (o[k] != 0) sg = o[k] > 0 ? 1 : -1;
+    long long c = 0, base = 2 * R + 1;
+    for (int k = dim - 1; k >= 0; --k) c = c * base + (sg * o[k] + R);
+    key[p] = ((unsigned long long)(gscan[p] - 1) << 16) | (unsigned long long)c;
+}
+
+template <class T>
+__global__ void k_scatter(const T *src, const long long *order, long long m, T *dst) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p < m) dst[order[p]] = src[p];
+}
+
+// padded kernel layout: level L of the canonical order occupies slots
+// [32 L, 32 L + 32); pair p sits at slot 32 L + (p - first pair of L)
+__global__ void k_fill_slots(const unsigned long long *key2s, long long m, const int32_t *grp_lvl,
+                             const long long *lvl_pair, const uint32_t *ab, long long *slot,
+                             uint32_t *kab) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    const long long g = (long long)(key2s[p] >> 8);
+    const int s = (int)(key2s[p] & 255);
+    const long long L = grp_lvl[g] + s;
+    const long long sl = 32 * L + (p - lvl_pair[L]);
+    slot[p] = sl;
+    kab[sl] = ab[p];
+}
+
+template <class R>
+__global__ void k_fill_slot_g(const R *g, const long long *slot, long long m, R *kg) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p < m) kg[slot[p]] = g[p];
+}
+
 __global__ void k_group_of_pair(const long long *gscan, long long m, const int32_t *sub,
                                 unsigned long long *key2) {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -854,10 +898,30 @@ mts_status build_typed(mts_body *b, const double *hX) {
     k_touch<<<grid_for(ng), TPB, 0, st>>>(gstart, ng, pa1, pb1, cell, D, b->blk_shift, bkey, bstart,
                                            bcnt, nblocks, b->touch_start, b->touch_cnt, gcol, gkey);
 
+    // visit order of the greedy: owner group, offset class, then (a, b)
+    const int Rr = (int)std::floor(2.0 * b->h / b->dx) + 1;
+    int32_t *pa2 = tmp.get<int32_t>(mm), *pb2 = tmp.get<int32_t>(mm);
+    long long *ord3 = tmp.get<long long>(mm);
+    NEED(pa2); NEED(pb2); NEED(ord3);
+    {
+        unsigned long long *k3 = tmp.get<unsigned long long>(mm), *k3s = tmp.get<unsigned long long>(mm);
+        long long *io = tmp.get<long long>(mm);
+        NEED(k3); NEED(k3s); NEED(io);
+        k_pair_class<<<grid_for(m), TPB, 0, st>>>(pa1, pb1, gscan, m, cell, D, Rr, k3);
+        k_iota<<<grid_for(m), TPB, 0, st>>>(io, m);
+        int gb3 = 1;
+        while ((1LL << gb3) <= ng) ++gb3;
+        MTS_TRY(cub_sort_pairs(tmp, k3, k3s, io, ord3, m, std::min(64, gb3 + 16), st));
+        k_gather<<<grid_for(m), TPB, 0, st>>>(pa1, ord3, m, pa2);
+        k_gather<<<grid_for(m), TPB, 0, st>>>(pb1, ord3, m, pb2);
+    }
+
     // greedy sub-colours, in batches of groups to bound the bitmask scratch
     int32_t *sub0 = tmp.get<int32_t>(mm), *nsub = tmp.get<int32_t>(ngg + 1);
     uint32_t *ab0 = tmp.get<uint32_t>(mm);
-    NEED(sub0); NEED(nsub); NEED(ab0);
+    int32_t *subc = tmp.get<int32_t>(mm);
+    uint32_t *abc = tmp.get<uint32_t>(mm);
+    NEED(sub0); NEED(nsub); NEED(ab0); NEED(subc); NEED(abc);
     long long per_group = (long long)nbk * b->mb * 4;   // 64-bit words
     long long batch = std::max(1LL, std::min(ng, (1LL << 25) / std::max(per_group, 1LL)));
     unsigned long long *used = tmp.get<unsigned long long>(batch * per_group + 1);
@@ -865,10 +929,14 @@ mts_status build_typed(mts_body *b, const double *hX) {
     for (long long gs = 0; gs < ng; gs += batch) {
         long long ge = std::min(ng, gs + batch);
         MTS_CUDA(cudaMemsetAsync(used, 0, (ge - gs) * per_group * sizeof(unsigned long long), st));
-        k_greedy<<<grid_for(ge - gs, 64), 64, 0, st>>>(gstart, gs, ge, ng, m, pa1, pb1, cell, D,
+        k_greedy<<<grid_for(ge - gs, 64), 64, 0, st>>>(gstart, gs, ge, ng, m, pa2, pb2, cell, D,
                                                          b->blk_shift, b->touch_start, b->mb, used,
-                                                         sub0, ab0, nsub, b->ctrl);
+                                                         subc, abc, nsub, b->ctrl);
     }
+    // back to (group, a, b) order, so that the final stable sort by
+    // (group, sub-colour) lists each level in ascending (a, b)
+    k_scatter<<<grid_for(m), TPB, 0, st>>>(subc, ord3, m, sub0);
+    k_scatter<<<grid_for(m), TPB, 0, st>>>(abc, ord3, m, ab0);
 
     // final canonical order: (group, sub-colour), stable
     unsigned long long *k2 = tmp.get<unsigned long long>(mm), *k2s = tmp.get<unsigned long long>(mm);
@@ -910,6 +978,19 @@ mts_status build_typed(mts_body *b, const double *hX) {
     k_levels<<<grid_for(m + 1), TPB, 0, st>>>(k2s, m, b->grp_lvl, b->lvl_pair, nlev);
     k_pair_coef<R, D><<<grid_for(m), TPB, 0, st>>>(b->pair_a, b->pair_b, m, b->X64, b->h, alpha,
                                                     b->V, (R *)b->pair_g);
+    // padded per-level layout for the damping kernel (32 slots per level)
+    {
+        const long long ns = 32LL * nlev;
+        MTS_TRY(dalloc_t(ctx, &b->pair_slot, mm));
+        MTS_TRY(dalloc_t(ctx, &b->kpad_ab, std::max(ns, 4LL)));
+        MTS_TRY(dalloc_into(ctx, &b->kpad_g, std::max(ns, 4LL) * sizeof(R) + 16));
+        MTS_CUDA(cudaMemsetAsync(b->kpad_ab, 0xff, std::max(ns, 4LL) * sizeof(uint32_t), st));
+        MTS_CUDA(cudaMemsetAsync(b->kpad_g, 0, std::max(ns, 4LL) * sizeof(R), st));
+        k_fill_slots<<<grid_for(m), TPB, 0, st>>>(k2s, m, b->grp_lvl, b->lvl_pair, b->pair_ab,
+                                                  b->pair_slot, b->kpad_ab);
+        k_fill_slot_g<R><<<grid_for(m), TPB, 0, st>>>((const R *)b->pair_g, b->pair_slot, m,
+                                                       (R *)b->kpad_g);
+    }
     int *dcol = tmp.get<int>(16);
     NEED(dcol);
     k_col_off<<<grid_for(ng + 1), TPB, 0, st>>>(gcol, ng, nbk, dcol);

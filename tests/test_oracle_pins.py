@@ -132,6 +132,12 @@ def test_colour_stages_are_matchings(dim, counts):
     # one owner block's level holds at most 32 pairs (one warp-wide pass)
     _, counts = np.unique(np.stack([col, key, sub]), axis=1, return_counts=True)
     assert counts.max() <= 32
+    # visiting the pairs by offset class keeps the level count near the degree
+    nlev = {}
+    for c, k, s_ in zip(col, key, sub):
+        nlev[(c, k)] = max(nlev.get((c, k), 0), s_ + 1)
+    deg = np.diff(off).max()
+    assert max(nlev.values()) <= deg + 12
     assert len(np.unique(col)) <= 2 ** dim
 
 
@@ -687,14 +693,26 @@ def test_colouring_matches_independent_greedy(dim, counts):
                 key |= ((int(c[k]) >> bit) & 1) << (bit * dim + k)
         return key
 
+    R = int(math.floor(2 * 1.3)) + 1
+
+    def oclass(a, b):
+        o = cell[b] - cell[a]
+        nz = [int(x) for x in o[::-1] if x != 0]      # first nonzero from the top axis
+        sg = 1 if (not nz or nz[0] > 0) else -1
+        c = 0
+        for k in range(dim - 1, -1, -1):
+            c = c * (2 * R + 1) + (sg * int(o[k]) + R)
+        return c
+
     recs = []
     for a in range(len(Xs)):
         for b in idx[off[a]:off[a + 1]]:
             if b > a:
                 owner = np.minimum(blk[a], blk[b])
                 col = sum(int(owner[k] & 1) << k for k in range(dim))
-                recs.append([col, mkey(owner), a, int(b)])
+                recs.append([col, mkey(owner), oclass(a, int(b)), a, int(b)])
     recs.sort()
+    recs = [[r[0], r[1], r[3], r[4]] for r in recs]
     used = {}
     count = {}
     subs = []
