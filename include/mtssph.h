@@ -221,6 +221,38 @@ typedef enum {
 mts_status mts_read_field(mts_body *body, int32_t field, double *host_out, int64_t len);
 mts_status mts_write_field(mts_body *body, int32_t field, const double *host_in, int64_t len);
 
+/* ------------------------------------------------------------------ */
+/* Allocation-free reduction                                            */
+/* ------------------------------------------------------------------ */
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory where they need the result: code whose device
+ * memory is entirely owned by another allocator (a framework's caching
+ * allocator or a fixed arena), code on a latency-critical path that cannot
+ * afford the device-wide synchronisation of cudaMalloc/cudaFree, and code that
+ * must not be able to fail with out-of-memory after set-up.
+ *
+ * Computes E_k = sum_i 1/2 mass |v_i|^2 and max_i |v_i| (FP64 accumulation,
+ * the reduction the slow-step driver applies after every substep).
+ *   v_dev   device, n x dim contiguous velocities: float for MTS_MIXED,
+ *           double for MTS_FP64 (caller-owned, read only)
+ *   out_dev device, 2 doubles (caller-owned): out_dev[0] = E_k, out_dev[1] = max |v|
+ *   stream  cudaStream_t to order the work on (NULL: the default stream); the
+ *           call returns without waiting for the result.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocator of any library.  Its
+ * only working memory is a fixed 16 KiB array of 1,024 block partials in this
+ * library's static device memory, present on every GPU that loads the library
+ * until the process exits.  The first call on each device looks that array's
+ * device address up (with the device current), so make the first call on a
+ * device before any stream capture on it.  All calls share the array and every
+ * call overwrites the partials it reads, so two calls that overlap on the GPU
+ * (for example on two streams) race and give wrong results.
+ * Errors: MTS_ERR_INVALID_ARG for NULL pointers, an unsupported precision or
+ * dim, n outside [1, MTS_NOALLOC_MAX_N], or a negative/non-finite mass;
+ * MTS_ERR_CUDA if a launch fails. */
+#define MTS_NOALLOC_MAX_N 2147483647LL
+mts_status mts_kinetic_energy_noalloc(const void *v_dev, int32_t precision, int32_t dim, int64_t n,
+                                      double mass, double *out_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

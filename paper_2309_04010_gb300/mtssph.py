@@ -116,6 +116,7 @@ def lib():
         "mts_set_profiling": [vp, i32],
         "mts_read_field": [vp, i32, vp, i64],
         "mts_write_field": [vp, i32, vp, i64],
+        "mts_kinetic_energy_noalloc": [vp, i32, i32, i64, d, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -334,3 +335,12 @@ def body_from_case(ctx: Context, case, precision: int = FP64) -> Body:
     if case.tip_ids is not None and len(case.tip_ids):
         b.set_tip(case.tip_ids)
     return b
+
+
+def kinetic_energy_noalloc(v_dev_ptr: int, precision: int, dim: int, n: int, mass: float,
+                           out_dev_ptr: int, stream: int = 0) -> None:
+    """mts_kinetic_energy_noalloc on caller-owned device buffers (no allocation):
+    out[0] = sum 1/2 mass |v|^2, out[1] = max |v|, ordered on `stream`."""
+    _check(lib().mts_kinetic_energy_noalloc(C.c_void_p(v_dev_ptr), precision, dim, n, mass,
+                                            C.c_void_p(out_dev_ptr), C.c_void_p(stream)),
+           "mts_kinetic_energy_noalloc")
