@@ -442,9 +442,11 @@ __global__ void k_scatter(const T *src, const long long *order, long long m, T *
 
 // padded kernel layout: level L of the canonical order occupies slots
 // [32 L, 32 L + 32); pair p sits at slot 32 L + (p - first pair of L)
+// slot words hold byte offsets (slot index * bytes per velocity slot) of the
+// two particles in the damping kernel's staged velocities
 __global__ void k_fill_slots(const unsigned long long *key2s, long long m, const int32_t *grp_lvl,
                              const long long *lvl_pair, const uint32_t *ab, long long *slot,
-                             uint32_t *kab) {
+                             uint32_t *kab, int bps) {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= m) return;
     const long long g = (long long)(key2s[p] >> 8);
@@ -452,7 +454,13 @@ __global__ void k_fill_slots(const unsigned long long *key2s, long long m, const
     const long long L = grp_lvl[g] + s;
     const long long sl = 32 * L + (p - lvl_pair[L]);
     slot[p] = sl;
-    kab[sl] = ab[p];
+    const uint32_t la = ab[p] & 0xffffu, lb = ab[p] >> 16;
+    kab[sl] = (la * (uint32_t)bps) | ((lb * (uint32_t)bps) << 16);
+}
+
+__global__ void k_fill_dummy(uint32_t *kab, long long ns, uint32_t dummy) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k < ns) kab[k] = dummy | (dummy << 16);
 }
 
 template <class R>
@@ -984,10 +992,17 @@ mts_status build_typed(mts_body *b, const double *hX) {
         MTS_TRY(dalloc_t(ctx, &b->pair_slot, mm));
         MTS_TRY(dalloc_t(ctx, &b->kpad_ab, std::max(ns, 4LL)));
         MTS_TRY(dalloc_into(ctx, &b->kpad_g, std::max(ns, 4LL) * sizeof(R) + 16));
-        MTS_CUDA(cudaMemsetAsync(b->kpad_ab, 0xff, std::max(ns, 4LL) * sizeof(uint32_t), st));
+        const int bps = Pad<D>::v * (int)sizeof(R);
+        const long long dummy = (long long)(1 << D) * b->mb * bps;   // byte offset of the dummy slot
+        if (dummy > 65535) {
+            set_error("damping blocks too large for 16-bit byte offsets (%d particles)", b->mb);
+            return MTS_ERR_INVALID_ARG;
+        }
+        k_fill_dummy<<<grid_for(std::max(ns, 4LL)), TPB, 0, st>>>(b->kpad_ab, std::max(ns, 4LL),
+                                                                 (uint32_t)dummy);
         MTS_CUDA(cudaMemsetAsync(b->kpad_g, 0, std::max(ns, 4LL) * sizeof(R), st));
         k_fill_slots<<<grid_for(m), TPB, 0, st>>>(k2s, m, b->grp_lvl, b->lvl_pair, b->pair_ab,
-                                                  b->pair_slot, b->kpad_ab);
+                                                  b->pair_slot, b->kpad_ab, bps);
         k_fill_slot_g<R><<<grid_for(m), TPB, 0, st>>>((const R *)b->pair_g, b->pair_slot, m,
                                                        (R *)b->kpad_g);
     }

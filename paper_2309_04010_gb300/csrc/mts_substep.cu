@@ -307,60 +307,68 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
 // level table, the touched particles' flags
 template <class R, int D>
 struct DampSmem {
-    // velocities, 32 slots per level of coefficients and pair words, flags
+    // velocities (+1 dummy slot, padded to 16 bytes), 32 slots per level of
+    // coefficients and pair words (16-byte aligned for cp.async), flags (+1)
+    __host__ __device__ static size_t vbytes(int mb) {
+        return (((size_t)((1 << D) * mb + 1) * Pad<D>::v * sizeof(R)) + 15) & ~size_t(15);
+    }
     __host__ __device__ static size_t bytes(int mb, int maxl) {
-        size_t b = (size_t)(1 << D) * mb * Pad<D>::v * sizeof(R) + (size_t)32 * maxl * sizeof(R) +
-                   (size_t)32 * maxl * 4 + (size_t)(1 << D) * mb;
+        size_t b = vbytes(mb) + (size_t)32 * maxl * sizeof(R) + (size_t)32 * maxl * 4 +
+                   (size_t)(1 << D) * mb + 1;
         return (b + 15) & ~size_t(15);
     }
 };
 
 // One backward-Euler update of the pair ODE m dv_a/dt = -B (v_a - v_b) with
 // x = (dt/2) B: w' = w / (1 + x (1/m_a + 1/m_b)), v_a -= x w' / m_a, v_b += x w' / m_b.
-// Bit 31 of the packed pair word marks a pair with a constrained axis
-// (1/m = 0 on that axis), handled per axis; all other pairs are free-free
-// with equal masses: v_a -= f w, v_b += f w with f = x/m / (1 + 2 x/m).
-constexpr uint32_t kPairFixBit = 0x80000000u;
-
+// Layout of a level slot: the pair word holds the byte offsets of v_a and v_b
+// in the staged velocities (low / high 16 bits); the coefficient g = B/eta is
+// stored negative for a pair with a constrained axis (1/m = 0 on that axis),
+// which takes the per-axis path.  Free-free pairs (equal masses):
+// v_a -= f w, v_b += f w with f = x/m / (1 + 2 x/m).  An empty slot points
+// both offsets at a dummy velocity slot and has g = 0.
 template <class R> __device__ __forceinline__ R fast_div(R a, R b) { return a / b; }
 template <> __device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
 
 template <class R, int D>
-__device__ __forceinline__ void damp_pair(uint32_t ab, R x, R *sv, const uint8_t *sf, R im) {
+__device__ __forceinline__ void damp_pair(uint32_t w, R g, unsigned char *svb, const uint8_t *sf,
+                                          R hcim, R im) {
     constexpr int P = Pad<D>::v;
-    const int la = (int)(ab & 0x7fffu), lb = (int)((ab >> 16) & 0x7fffu);
+    constexpr int BPS = P * (int)sizeof(R);
+    R *pa = reinterpret_cast<R *>(svb + (w & 0xffffu));
+    R *pb = reinterpret_cast<R *>(svb + (w >> 16));
     R va[P], vb[P];
-    ld_vec<R, P>(va, sv + la * P);
-    ld_vec<R, P>(vb, sv + lb * P);
-    const R xm = x * im;
-    const R f2 = fast_div<R>(xm, R(1) + R(2) * xm);   // both free
-    if (!(ab & kPairFixBit)) {
+    ld_vec<R, P>(va, pa);
+    ld_vec<R, P>(vb, pb);
+    if (g >= R(0)) {
+        const R xm = hcim * g;
+        const R f2 = fast_div<R>(xm, R(1) + R(2) * xm);
 #pragma unroll
         for (int q = 0; q < D; ++q) {
-            const R w = va[q] - vb[q];
-            va[q] -= f2 * w;
-            vb[q] += f2 * w;
+            const R d = va[q] - vb[q];
+            va[q] -= f2 * d;
+            vb[q] += f2 * d;
         }
     } else {
-        // on an axis where one particle is constrained (1/m = 0) the update of
-        // the free one is x/m / (1 + x/m) w; a constrained one does not move
+        // on an axis where one particle is constrained the free one moves by
+        // x/m / (1 + x/m) w; a constrained one does not move
+        const R xm = -hcim * g;
+        const R f2 = fast_div<R>(xm, R(1) + R(2) * xm);
         const R f1 = fast_div<R>(xm, R(1) + xm);
-        const uint8_t fa = sf[la], fb = sf[lb];
+        const uint8_t fa = sf[(w & 0xffffu) / BPS], fb = sf[(w >> 16) / BPS];
 #pragma unroll
         for (int q = 0; q < D; ++q) {
             const bool a_free = !((fa >> q) & 1), b_free = !((fb >> q) & 1);
             const R ca = a_free ? (b_free ? f2 : f1) : R(0);
             const R cb = b_free ? (a_free ? f2 : f1) : R(0);
-            const R w = va[q] - vb[q];
-            va[q] -= ca * w;
-            vb[q] += cb * w;
+            const R d = va[q] - vb[q];
+            va[q] -= ca * d;
+            vb[q] += cb * d;
         }
     }
-    st_vec<R, P>(sv + la * P, va);
-    st_vec<R, P>(sv + lb * P, vb);
+    st_vec<R, P>(pa, va);
+    st_vec<R, P>(pb, vb);
 }
-
-constexpr uint32_t kEmptySlot = 0xffffffffu;
 
 template <class R, int D>
 __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long long g_end,
@@ -374,8 +382,8 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     if (g >= g_end) return;
     const int mb = A.mb;
     unsigned char *base = smem + (size_t)warp * DampSmem<R, D>::bytes(mb, A.max_group_levels);
-    R *sv = reinterpret_cast<R *>(base);
-    R *sg = sv + (size_t)NB * mb * P;
+    R *sv = reinterpret_cast<R *>(base);                 // NB * mb slots + 1 dummy slot
+    R *sg = reinterpret_cast<R *>(base + DampSmem<R, D>::vbytes(mb));
     uint32_t *sab = reinterpret_cast<uint32_t *>(sg + 32 * A.max_group_levels);
     uint8_t *sf = reinterpret_cast<uint8_t *>(sab + 32 * A.max_group_levels);
     int ts[NB], tc[NB];
@@ -400,23 +408,43 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
 #pragma unroll
     for (int e = 0; e < NB; ++e)
         for (int t = lane; t < tc[e]; t += 32) sf[e * mb + t] = A.flags[ts[e] + t];
+    if (lane == 0) {
+        sf[NB * mb] = 0;
+        R z[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) z[q] = R(0);
+        st_vec<R, P>(sv + (size_t)NB * mb * P, z);      // dummy slot of the empty level slots
+    }
     cp_async_wait_all();
     __syncwarp();
-    const R hc = (R)(0.5 * A.ctrl->dt) * A.eta;   // dt/2 * eta
     const R im = (R)(1.0 / A.mass);
-    if (mode & 1) {
+    const R hcim = (R)(0.5 * A.ctrl->dt) * A.eta * im;   // (dt/2) eta / m
+    unsigned char *svb = reinterpret_cast<unsigned char *>(sv);
+    if (nl > 0 && (mode & 1)) {
+        uint32_t wn = sab[lane];
+        R gn = sg[lane];
         for (int l = 0; l < nl; ++l) {
-            const int k = 32 * l + lane;
-            const uint32_t ab = sab[k];
-            if (ab != kEmptySlot) damp_pair<R, D>(ab, hc * sg[k], sv, sf, im);
+            const uint32_t w = wn;
+            const R gc = gn;
+            if (l + 1 < nl) {                 // next level's slot, off the v chain
+                wn = sab[32 * (l + 1) + lane];
+                gn = sg[32 * (l + 1) + lane];
+            }
+            damp_pair<R, D>(w, gc, svb, sf, hcim, im);
             __syncwarp();
         }
     }
-    if (mode & 2) {
+    if (nl > 0 && (mode & 2)) {
+        uint32_t wn = sab[32 * (nl - 1) + lane];
+        R gn = sg[32 * (nl - 1) + lane];
         for (int l = nl - 1; l >= 0; --l) {
-            const int k = 32 * l + lane;
-            const uint32_t ab = sab[k];
-            if (ab != kEmptySlot) damp_pair<R, D>(ab, hc * sg[k], sv, sf, im);
+            const uint32_t w = wn;
+            const R gc = gn;
+            if (l > 0) {
+                wn = sab[32 * (l - 1) + lane];
+                gn = sg[32 * (l - 1) + lane];
+            }
+            damp_pair<R, D>(w, gc, svb, sf, hcim, im);
             __syncwarp();
         }
     }
@@ -429,14 +457,16 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
         }
 }
 
-// pair words: set bit 31 when either particle has a constrained axis
-__global__ void k_pair_fixbits(uint32_t *kab, const long long *slot, const int32_t *pa,
-                               const int32_t *pb, long long m, const uint8_t *flags, int fixmask) {
+// pair coefficients: negative when either particle has a constrained axis
+template <class R>
+__global__ void k_pair_fixsign(R *kg, const long long *slot, const int32_t *pa, const int32_t *pb,
+                               long long m, const uint8_t *flags, int fixmask) {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= m) return;
     const bool fix = (flags[pa[p]] | flags[pb[p]]) & fixmask;
-    uint32_t &w = kab[slot[p]];
-    w = fix ? (w | kPairFixBit) : (w & ~kPairFixBit);
+    R &c = kg[slot[p]];
+    const R a = c < R(0) ? -c : c;
+    c = fix ? -a : a;
 }
 
 // --------------------------------------------------------------------- drift
@@ -1023,8 +1053,15 @@ mts_status prepare_kernels(mts_body *b) { return DISPATCH(prepare_t, b); }
 
 mts_status update_pair_fixbits(mts_body *b) {
     if (b->npairs == 0) return MTS_OK;
-    k_pair_fixbits<<<(unsigned)((b->npairs + 255) / 256), 256, 0, b->ctx->stream>>>(
-        b->kpad_ab, b->pair_slot, b->pair_a, b->pair_b, b->npairs, b->flags, (1 << b->dim) - 1);
+    const unsigned grid = (unsigned)((b->npairs + 255) / 256);
+    if (b->precision == MTS_FP64)
+        k_pair_fixsign<double><<<grid, 256, 0, b->ctx->stream>>>(
+            (double *)b->kpad_g, b->pair_slot, b->pair_a, b->pair_b, b->npairs, b->flags,
+            (1 << b->dim) - 1);
+    else
+        k_pair_fixsign<float><<<grid, 256, 0, b->ctx->stream>>>(
+            (float *)b->kpad_g, b->pair_slot, b->pair_a, b->pair_b, b->npairs, b->flags,
+            (1 << b->dim) - 1);
     MTS_CUDA(cudaGetLastError());
     return MTS_OK;
 }
