@@ -77,6 +77,14 @@ int mts_version(void);
 /* neighbour set and the correction matrix B0 are built once in the     */
 /* reference configuration).                                             */
 /* ------------------------------------------------------------------ */
+typedef enum {
+    MTS_DAMP_AUTO = 0,       /* library's choice (reported by mts_body_damping_layout) */
+    MTS_DAMP_BLOCKS = 1,     /* blocks on every axis, one warp per owner block,       */
+                             /* at most 32 pairs per sub-colour                       */
+    MTS_DAMP_WIDE = 2        /* shortest axis unblocked, one CTA per owner block,     */
+                             /* no cap on pairs per sub-colour                        */
+} mts_damp_layout;
+
 typedef struct {
     int32_t dim;             /* 2 (plane strain) or 3                                 */
     int32_t precision;       /* mts_precision                                         */
@@ -84,17 +92,30 @@ typedef struct {
     const double *X;         /* host, n x dim reference positions, copied             */
     double dx;               /* lattice spacing: particle volume dx^dim               */
     double h_over_dx;        /* smoothing length h = h_over_dx * dx, support 2h       */
+    int32_t damp_layout;     /* mts_damp_layout of the pairwise damping order         */
+    int32_t reserved;
 } mts_body_desc;
 
 /* Builds, on the GPU: the Morton order of the particles (cell = floor((X -
  * Xmin)/dx), bit-interleaved key with x lowest, ties by original index), the
  * neighbour CSR (all j != i with |X_i - X_j|^2 < (2h)^2 evaluated in FP64
  * without fused multiply-add, ascending), B0 (Sec. 3.1, correction matrix),
- * and the canonical damping order (owner blocks, colours, greedy
- * sub-colours).  Errors: MTS_ERR_INVALID_ARG (bad desc, non-finite X),
- * MTS_ERR_SINGULAR_B, MTS_ERR_OOM. */
+ * and the canonical damping order: owner blocks (width 2^shift cells per
+ * blocked axis, 2^shift * dx > 2h), pair owner = componentwise-min block of
+ * its particles, colour = parity bits of the owner, and inside an owner block
+ * a greedy sub-colouring that visits pairs by sign-folded cell-offset class
+ * and then (a, b), taking the smallest sub-colour unused at a and b (with room
+ * under the level cap).  Errors: MTS_ERR_INVALID_ARG (bad desc, non-finite
+ * X), MTS_ERR_SINGULAR_B, MTS_ERR_OOM. */
 mts_status mts_body_create(mts_ctx *ctx, const mts_body_desc *desc, mts_body **out);
 void mts_body_destroy(mts_body *body);
+
+/* The damping order's layout (part of its definition, Sec. 4.3 ordering
+ * reading): shift[k] = log2 of the owner-block width in cells on axis k, or
+ * MTS_WHOLE_AXIS when axis k is not blocked; *level_cap = the cap on pairs per
+ * sub-colour of one owner block (0 = none). */
+#define MTS_WHOLE_AXIS 62
+mts_status mts_body_damping_layout(const mts_body *body, int32_t shift[3], int32_t *level_cap);
 
 /* Sorted position -> original index (n entries, host). */
 mts_status mts_body_permutation(const mts_body *body, int64_t *perm);

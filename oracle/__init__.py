@@ -39,6 +39,7 @@ SVK = 0
 J2 = 1
 
 F_U, F_X, F_V, F_DEFGRAD, F_PB, F_C, F_ALPHA, F_CPINV, F_ACC = range(9)
+WHOLE_AXIS = 62
 
 
 class StepParams(C.Structure):
@@ -81,6 +82,8 @@ def lib():
         L.ob_kernel_dwdr.restype = d
         L.ob_kernel_dwdr.argtypes = [C.c_int, d, d]
         L.ob_create.argtypes = [C.c_int, i64, vp, d, d, C.c_int, C.POINTER(vp)]
+        L.ob_create_layout.argtypes = [C.c_int, i64, vp, d, d, C.c_int, vp, C.c_int32,
+                                       C.POINTER(vp)]
         L.ob_destroy.argtypes = [vp]
         L.ob_destroy.restype = None
         for name in ("ob_nnz", "ob_npairs", "ob_n"):
@@ -155,12 +158,20 @@ def stress_point(model: int, rho0: float, E: float, nu: float, F: np.ndarray,
 class OracleBody:
     """A particle body advanced by the FP64 oracle (same calls as the library)."""
 
-    def __init__(self, X: np.ndarray, dx: float, h_over_dx: float = 1.3, brute: bool = False):
+    def __init__(self, X: np.ndarray, dx: float, h_over_dx: float = 1.3, brute: bool = False,
+                 damp_layout=None):
+        """damp_layout = (shifts per axis, level cap) of the damping order; shifts
+        are log2 of the block width in cells, WHOLE_AXIS for an unblocked axis,
+        -1 for the smallest admissible width.  Default: smallest blocks, cap 32."""
         X = np.ascontiguousarray(X, dtype=np.float64)
         self.n, self.dim = X.shape
         h = C.c_void_p()
-        _check(lib().ob_create(self.dim, self.n, _ptr(X), dx, h_over_dx, int(brute),
-                               C.byref(h)), "create")
+        if damp_layout is None:
+            damp_layout = ((-1, -1, -1), 32)
+        shifts = np.ascontiguousarray(list(damp_layout[0]) + [-1] * (3 - len(damp_layout[0])),
+                                      dtype=np.int32)
+        _check(lib().ob_create_layout(self.dim, self.n, _ptr(X), dx, h_over_dx, int(brute),
+                                      _ptr(shifts), int(damp_layout[1]), C.byref(h)), "create")
         self._h = h
 
     def __del__(self):
@@ -278,9 +289,9 @@ class OracleBody:
         return out.reshape(self.n, self.dim, self.dim)
 
 
-def body_from_case(case, brute: bool = False) -> OracleBody:
+def body_from_case(case, brute: bool = False, damp_layout=None) -> OracleBody:
     """Oracle body with the material, damping, diffusion and BCs of a synth Case."""
-    b = OracleBody(case.X, case.dx, case.h_over_dx, brute=brute)
+    b = OracleBody(case.X, case.dx, case.h_over_dx, brute=brute, damp_layout=damp_layout)
     m = case.material
     b.set_material(SVK if m.model == "svk" else J2, m.rho0, m.E, m.nu, m.sigma0, m.sigma_inf,
                    m.delta, m.H)

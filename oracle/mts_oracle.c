@@ -96,7 +96,10 @@ typedef struct {
     int dim;
     int64_t n;
     double dx, h, V, cut2;
-    int blk_shift;           /* damping blocks are 2^blk_shift cells wide */
+    int blk_shift;           /* smallest damping block width (2^blk_shift cells) */
+    int ax_shift[3];         /* damping block width per axis: 2^ax_shift cells;  */
+                             /* OB_WHOLE_AXIS = one block spans the whole axis   */
+    int level_cap;           /* max pairs per sub-colour of a block (0 = none)   */
     double Xmin[3];
     double *X;               /* sorted order, n x 3 (z = 0 in 2D)          */
     int64_t *perm;           /* sorted position -> original index          */
@@ -425,7 +428,7 @@ static int cmp_pair_final(const void *x, const void *y) {
 }
 
 #define OB_MAXSUB 256
-#define OB_LEVEL_CAP 32
+#define OB_WHOLE_AXIS 62
 static int build_colouring(ob_body *b) {
     int d = b->dim;
     int64_t np = b->nnz / 2;
@@ -439,8 +442,8 @@ static int build_colouring(ob_body *b) {
             int64_t ob[3] = {0, 0, 0};
             int col = 0;
             for (int k = 0; k < d; k++) {
-                int64_t ba = b->cell[3 * a + k] >> b->blk_shift;
-                int64_t bb = b->cell[3 * j + k] >> b->blk_shift;
+                int64_t ba = b->cell[3 * a + k] >> b->ax_shift[k];
+                int64_t bb = b->cell[3 * j + k] >> b->ax_shift[k];
                 ob[k] = ba < bb ? ba : bb;
                 col |= (int)(ob[k] & 1) << k;
             }
@@ -468,7 +471,8 @@ static int build_colouring(ob_body *b) {
             uint64_t *ub = used + (size_t)pr[t].b * (OB_MAXSUB / 64);
             int c = 0;
             while (c < OB_MAXSUB &&
-                   ((((ua[c >> 6] | ub[c >> 6]) >> (c & 63)) & 1) || count[c] >= OB_LEVEL_CAP))
+                   ((((ua[c >> 6] | ub[c >> 6]) >> (c & 63)) & 1) ||
+                    (b->level_cap > 0 && count[c] >= b->level_cap)))
                 c++;
             if (c >= OB_MAXSUB) { free(used); free(pr); return OB_ERR_STATE; }
             count[c]++;
@@ -513,9 +517,22 @@ void ob_destroy(ob_body *b) {
     free(b);
 }
 
+/* layout of the damping order: block width per axis as a shift (cells =
+ * 2^shift; OB_WHOLE_AXIS for an unblocked axis; negative = the smallest
+ * power of two >= floor(2h/dx) + 1) and the cap on pairs per sub-colour */
+int ob_create_layout(int dim, int64_t n, const double *Xorig, double dx, double h_over_dx,
+                     int brute, const int32_t ax_shift[3], int32_t level_cap, ob_body **out);
+
 int ob_create(int dim, int64_t n, const double *Xorig, double dx, double h_over_dx,
               int brute, ob_body **out) {
+    const int32_t def[3] = {-1, -1, -1};
+    return ob_create_layout(dim, n, Xorig, dx, h_over_dx, brute, def, 32, out);
+}
+
+int ob_create_layout(int dim, int64_t n, const double *Xorig, double dx, double h_over_dx,
+                     int brute, const int32_t ax_shift[3], int32_t level_cap, ob_body **out) {
     *out = NULL;
+    if (level_cap < 0) return OB_ERR_ARG;
     if ((dim != 2 && dim != 3) || n < 2 || !(dx > 0.0) || !(h_over_dx > 0.0) || n > 2000000000LL)
         return OB_ERR_ARG;
     ob_body *b = calloc(1, sizeof(ob_body));
@@ -529,6 +546,12 @@ int ob_create(int dim, int64_t n, const double *Xorig, double dx, double h_over_
     int64_t need = (int64_t)floor(w / dx) + 1;
     b->blk_shift = 0;
     while ((1LL << b->blk_shift) < need) b->blk_shift++;
+    for (int k = 0; k < 3; k++) {
+        int sh = ax_shift[k] < 0 ? b->blk_shift : ax_shift[k];
+        if (sh < b->blk_shift || sh > OB_WHOLE_AXIS) { free(b); return OB_ERR_ARG; }
+        b->ax_shift[k] = sh;
+    }
+    b->level_cap = level_cap;
     for (int k = 0; k < 3; k++) b->Xmin[k] = 0.0;
     for (int k = 0; k < dim; k++) {
         double mn = Xorig[k];

@@ -90,7 +90,8 @@ void body_free(mts_body *b) {
                      (void **)&b->part_drift, (void **)&b->scratch, (void **)&b->halo_off,
                      (void **)&b->halo_idx, (void **)&b->lself, (void **)&b->lell,
                      (void **)&b->lell_off, (void **)&b->tile_w, (void **)&b->pair_slot,
-                     (void **)&b->kpad_ab, (void **)&b->kpad_g};
+                     (void **)&b->kpad_ab, (void **)&b->kpad_g, (void **)&b->bperm,
+                     (void **)&b->bflags};
     for (void **pp : ptrs) {
         dfree(b->ctx, *pp);
         *pp = nullptr;
@@ -344,9 +345,11 @@ mts_status mts_body_create(mts_ctx *ctx, const mts_body_desc *desc, mts_body **o
     *out = nullptr;
     if ((desc->dim != 2 && desc->dim != 3) || desc->n < 2 || desc->n >= (1LL << 31) ||
         !(desc->dx > 0) || !std::isfinite(desc->dx) || !(desc->h_over_dx > 0) ||
-        !(desc->h_over_dx < 8) || (desc->precision != MTS_FP64 && desc->precision != MTS_MIXED)) {
-        set_error("mts_body_create: invalid descriptor (dim %d, n %lld, dx %g, h/dx %g, precision %d)",
-                  desc->dim, (long long)desc->n, desc->dx, desc->h_over_dx, desc->precision);
+        !(desc->h_over_dx < 8) || (desc->precision != MTS_FP64 && desc->precision != MTS_MIXED) ||
+        desc->damp_layout < MTS_DAMP_AUTO || desc->damp_layout > MTS_DAMP_WIDE) {
+        set_error("mts_body_create: invalid descriptor (dim %d, n %lld, dx %g, h/dx %g, precision %d, "
+                  "damping layout %d)", desc->dim, (long long)desc->n, desc->dx, desc->h_over_dx,
+                  desc->precision, desc->damp_layout);
         return MTS_ERR_INVALID_ARG;
     }
     MTS_CUDA(cudaSetDevice(ctx->device));
@@ -364,6 +367,7 @@ mts_status mts_body_create(mts_ctx *ctx, const mts_body_desc *desc, mts_body **o
     long long need = (long long)std::floor(w / b->dx) + 1;
     b->blk_shift = 0;
     while ((1LL << b->blk_shift) < need) ++b->blk_shift;
+    b->damp_req = desc->damp_layout;
     b->rsize = b->precision == MTS_FP64 ? 8 : 4;
     b->graph_dirty = true;
     const long long n = b->n;
@@ -429,6 +433,16 @@ void mts_body_destroy(mts_body *body) {
     if (!body) return;
     cudaStreamSynchronize(body->ctx->stream);
     body_free(body);
+}
+
+mts_status mts_body_damping_layout(const mts_body *b, int32_t shift[3], int32_t *level_cap) {
+    if (!b || !shift || !level_cap) {
+        set_error("mts_body_damping_layout: NULL argument");
+        return MTS_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < 3; ++k) shift[k] = b->ax_shift[k] >= kWholeAxis ? MTS_WHOLE_AXIS : b->ax_shift[k];
+    *level_cap = b->level_cap;
+    return MTS_OK;
 }
 
 mts_status mts_body_permutation(const mts_body *b, int64_t *perm) {

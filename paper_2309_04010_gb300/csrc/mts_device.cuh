@@ -122,6 +122,13 @@ __device__ __forceinline__ void cp_async_reals(R *smem, const R *gmem) {
     }
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// close this thread's current group of copies
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // ------------------------------------------------------------------ math
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }

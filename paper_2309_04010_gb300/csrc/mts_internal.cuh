@@ -34,6 +34,9 @@ constexpr int kTipBit = 16;
 constexpr int kCHeldBit = 32;
 constexpr int kBlock = 256;  // threads per block of the per-particle kernels
 constexpr int kLevelCap = 32;  // pairs per damping level: one warp-wide pass
+constexpr int kWholeAxis = 62; // owner-block shift of an unblocked axis
+constexpr int kWideThreads = 256;   // threads of the CTA-per-group damping kernel
+constexpr int kWideRing = 8;        // level buffers of its pair-data ring
 
 // ------------------------------------------------------------------ errors
 void set_error(const char *fmt, ...);
@@ -103,11 +106,15 @@ struct Args {
     const R *pair_g;
     const long long *lvl_pair;   // level -> first pair, total_levels + 1
     const int32_t *grp_lvl;      // group -> first level, n_groups + 1
-    const int32_t *touch_start;  // group x NB
+    const int32_t *touch_start;  // group x NB: first block-sorted position of a touched block
     const int32_t *touch_cnt;
+    const int32_t *bperm;        // block-sorted position -> particle
+    const uint8_t *bflags;       // flags in block-sorted order (wide layout)
     int mb;                      // max particles per damping block (local stride)
+    int nbw;                     // touched blocks per owner group (2^blocked axes)
     int max_group_pairs;         // largest pair list of one owner group
     int max_group_levels;
+    int max_level_pairs;         // largest level (sub-colour of one group)
     // Morton tiles of T particles with their neighbour halo (shared-memory staging)
     int T;                       // particles per tile = threads per CTA
     long long ntiles;            // CTAs of the tiled kernels (= force partials)
@@ -151,6 +158,10 @@ struct mts_body {
     long long n;
     double dx, h, V, cut2;
     int blk_shift;
+    int damp_req;         // requested mts_damp_layout
+    int damp_layout;      // resolved: MTS_DAMP_BLOCKS or MTS_DAMP_WIDE
+    int ax_shift[3];      // owner-block width per axis (kWholeAxis = unblocked)
+    int level_cap;        // pairs per sub-colour of one group (0 = none)
     double Xmin[3];
     size_t rsize;  // sizeof(R)
 
@@ -174,10 +185,12 @@ struct mts_body {
     long long *lvl_pair;
     int32_t *grp_lvl;
     int32_t *touch_start, *touch_cnt;
+    int32_t *bperm;           // block-sorted position -> particle (identity for BLOCKS)
+    uint8_t *bflags;          // flags in block-sorted order (WIDE only)
     long long n_groups, n_levels;
     int col_off[9];
-    int mb;
-    int max_group_pairs, max_group_levels;
+    int mb, nbw;
+    int max_group_pairs, max_group_levels, max_level_pairs;
 
     // Morton tiles with neighbour halos
     int T;
@@ -241,6 +254,8 @@ mts_status launch_force(mts_body *b);
 mts_status launch_damping(mts_body *b, long long *launches = nullptr);
 mts_status launch_drift(mts_body *b);
 mts_status prepare_kernels(mts_body *b);
+// shared memory of the CTA-per-group damping kernel for this body's layout
+size_t damp_wide_smem(const mts_body *b);
 mts_status update_pair_fixbits(mts_body *b);
 mts_status launch_slow_begin(mts_body *b);
 mts_status launch_diffusion(mts_body *b, double dt);

@@ -253,8 +253,14 @@ __global__ void k_count_pairs(const long long *off, const int32_t *idx, long lon
     cnt[a] = c;
 }
 
+// owner-block widths per axis: 2^s cells, or the whole axis (s = kWholeAxis)
+struct Shifts {
+    int s[3];
+};
+__host__ __device__ inline long long bco(long long c, int s) { return s >= 31 ? 0 : c >> s; }
+
 __global__ void k_fill_pairs(const long long *off, const int32_t *idx, const int *cell,
-                             long long n, int dim, int shift, const long long *poff,
+                             long long n, int dim, Shifts sh, const long long *poff,
                              int32_t *pa, int32_t *pb, unsigned long long *key) {
     long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (a >= n) return;
@@ -265,7 +271,7 @@ __global__ void k_fill_pairs(const long long *off, const int32_t *idx, const int
         long long ob[3] = {0, 0, 0};
         int col = 0;
         for (int k = 0; k < dim; ++k) {
-            long long ba = cell[a * 3 + k] >> shift, bb = cell[(long long)b * 3 + k] >> shift;
+            long long ba = bco(cell[a * 3 + k], sh.s[k]), bb = bco(cell[(long long)b * 3 + k], sh.s[k]);
             ob[k] = ba < bb ? ba : bb;
             col |= (int)(ob[k] & 1) << k;
         }
@@ -299,12 +305,23 @@ __global__ void k_run_starts(const long long *scan, long long m, long long *star
     if (p == 0 || scan[p] != scan[p - 1]) start[scan[p] - 1] = p;
 }
 
-__global__ void k_block_keys(const int *cell, long long n, int dim, int shift,
+__global__ void k_block_keys(const int *cell, long long n, int dim, Shifts sh,
                              unsigned long long *bkey) {
     long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= n) return;
-    bkey[s] = morton(dim, cell[s * 3] >> shift, cell[s * 3 + 1] >> shift,
-                     cell[s * 3 + 2] >> shift);
+    bkey[s] = morton(dim, bco(cell[s * 3], sh.s[0]), bco(cell[s * 3 + 1], sh.s[1]),
+                     bco(cell[s * 3 + 2], sh.s[2]));
+}
+
+template <class T>
+__global__ void k_inverse(const long long *perm, long long n, T *inv) {
+    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s < n) inv[perm[s]] = (T)s;
+}
+
+__global__ void k_to_i32(const long long *in, long long n, int32_t *out) {
+    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s < n) out[s] = (int32_t)in[s];
 }
 
 __global__ void k_block_table(const long long *bstart, long long nb, long long n,
@@ -329,9 +346,19 @@ __device__ long long find_key(const unsigned long long *keys, long long m, unsig
     return (lo < m && keys[lo] == k) ? lo : -1;
 }
 
-// per owner group: the 2^d touched blocks (owner + e), their start and count
+// the blocked axes in ascending order; bit j of a touched-block index is the
+// +1 step on the j-th of them
+__device__ inline int blocked_axes(const Shifts &sh, int dim, int *ax) {
+    int nb = 0;
+    for (int k = 0; k < dim; ++k)
+        if (sh.s[k] < kWholeAxis) ax[nb++] = k;
+    return nb;
+}
+
+// per owner group: the touched blocks (owner + steps on the blocked axes),
+// their first block-sorted position and particle count
 __global__ void k_touch(const long long *gstart, long long ng, const int32_t *pa, const int32_t *pb,
-                        const int *cell, int dim, int shift, const unsigned long long *bkey,
+                        const int *cell, int dim, Shifts sh, const unsigned long long *bkey,
                         const long long *bstart, const int *bcnt, long long nblocks,
                         int32_t *tstart, int32_t *tcnt, int32_t *gcol, long long *gkey) {
     long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -341,41 +368,52 @@ __global__ void k_touch(const long long *gstart, long long ng, const int32_t *pa
     long long ob[3] = {0, 0, 0};
     int col = 0;
     for (int k = 0; k < dim; ++k) {
-        long long ba = cell[(long long)a * 3 + k] >> shift, bb = cell[(long long)b * 3 + k] >> shift;
+        long long ba = bco(cell[(long long)a * 3 + k], sh.s[k]);
+        long long bb = bco(cell[(long long)b * 3 + k], sh.s[k]);
         ob[k] = ba < bb ? ba : bb;
         col |= (int)(ob[k] & 1) << k;
     }
     gcol[g] = col;
     gkey[g] = (long long)morton(dim, ob[0], ob[1], ob[2]);
-    int nbk = 1 << dim;
+    int ax[3];
+    const int nblk = blocked_axes(sh, dim, ax);
+    const int nbk = 1 << dim;
     for (int e = 0; e < nbk; ++e) {
-        long long c0 = ob[0] + (e & 1), c1 = ob[1] + ((e >> 1) & 1), c2 = dim == 3 ? ob[2] + ((e >> 2) & 1) : 0;
-        long long bi = find_key(bkey, nblocks, morton(dim, c0, c1, c2));
+        long long bi = -1;
+        if (e < (1 << nblk)) {
+            long long c[3] = {ob[0], ob[1], ob[2]};
+            for (int j = 0; j < nblk; ++j) c[ax[j]] += (e >> j) & 1;
+            bi = find_key(bkey, nblocks, morton(dim, c[0], c[1], c[2]));
+        }
         tstart[g * nbk + e] = bi >= 0 ? (int32_t)bstart[bi] : 0;
         tcnt[g * nbk + e] = bi >= 0 ? bcnt[bi] : 0;
     }
 }
 
 // greedy sub-colouring of one owner group per thread; local particle index =
-// e * mb + (particle - start of block owner + e)
+// e * mb + (block-sorted position - start of touched block e); cap = most
+// pairs per sub-colour (0 = no cap)
 __global__ void k_greedy(const long long *gstart, long long g0, long long g1, long long ng,
                          long long m, const int32_t *pa, const int32_t *pb, const int *cell,
-                         int dim, int shift, const int32_t *tstart, int mb,
-                         unsigned long long *used, int32_t *sub, uint32_t *ab, int32_t *nsub,
-                         Control *ctrl) {
+                         int dim, Shifts sh, const int32_t *tstart, const int32_t *binv, int mb,
+                         int nbw, int cap, unsigned long long *used, int32_t *sub, uint32_t *ab,
+                         int32_t *nsub, Control *ctrl) {
     long long g = g0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (g >= g1) return;
-    int nbk = 1 << dim;
-    unsigned long long *U = used + (g - g0) * (long long)nbk * mb * 4;
+    const int nbk = 1 << dim;
+    unsigned long long *U = used + (g - g0) * (long long)nbw * mb * 4;
     long long p0 = gstart[g], p1 = g + 1 < ng ? gstart[g + 1] : m;
     long long ob[3] = {0, 0, 0};
     {
         int a = pa[p0], b = pb[p0];
         for (int k = 0; k < dim; ++k) {
-            long long ba = cell[(long long)a * 3 + k] >> shift, bb = cell[(long long)b * 3 + k] >> shift;
+            long long ba = bco(cell[(long long)a * 3 + k], sh.s[k]);
+            long long bb = bco(cell[(long long)b * 3 + k], sh.s[k]);
             ob[k] = ba < bb ? ba : bb;
         }
     }
+    int ax[3];
+    const int nblk = blocked_axes(sh, dim, ax);
     int maxc = -1;
     int count[256];
     for (int c = 0; c < 256; ++c) count[c] = 0;
@@ -384,19 +422,18 @@ __global__ void k_greedy(const long long *gstart, long long g0, long long g1, lo
         int pp[2] = {pa[p], pb[p]};
         for (int t = 0; t < 2; ++t) {
             int e = 0;
-            for (int k = 0; k < dim; ++k)
-                e |= (int)((cell[(long long)pp[t] * 3 + k] >> shift) - ob[k]) << k;
-            loc[t] = e * mb + (pp[t] - tstart[g * nbk + e]);
+            for (int j = 0; j < nblk; ++j)
+                e |= (int)(bco(cell[(long long)pp[t] * 3 + ax[j]], sh.s[ax[j]]) - ob[ax[j]]) << j;
+            loc[t] = e * mb + (binv[pp[t]] - tstart[g * nbk + e]);
         }
         unsigned long long *ua = U + (long long)loc[0] * 4, *ub = U + (long long)loc[1] * 4;
         // smallest sub-colour free at both particles that still has room
-        // (at most kLevelCap pairs per level: one warp-wide pass)
         int c = -1;
         for (int w = 0; w < 4 && c < 0; ++w) {
             unsigned long long free_bits = ~(ua[w] | ub[w]);
             while (free_bits) {
                 const int cand = w * 64 + __ffsll((long long)free_bits) - 1;
-                if (count[cand] < kLevelCap) {
+                if (cap == 0 || count[cand] < cap) {
                     c = cand;
                     break;
                 }
@@ -602,6 +639,11 @@ __global__ void k_group_max(const long long *lvl_pair, const int32_t *grp_lvl, l
     atomicMax(mx + 1, (unsigned int)(grp_lvl[g + 1] - grp_lvl[g]));
 }
 
+__global__ void k_level_max(const long long *lvl_pair, long long nlev, unsigned int *mx) {
+    long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (L < nlev) atomicMax(mx, (unsigned int)(lvl_pair[L + 1] - lvl_pair[L]));
+}
+
 __global__ void k_col_off(const int32_t *gcol, long long ng, int ncol, int *col_off) {
     long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (g > ng) return;
@@ -736,6 +778,275 @@ mts_status build_tiles(mts_body *b, Tmp &tmp, cudaStream_t st, int T) {
     return MTS_OK;
 }
 
+// release the damping-order arrays of a layout that did not fit
+void free_damping(mts_body *b) {
+    void **ptrs[] = {(void **)&b->pair_a, (void **)&b->pair_b, (void **)&b->pair_col,
+                     (void **)&b->pair_sub, (void **)&b->pair_key, (void **)&b->pair_ab,
+                     (void **)&b->pair_g, (void **)&b->lvl_pair, (void **)&b->grp_lvl,
+                     (void **)&b->touch_start, (void **)&b->touch_cnt, (void **)&b->pair_slot,
+                     (void **)&b->kpad_ab, (void **)&b->kpad_g, (void **)&b->bperm,
+                     (void **)&b->bflags};
+    for (void **pp : ptrs) {
+        dfree(b->ctx, *pp);
+        *pp = nullptr;
+    }
+}
+
+// The canonical damping order for the layout in b->ax_shift / b->level_cap.
+// *no_fit is set (with MTS_ERR_INVALID_ARG) when the CTA-per-group kernel of
+// the wide layout cannot stage an owner group.
+template <class R, int D>
+mts_status build_damping(mts_body *b, Tmp &tmp, cudaStream_t st, const int *cell, bool *no_fit) {
+    mts_ctx *ctx = b->ctx;
+    const long long n = b->n;
+    const bool wide = b->damp_layout == MTS_DAMP_WIDE;
+    const Shifts sh{{b->ax_shift[0], b->ax_shift[1], b->ax_shift[2]}};
+    int nblocked = 0;
+    for (int k = 0; k < D; ++k) nblocked += b->ax_shift[k] < kWholeAxis;
+    const int nbk = 1 << D, nbw = 1 << nblocked;
+    *no_fit = false;
+
+    // owned pairs, keyed by (colour, owner block)
+    long long *pcnt = tmp.get<long long>(n + 1), *poff = tmp.get<long long>(n + 1);
+    NEED(pcnt); NEED(poff);
+    k_count_pairs<<<grid_for(n), TPB, 0, st>>>(b->nb_off, b->nb_idx, n, pcnt);
+    MTS_CUDA(cudaMemsetAsync(pcnt + n, 0, sizeof(long long), st));
+    MTS_TRY(cub_excl_sum(tmp, pcnt, poff, n + 1, st));
+    long long m = 0;
+    MTS_TRY(to_host(&m, poff + n, 1, st));
+    b->npairs = m;
+    if (m * 2 != b->nnz) {
+        set_error("neighbour lists are not symmetric (%lld pairs, %lld entries)", m, b->nnz);
+        return MTS_ERR_STATE;
+    }
+    const long long mm = std::max(m, 1LL);
+    int32_t *pa0 = tmp.get<int32_t>(mm), *pb0 = tmp.get<int32_t>(mm);
+    unsigned long long *pk0 = tmp.get<unsigned long long>(mm), *pk1 = tmp.get<unsigned long long>(mm);
+    long long *ord = tmp.get<long long>(mm), *ord1 = tmp.get<long long>(mm);
+    NEED(pa0); NEED(pb0); NEED(pk0); NEED(pk1); NEED(ord); NEED(ord1);
+    k_fill_pairs<<<grid_for(n), TPB, 0, st>>>(b->nb_off, b->nb_idx, cell, n, D, sh, poff, pa0, pb0,
+                                              pk0);
+    k_iota<<<grid_for(m), TPB, 0, st>>>(ord, m);
+    MTS_TRY(cub_sort_pairs(tmp, pk0, pk1, ord, ord1, m, 63, st));
+    int32_t *pa1 = tmp.get<int32_t>(mm), *pb1 = tmp.get<int32_t>(mm);
+    NEED(pa1); NEED(pb1);
+    k_gather<<<grid_for(m), TPB, 0, st>>>(pa0, ord1, m, pa1);
+    k_gather<<<grid_for(m), TPB, 0, st>>>(pb0, ord1, m, pb1);
+
+    // owner groups
+    long long *flag = tmp.get<long long>(mm), *gscan = tmp.get<long long>(mm);
+    NEED(flag); NEED(gscan);
+    k_run_flags<<<grid_for(m), TPB, 0, st>>>(pk1, m, flag);
+    MTS_TRY(cub_incl_sum(tmp, flag, gscan, m, st));
+    long long ng = 0;
+    if (m > 0) MTS_TRY(to_host(&ng, gscan + m - 1, 1, st));
+    b->n_groups = ng;
+    const long long ngg = std::max(ng, 1LL);
+    long long *gstart = tmp.get<long long>(ngg + 1);
+    NEED(gstart);
+    k_run_starts<<<grid_for(m), TPB, 0, st>>>(gscan, m, gstart);
+
+    // block table over the block-sorted order (stable by block key; with the
+    // same shift on every axis the Morton order is already block-sorted, so
+    // the permutation is the identity there)
+    unsigned long long *bkp = tmp.get<unsigned long long>(n), *bks = tmp.get<unsigned long long>(n);
+    long long *io = tmp.get<long long>(n), *bp64 = tmp.get<long long>(n);
+    long long *bflag = tmp.get<long long>(n), *bscan = tmp.get<long long>(n);
+    int32_t *binv = tmp.get<int32_t>(n);
+    NEED(bkp); NEED(bks); NEED(io); NEED(bp64); NEED(bflag); NEED(bscan); NEED(binv);
+    k_block_keys<<<grid_for(n), TPB, 0, st>>>(cell, n, D, sh, bkp);
+    k_iota<<<grid_for(n), TPB, 0, st>>>(io, n);
+    MTS_TRY(cub_sort_pairs(tmp, bkp, bks, io, bp64, n, 64, st));
+    MTS_TRY(dalloc_t(ctx, &b->bperm, n));
+    k_to_i32<<<grid_for(n), TPB, 0, st>>>(bp64, n, b->bperm);
+    k_inverse<int32_t><<<grid_for(n), TPB, 0, st>>>(bp64, n, binv);
+    k_run_flags<<<grid_for(n), TPB, 0, st>>>(bks, n, bflag);
+    MTS_TRY(cub_incl_sum(tmp, bflag, bscan, n, st));
+    long long nblocks = 0;
+    MTS_TRY(to_host(&nblocks, bscan + n - 1, 1, st));
+    long long *bstart = tmp.get<long long>(nblocks + 1);
+    unsigned long long *bkey = tmp.get<unsigned long long>(nblocks + 1);
+    int *bcnt = tmp.get<int>(nblocks + 1);
+    unsigned int *dmb = tmp.get<unsigned int>(1);
+    NEED(bstart); NEED(bkey); NEED(bcnt); NEED(dmb);
+    k_run_starts<<<grid_for(n), TPB, 0, st>>>(bscan, n, bstart);
+    MTS_CUDA(cudaMemsetAsync(dmb, 0, sizeof(unsigned), st));
+    k_block_table<<<grid_for(nblocks), TPB, 0, st>>>(bstart, nblocks, n, bks, bkey, bcnt, dmb);
+    unsigned int hmb = 0;
+    MTS_TRY(to_host(&hmb, dmb, 1, st));
+    if (wide) {
+        // 16-bit slot indices of the staged velocities, one dummy slot spare
+        if ((long long)hmb * nbw + 1 > 65535) {
+            set_error("wide damping block holds %u particles; at most %d fit the 16-bit slot index",
+                      hmb, 65534 / nbw);
+            *no_fit = true;
+            return MTS_ERR_INVALID_ARG;
+        }
+    } else if ((long long)hmb * nbk > 32767) {
+        set_error("damping block holds %u particles; at most %d fit the 15-bit local index",
+                  hmb, 32767 / nbk);
+        return MTS_ERR_INVALID_ARG;
+    }
+    b->mb = (int)hmb;
+    b->nbw = nbw;
+
+    int32_t *gcol = tmp.get<int32_t>(ngg);
+    long long *gkey = tmp.get<long long>(ngg);
+    NEED(gcol); NEED(gkey);
+    MTS_TRY(dalloc_t(ctx, &b->touch_start, ngg * nbk));
+    MTS_TRY(dalloc_t(ctx, &b->touch_cnt, ngg * nbk));
+    k_touch<<<grid_for(ng), TPB, 0, st>>>(gstart, ng, pa1, pb1, cell, D, sh, bkey, bstart, bcnt,
+                                           nblocks, b->touch_start, b->touch_cnt, gcol, gkey);
+
+    // visit order of the greedy: owner group, offset class, then (a, b)
+    const int Rr = (int)std::floor(2.0 * b->h / b->dx) + 1;
+    int32_t *pa2 = tmp.get<int32_t>(mm), *pb2 = tmp.get<int32_t>(mm);
+    long long *ord3 = tmp.get<long long>(mm);
+    NEED(pa2); NEED(pb2); NEED(ord3);
+    {
+        unsigned long long *k3 = tmp.get<unsigned long long>(mm), *k3s = tmp.get<unsigned long long>(mm);
+        long long *io3 = tmp.get<long long>(mm);
+        NEED(k3); NEED(k3s); NEED(io3);
+        k_pair_class<<<grid_for(m), TPB, 0, st>>>(pa1, pb1, gscan, m, cell, D, Rr, k3);
+        k_iota<<<grid_for(m), TPB, 0, st>>>(io3, m);
+        int gb3 = 1;
+        while ((1LL << gb3) <= ng) ++gb3;
+        MTS_TRY(cub_sort_pairs(tmp, k3, k3s, io3, ord3, m, std::min(64, gb3 + 16), st));
+        k_gather<<<grid_for(m), TPB, 0, st>>>(pa1, ord3, m, pa2);
+        k_gather<<<grid_for(m), TPB, 0, st>>>(pb1, ord3, m, pb2);
+    }
+
+    // greedy sub-colours, in batches of groups to bound the bitmask scratch
+    int32_t *sub0 = tmp.get<int32_t>(mm), *nsub = tmp.get<int32_t>(ngg + 1);
+    uint32_t *ab0 = tmp.get<uint32_t>(mm);
+    int32_t *subc = tmp.get<int32_t>(mm);
+    uint32_t *abc = tmp.get<uint32_t>(mm);
+    NEED(sub0); NEED(nsub); NEED(ab0); NEED(subc); NEED(abc);
+    long long per_group = (long long)nbw * b->mb * 4;   // 64-bit words
+    long long batch = std::max(1LL, std::min(ng, (1LL << 25) / std::max(per_group, 1LL)));
+    unsigned long long *used = tmp.get<unsigned long long>(batch * per_group + 1);
+    NEED(used);
+    for (long long gs = 0; gs < ng; gs += batch) {
+        long long ge = std::min(ng, gs + batch);
+        MTS_CUDA(cudaMemsetAsync(used, 0, (ge - gs) * per_group * sizeof(unsigned long long), st));
+        k_greedy<<<grid_for(ge - gs, 64), 64, 0, st>>>(gstart, gs, ge, ng, m, pa2, pb2, cell, D, sh,
+                                                         b->touch_start, binv, b->mb, nbw,
+                                                         b->level_cap, used, subc, abc, nsub,
+                                                         b->ctrl);
+    }
+    // back to (group, a, b) order, so that the final stable sort by
+    // (group, sub-colour) lists each level in ascending (a, b)
+    k_scatter<<<grid_for(m), TPB, 0, st>>>(subc, ord3, m, sub0);
+    k_scatter<<<grid_for(m), TPB, 0, st>>>(abc, ord3, m, ab0);
+
+    // final canonical order: (group, sub-colour), stable
+    unsigned long long *k2 = tmp.get<unsigned long long>(mm), *k2s = tmp.get<unsigned long long>(mm);
+    NEED(k2); NEED(k2s);
+    k_group_of_pair<<<grid_for(m), TPB, 0, st>>>(gscan, m, sub0, k2);
+    k_iota<<<grid_for(m), TPB, 0, st>>>(ord, m);
+    int gbits = 1;
+    while ((1LL << gbits) <= ng) ++gbits;
+    MTS_TRY(cub_sort_pairs(tmp, k2, k2s, ord, ord1, m, std::min(64, gbits + 8), st));
+    MTS_TRY(dalloc_t(ctx, &b->pair_a, mm));
+    MTS_TRY(dalloc_t(ctx, &b->pair_b, mm));
+    MTS_TRY(dalloc_t(ctx, &b->pair_sub, mm));
+    MTS_TRY(dalloc_t(ctx, &b->pair_col, mm));
+    MTS_TRY(dalloc_t(ctx, &b->pair_key, mm));
+    MTS_TRY(dalloc_t(ctx, &b->pair_ab, mm));
+    MTS_TRY(dalloc_into(ctx, &b->pair_g, mm * sizeof(R) + 16));
+    k_gather<<<grid_for(m), TPB, 0, st>>>(pa1, ord1, m, b->pair_a);
+    k_gather<<<grid_for(m), TPB, 0, st>>>(pb1, ord1, m, b->pair_b);
+    k_gather<<<grid_for(m), TPB, 0, st>>>(sub0, ord1, m, b->pair_sub);
+    k_gather<<<grid_for(m), TPB, 0, st>>>(ab0, ord1, m, b->pair_ab);
+    // per-pair colour and owner key from the group of each final pair
+    {
+        long long *gid = tmp.get<long long>(mm), *g0i = tmp.get<long long>(mm);
+        NEED(gid); NEED(g0i);
+        k_gather<<<grid_for(m), TPB, 0, st>>>(gscan, ord1, m, gid);   // 1-based group ids
+        k_minus_one<<<grid_for(m), TPB, 0, st>>>(gid, m, g0i);
+        k_gather<<<grid_for(m), TPB, 0, st>>>(gcol, g0i, m, b->pair_col);
+        k_gather<<<grid_for(m), TPB, 0, st>>>(gkey, g0i, m, b->pair_key);
+    }
+
+    // levels
+    MTS_TRY(dalloc_t(ctx, &b->grp_lvl, ngg + 1));
+    MTS_CUDA(cudaMemsetAsync(nsub + ng, 0, sizeof(int32_t), st));
+    MTS_TRY(cub_excl_sum(tmp, nsub, b->grp_lvl, ng + 1, st));
+    int nlev = 0;
+    MTS_TRY(to_host(&nlev, b->grp_lvl + ng, 1, st));
+    b->n_levels = nlev;
+    MTS_TRY(dalloc_t(ctx, &b->lvl_pair, (long long)nlev + 1));
+    k_levels<<<grid_for(m + 1), TPB, 0, st>>>(k2s, m, b->grp_lvl, b->lvl_pair, nlev);
+    k_pair_coef<R, D><<<grid_for(m), TPB, 0, st>>>(b->pair_a, b->pair_b, m, b->X64, b->h,
+                                                    kernel_alpha(D, b->h), b->V, (R *)b->pair_g);
+    {
+        unsigned int *mx = tmp.get<unsigned int>(3);
+        NEED(mx);
+        MTS_CUDA(cudaMemsetAsync(mx, 0, 3 * sizeof(unsigned), st));
+        k_group_max<<<grid_for(ng), TPB, 0, st>>>(b->lvl_pair, b->grp_lvl, ng, mx);
+        k_level_max<<<grid_for(nlev), TPB, 0, st>>>(b->lvl_pair, nlev, mx + 2);
+        unsigned int hm[3];
+        MTS_TRY(to_host(hm, mx, 3, st));
+        b->max_group_pairs = (int)hm[0];
+        b->max_group_levels = (int)hm[1];
+        b->max_level_pairs = (int)hm[2];
+    }
+    if (wide) {
+        const size_t need = damp_wide_smem(b);
+        if (need > 227 * 1024) {
+            set_error("wide damping needs %zu bytes of shared memory per owner group "
+                      "(block %d particles, %d levels of up to %d pairs)", need, b->mb,
+                      b->max_group_levels, b->max_level_pairs);
+            *no_fit = true;
+            return MTS_ERR_INVALID_ARG;
+        }
+        // the kernel streams the canonical order: pair words hold slot
+        // indices, coefficients carry the constrained-pair sign
+        MTS_TRY(dalloc_t(ctx, &b->pair_slot, mm));
+        MTS_TRY(dalloc_t(ctx, &b->kpad_ab, mm));
+        MTS_TRY(dalloc_into(ctx, &b->kpad_g, mm * sizeof(R) + 16));
+        k_iota<<<grid_for(m), TPB, 0, st>>>(b->pair_slot, m);
+        MTS_TRY(dalloc_t(ctx, &b->bflags, n));
+        MTS_CUDA(cudaMemsetAsync(b->bflags, 0, n, st));   // flags start at zero
+        MTS_CUDA(cudaMemcpyAsync(b->kpad_ab, b->pair_ab, m * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToDevice, st));
+        MTS_CUDA(cudaMemcpyAsync(b->kpad_g, b->pair_g, m * sizeof(R), cudaMemcpyDeviceToDevice, st));
+    } else {
+        // padded per-level layout for the warp-per-group kernel (32 slots per level)
+        const long long ns = 32LL * nlev;
+        MTS_TRY(dalloc_t(ctx, &b->pair_slot, mm));
+        MTS_TRY(dalloc_t(ctx, &b->kpad_ab, std::max(ns, 4LL)));
+        MTS_TRY(dalloc_into(ctx, &b->kpad_g, std::max(ns, 4LL) * sizeof(R) + 16));
+        const int bps = Pad<D>::v * (int)sizeof(R);
+        const long long dummy = (long long)nbk * b->mb * bps;   // byte offset of the dummy slot
+        if (dummy > 65535) {
+            set_error("damping blocks too large for 16-bit byte offsets (%d particles)", b->mb);
+            return MTS_ERR_INVALID_ARG;
+        }
+        k_fill_dummy<<<grid_for(std::max(ns, 4LL)), TPB, 0, st>>>(b->kpad_ab, std::max(ns, 4LL),
+                                                                 (uint32_t)dummy);
+        MTS_CUDA(cudaMemsetAsync(b->kpad_g, 0, std::max(ns, 4LL) * sizeof(R), st));
+        k_fill_slots<<<grid_for(m), TPB, 0, st>>>(k2s, m, b->grp_lvl, b->lvl_pair, b->pair_ab,
+                                                  b->pair_slot, b->kpad_ab, bps);
+        k_fill_slot_g<R><<<grid_for(m), TPB, 0, st>>>((const R *)b->pair_g, b->pair_slot, m,
+                                                       (R *)b->kpad_g);
+    }
+    int *dcol = tmp.get<int>(16);
+    NEED(dcol);
+    k_col_off<<<grid_for(ng + 1), TPB, 0, st>>>(gcol, ng, nbk, dcol);
+    MTS_TRY(to_host(b->col_off, dcol, nbk + 1, st));
+    return MTS_OK;
+}
+
+// layout of the damping order: every axis blocked (cap 32 pairs per level),
+// or axis k_whole unblocked (no cap)
+void set_layout(mts_body *b, int layout, int k_whole) {
+    b->damp_layout = layout;
+    for (int k = 0; k < 3; ++k)
+        b->ax_shift[k] = (layout == MTS_DAMP_WIDE && k == k_whole) ? kWholeAxis : b->blk_shift;
+    b->level_cap = layout == MTS_DAMP_WIDE ? 0 : kLevelCap;
+}
+
 template <class R, int D>
 mts_status build_typed(mts_body *b, const double *hX) {
     mts_ctx *ctx = b->ctx;
@@ -831,197 +1142,36 @@ mts_status build_typed(mts_body *b, const double *hX) {
     k_b0<R, D><<<grid_for(n), TPB, 0, st>>>(b->X64, b->nb_off, b->nb_idx, n, b->h, alpha, b->V,
                                              (R *)b->B0, b->ctrl);
 
-    // -- damping order: owned pairs
-    long long *pcnt = tmp.get<long long>(n + 1), *poff = tmp.get<long long>(n + 1);
-    NEED(pcnt); NEED(poff);
-    k_count_pairs<<<grid_for(n), TPB, 0, st>>>(b->nb_off, b->nb_idx, n, pcnt);
-    MTS_CUDA(cudaMemsetAsync(pcnt + n, 0, sizeof(long long), st));
-    MTS_TRY(cub_excl_sum(tmp, pcnt, poff, n + 1, st));
-    long long m = 0;
-    MTS_TRY(to_host(&m, poff + n, 1, st));
-    b->npairs = m;
-    if (m * 2 != b->nnz) {
-        set_error("neighbour lists are not symmetric (%lld pairs, %lld entries)", m, b->nnz);
-        return MTS_ERR_STATE;
-    }
-    const long long mm = std::max(m, 1LL);
-    int32_t *pa0 = tmp.get<int32_t>(mm), *pb0 = tmp.get<int32_t>(mm);
-    unsigned long long *pk0 = tmp.get<unsigned long long>(mm), *pk1 = tmp.get<unsigned long long>(mm);
-    long long *ord = tmp.get<long long>(mm), *ord1 = tmp.get<long long>(mm);
-    NEED(pa0); NEED(pb0); NEED(pk0); NEED(pk1); NEED(ord); NEED(ord1);
-    k_fill_pairs<<<grid_for(n), TPB, 0, st>>>(b->nb_off, b->nb_idx, cell, n, D, b->blk_shift, poff,
-                                              pa0, pb0, pk0);
-    k_iota<<<grid_for(m), TPB, 0, st>>>(ord, m);
-    MTS_TRY(cub_sort_pairs(tmp, pk0, pk1, ord, ord1, m, 63, st));
-    int32_t *pa1 = tmp.get<int32_t>(mm), *pb1 = tmp.get<int32_t>(mm);
-    NEED(pa1); NEED(pb1);
-    k_gather<<<grid_for(m), TPB, 0, st>>>(pa0, ord1, m, pa1);
-    k_gather<<<grid_for(m), TPB, 0, st>>>(pb0, ord1, m, pb1);
-
-    // owner groups
-    long long *flag = tmp.get<long long>(mm), *gscan = tmp.get<long long>(mm);
-    NEED(flag); NEED(gscan);
-    k_run_flags<<<grid_for(m), TPB, 0, st>>>(pk1, m, flag);
-    MTS_TRY(cub_incl_sum(tmp, flag, gscan, m, st));
-    long long ng = 0;
-    if (m > 0) MTS_TRY(to_host(&ng, gscan + m - 1, 1, st));
-    b->n_groups = ng;
-    const long long ngg = std::max(ng, 1LL);
-    long long *gstart = tmp.get<long long>(ngg + 1);
-    NEED(gstart);
-    k_run_starts<<<grid_for(m), TPB, 0, st>>>(gscan, m, gstart);
-
-    // block table (particles are contiguous per block in Morton order)
-    unsigned long long *bkp = tmp.get<unsigned long long>(n);
-    long long *bflag = tmp.get<long long>(n), *bscan = tmp.get<long long>(n);
-    NEED(bkp); NEED(bflag); NEED(bscan);
-    k_block_keys<<<grid_for(n), TPB, 0, st>>>(cell, n, D, b->blk_shift, bkp);
-    k_run_flags<<<grid_for(n), TPB, 0, st>>>(bkp, n, bflag);
-    MTS_TRY(cub_incl_sum(tmp, bflag, bscan, n, st));
-    long long nblocks = 0;
-    MTS_TRY(to_host(&nblocks, bscan + n - 1, 1, st));
-    long long *bstart = tmp.get<long long>(nblocks + 1);
-    unsigned long long *bkey = tmp.get<unsigned long long>(nblocks + 1);
-    int *bcnt = tmp.get<int>(nblocks + 1);
-    unsigned int *dmb = tmp.get<unsigned int>(1);
-    NEED(bstart); NEED(bkey); NEED(bcnt); NEED(dmb);
-    k_run_starts<<<grid_for(n), TPB, 0, st>>>(bscan, n, bstart);
-    MTS_CUDA(cudaMemsetAsync(dmb, 0, sizeof(unsigned), st));
-    k_block_table<<<grid_for(nblocks), TPB, 0, st>>>(bstart, nblocks, n, bkp, bkey, bcnt, dmb);
-    unsigned int hmb = 0;
-    MTS_TRY(to_host(&hmb, dmb, 1, st));
-    const int nbk = 1 << D;
-    if ((long long)hmb * nbk > 32767) {
-        set_error("damping block holds %u particles; at most %d fit the 15-bit local index",
-                  hmb, 32767 / nbk);
-        return MTS_ERR_INVALID_ARG;
-    }
-    b->mb = (int)hmb;
-
-    int32_t *gcol = tmp.get<int32_t>(ngg);
-    long long *gkey = tmp.get<long long>(ngg);
-    NEED(gcol); NEED(gkey);
-    MTS_TRY(dalloc_t(ctx, &b->touch_start, ngg * nbk));
-    MTS_TRY(dalloc_t(ctx, &b->touch_cnt, ngg * nbk));
-    k_touch<<<grid_for(ng), TPB, 0, st>>>(gstart, ng, pa1, pb1, cell, D, b->blk_shift, bkey, bstart,
-                                           bcnt, nblocks, b->touch_start, b->touch_cnt, gcol, gkey);
-
-    // visit order of the greedy: owner group, offset class, then (a, b)
-    const int Rr = (int)std::floor(2.0 * b->h / b->dx) + 1;
-    int32_t *pa2 = tmp.get<int32_t>(mm), *pb2 = tmp.get<int32_t>(mm);
-    long long *ord3 = tmp.get<long long>(mm);
-    NEED(pa2); NEED(pb2); NEED(ord3);
+    // -- damping order.  AUTO takes the wide layout (shortest axis unblocked,
+    // ties to the higher axis) when that axis spans at most 64 cells in 3D or
+    // 256 in 2D and an owner group fits one CTA, else blocks on every axis.
     {
-        unsigned long long *k3 = tmp.get<unsigned long long>(mm), *k3s = tmp.get<unsigned long long>(mm);
-        long long *io = tmp.get<long long>(mm);
-        NEED(k3); NEED(k3s); NEED(io);
-        k_pair_class<<<grid_for(m), TPB, 0, st>>>(pa1, pb1, gscan, m, cell, D, Rr, k3);
-        k_iota<<<grid_for(m), TPB, 0, st>>>(io, m);
-        int gb3 = 1;
-        while ((1LL << gb3) <= ng) ++gb3;
-        MTS_TRY(cub_sort_pairs(tmp, k3, k3s, io, ord3, m, std::min(64, gb3 + 16), st));
-        k_gather<<<grid_for(m), TPB, 0, st>>>(pa1, ord3, m, pa2);
-        k_gather<<<grid_for(m), TPB, 0, st>>>(pb1, ord3, m, pb2);
-    }
-
-    // greedy sub-colours, in batches of groups to bound the bitmask scratch
-    int32_t *sub0 = tmp.get<int32_t>(mm), *nsub = tmp.get<int32_t>(ngg + 1);
-    uint32_t *ab0 = tmp.get<uint32_t>(mm);
-    int32_t *subc = tmp.get<int32_t>(mm);
-    uint32_t *abc = tmp.get<uint32_t>(mm);
-    NEED(sub0); NEED(nsub); NEED(ab0); NEED(subc); NEED(abc);
-    long long per_group = (long long)nbk * b->mb * 4;   // 64-bit words
-    long long batch = std::max(1LL, std::min(ng, (1LL << 25) / std::max(per_group, 1LL)));
-    unsigned long long *used = tmp.get<unsigned long long>(batch * per_group + 1);
-    NEED(used);
-    for (long long gs = 0; gs < ng; gs += batch) {
-        long long ge = std::min(ng, gs + batch);
-        MTS_CUDA(cudaMemsetAsync(used, 0, (ge - gs) * per_group * sizeof(unsigned long long), st));
-        k_greedy<<<grid_for(ge - gs, 64), 64, 0, st>>>(gstart, gs, ge, ng, m, pa2, pb2, cell, D,
-                                                         b->blk_shift, b->touch_start, b->mb, used,
-                                                         subc, abc, nsub, b->ctrl);
-    }
-    // back to (group, a, b) order, so that the final stable sort by
-    // (group, sub-colour) lists each level in ascending (a, b)
-    k_scatter<<<grid_for(m), TPB, 0, st>>>(subc, ord3, m, sub0);
-    k_scatter<<<grid_for(m), TPB, 0, st>>>(abc, ord3, m, ab0);
-
-    // final canonical order: (group, sub-colour), stable
-    unsigned long long *k2 = tmp.get<unsigned long long>(mm), *k2s = tmp.get<unsigned long long>(mm);
-    NEED(k2); NEED(k2s);
-    k_group_of_pair<<<grid_for(m), TPB, 0, st>>>(gscan, m, sub0, k2);
-    k_iota<<<grid_for(m), TPB, 0, st>>>(ord, m);
-    int gbits = 1;
-    while ((1LL << gbits) <= ng) ++gbits;
-    MTS_TRY(cub_sort_pairs(tmp, k2, k2s, ord, ord1, m, std::min(64, gbits + 8), st));
-    MTS_TRY(dalloc_t(ctx, &b->pair_a, mm));
-    MTS_TRY(dalloc_t(ctx, &b->pair_b, mm));
-    MTS_TRY(dalloc_t(ctx, &b->pair_sub, mm));
-    MTS_TRY(dalloc_t(ctx, &b->pair_col, mm));
-    MTS_TRY(dalloc_t(ctx, &b->pair_key, mm));
-    MTS_TRY(dalloc_t(ctx, &b->pair_ab, mm));
-    MTS_TRY(dalloc_into(ctx, &b->pair_g, mm * sizeof(R) + 16));
-    k_gather<<<grid_for(m), TPB, 0, st>>>(pa1, ord1, m, b->pair_a);
-    k_gather<<<grid_for(m), TPB, 0, st>>>(pb1, ord1, m, b->pair_b);
-    k_gather<<<grid_for(m), TPB, 0, st>>>(sub0, ord1, m, b->pair_sub);
-    k_gather<<<grid_for(m), TPB, 0, st>>>(ab0, ord1, m, b->pair_ab);
-    // per-pair colour and owner key from the group of each final pair
-    {
-        long long *gid = tmp.get<long long>(mm), *g0i = tmp.get<long long>(mm);
-        NEED(gid); NEED(g0i);
-        k_gather<<<grid_for(m), TPB, 0, st>>>(gscan, ord1, m, gid);   // 1-based group ids
-        k_minus_one<<<grid_for(m), TPB, 0, st>>>(gid, m, g0i);
-        k_gather<<<grid_for(m), TPB, 0, st>>>(gcol, g0i, m, b->pair_col);
-        k_gather<<<grid_for(m), TPB, 0, st>>>(gkey, g0i, m, b->pair_key);
-    }
-
-    // levels
-    MTS_TRY(dalloc_t(ctx, &b->grp_lvl, ngg + 1));
-    MTS_CUDA(cudaMemsetAsync(nsub + ng, 0, sizeof(int32_t), st));
-    MTS_TRY(cub_excl_sum(tmp, nsub, b->grp_lvl, ng + 1, st));
-    int nlev = 0;
-    MTS_TRY(to_host(&nlev, b->grp_lvl + ng, 1, st));
-    b->n_levels = nlev;
-    MTS_TRY(dalloc_t(ctx, &b->lvl_pair, (long long)nlev + 1));
-    k_levels<<<grid_for(m + 1), TPB, 0, st>>>(k2s, m, b->grp_lvl, b->lvl_pair, nlev);
-    k_pair_coef<R, D><<<grid_for(m), TPB, 0, st>>>(b->pair_a, b->pair_b, m, b->X64, b->h, alpha,
-                                                    b->V, (R *)b->pair_g);
-    // padded per-level layout for the damping kernel (32 slots per level)
-    {
-        const long long ns = 32LL * nlev;
-        MTS_TRY(dalloc_t(ctx, &b->pair_slot, mm));
-        MTS_TRY(dalloc_t(ctx, &b->kpad_ab, std::max(ns, 4LL)));
-        MTS_TRY(dalloc_into(ctx, &b->kpad_g, std::max(ns, 4LL) * sizeof(R) + 16));
-        const int bps = Pad<D>::v * (int)sizeof(R);
-        const long long dummy = (long long)(1 << D) * b->mb * bps;   // byte offset of the dummy slot
-        if (dummy > 65535) {
-            set_error("damping blocks too large for 16-bit byte offsets (%d particles)", b->mb);
-            return MTS_ERR_INVALID_ARG;
+        const long long cells[3] = {g0, g1, g2};
+        int kmin = 0;
+        for (int k = 1; k < D; ++k)
+            if (cells[k] <= cells[kmin]) kmin = k;
+        const bool try_wide = b->damp_req == MTS_DAMP_WIDE ||
+                              (b->damp_req == MTS_DAMP_AUTO && cells[kmin] <= (D == 3 ? 64 : 256));
+        bool built = false;
+        if (try_wide) {
+            set_layout(b, MTS_DAMP_WIDE, kmin);
+            bool no_fit = false;
+            const mts_status s = build_damping<R, D>(b, tmp, st, cell, &no_fit);
+            if (s == MTS_OK) {
+                built = true;
+            } else if (!(no_fit && b->damp_req == MTS_DAMP_AUTO)) {
+                return s;
+            } else {
+                MTS_CUDA(cudaStreamSynchronize(st));
+                free_damping(b);
+            }
         }
-        k_fill_dummy<<<grid_for(std::max(ns, 4LL)), TPB, 0, st>>>(b->kpad_ab, std::max(ns, 4LL),
-                                                                 (uint32_t)dummy);
-        MTS_CUDA(cudaMemsetAsync(b->kpad_g, 0, std::max(ns, 4LL) * sizeof(R), st));
-        k_fill_slots<<<grid_for(m), TPB, 0, st>>>(k2s, m, b->grp_lvl, b->lvl_pair, b->pair_ab,
-                                                  b->pair_slot, b->kpad_ab, bps);
-        k_fill_slot_g<R><<<grid_for(m), TPB, 0, st>>>((const R *)b->pair_g, b->pair_slot, m,
-                                                       (R *)b->kpad_g);
+        if (!built) {
+            set_layout(b, MTS_DAMP_BLOCKS, 0);
+            bool no_fit = false;
+            MTS_TRY((build_damping<R, D>(b, tmp, st, cell, &no_fit)));
+        }
     }
-    int *dcol = tmp.get<int>(16);
-    NEED(dcol);
-    k_col_off<<<grid_for(ng + 1), TPB, 0, st>>>(gcol, ng, nbk, dcol);
-    MTS_TRY(to_host(b->col_off, dcol, nbk + 1, st));
-
-    {
-        unsigned int *mx = tmp.get<unsigned int>(2);
-        NEED(mx);
-        MTS_CUDA(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned), st));
-        k_group_max<<<grid_for(ng), TPB, 0, st>>>(b->lvl_pair, b->grp_lvl, ng, mx);
-        unsigned int hm[2];
-        MTS_TRY(to_host(hm, mx, 2, st));
-        b->max_group_pairs = (int)hm[0];
-        b->max_group_levels = (int)hm[1];
-    }
-
     // -- Morton tiles and their halos (particles + neighbours), local ELL
     MTS_TRY(build_tiles(b, tmp, st, sizeof(R) == 4 ? 256 : 128));
 

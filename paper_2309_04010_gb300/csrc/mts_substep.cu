@@ -58,7 +58,7 @@ __device__ __forceinline__ int stage_halo(const Args<R> &A, R *sX, R *sY, const 
         for (int u = 0; u < U; ++u) {
             const int k = k0 + u * blockDim.x;
             if (g[u] < 0) continue;
-            cp_async_reals<R, P>(sX + (size_t)k * P, A.X + (size_t)g[u] * P);
+            if (sX) cp_async_reals<R, P>(sX + (size_t)k * P, A.X + (size_t)g[u] * P);
             if (sY) cp_async_reals<R, NY>(sY + (size_t)k * NY, Y + (size_t)g[u] * NY);
         }
     }
@@ -186,7 +186,20 @@ __global__ void __launch_bounds__(256) k_stress(Args<R> A) {
             for (int k = 0; k < D; ++k) acc += P3[r][k] * B[k][c];
             PB[r][c] = acc;
         }
-    st_mat<R, D>(A.PB + i * MatS<D>::v, PB);
+    if constexpr (D == 3) {
+        // force record: X then P B0 row-major, 12 reals (three 16-byte rows)
+        R rec[12];
+        ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(rec), sX + A.lself[i] * P);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) rec[3 + 3 * r + c] = PB[r][c];
+        st_vec<R, 4>(A.PB + i * 12, *reinterpret_cast<const R(*)[4]>(rec));
+        st_vec<R, 4>(A.PB + i * 12 + 4, *reinterpret_cast<const R(*)[4]>(rec + 4));
+        st_vec<R, 4>(A.PB + i * 12 + 8, *reinterpret_cast<const R(*)[4]>(rec + 8));
+    } else {
+        st_mat<R, D>(A.PB + i * MatS<D>::v, PB);
+    }
 }
 
 // --------------------------------------------------------------------- K_B
@@ -196,28 +209,34 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
     constexpr int P = Pad<D>::v;
     constexpr int MS = MatS<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
+    // 3D: one 12-real record per halo particle (X, then P B0 row-major);
+    // 2D: X and P B0 in two arrays
     R *sX = reinterpret_cast<R *>(smem);
-    R *sP = reinterpret_cast<R *>(smem + second_off<R, P>(A.max_halo));
-    stage_halo<R, P, MS>(A, sX, sP, A.PB);
+    R *sP = D == 3 ? sX : reinterpret_cast<R *>(smem + second_off<R, P>(A.max_halo));
+    stage_halo<R, P, MS>(A, D == 3 ? nullptr : sX, sP, A.PB);
     const long long t = blockIdx.x;
     const long long i = t * A.T + threadIdx.x;
     double amax = 0.0, fm[3] = {0.0, 0.0, 0.0};
     if (i < A.n) {
         const int li = A.lself[i];
         R xa[P];
-        ld_vec<R, P>(xa, sX + li * P);
         R Pa[D][D];
         if constexpr (D == 2) {
+            ld_vec<R, P>(xa, sX + li * P);
             R q[4];
             ld_vec<R, 4>(q, sP + li * 4);
             Pa[0][0] = q[0]; Pa[0][1] = q[1]; Pa[1][0] = q[2]; Pa[1][1] = q[3];
         } else {
+            R q[12];
+            ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(q), sP + li * 12);
+            ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(q + 4), sP + li * 12 + 4);
+            ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(q + 8), sP + li * 12 + 8);
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                R q[4];
-                ld_vec<R, 4>(q, sP + li * 12 + 4 * r);
-                Pa[r][0] = q[0]; Pa[r][1] = q[1]; Pa[r][2] = q[2];
-            }
+            for (int k = 0; k < 3; ++k) xa[k] = q[k];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Pa[r][c] = q[3 + 3 * r + c];
         }
         // a_a = (PB_a sum_b g_ab + sum_b PB_b g_ab) / rho0, g_ab = V grad_a W_ab
         R acc[D], gs[D];
@@ -228,12 +247,19 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
         const int w = A.tile_w[t];
         const R inv_h = A.inv_h, kcoef = A.kcoef;
         for_each_neighbour(row, T, w, [&](int l) {
-            R xb[P];
-            ld_vec<R, P>(xb, sX + l * P);
+            R q[12];
+            if constexpr (D == 2) {
+                ld_vec<R, 2>(*reinterpret_cast<R(*)[2]>(q), sX + l * 2);
+                ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(q + 3), sP + l * 4);
+            } else {
+                ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(q), sP + l * 12);
+                ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(q + 4), sP + l * 12 + 4);
+                ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(q + 8), sP + l * 12 + 8);
+            }
             R d[D], r2 = R(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                d[k] = xa[k] - xb[k];
+                d[k] = xa[k] - q[k];
                 r2 += d[k] * d[k];
             }
             const R tt = R(1) - R(0.5) * nsqrt(r2) * inv_h;
@@ -243,18 +269,12 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
                 d[k] *= f;
                 gs[k] += d[k];
             }
-            if constexpr (D == 2) {
-                R q[4];
-                ld_vec<R, 4>(q, sP + l * 4);
-                acc[0] += q[0] * d[0] + q[1] * d[1];
-                acc[1] += q[2] * d[0] + q[3] * d[1];
-            } else {
 #pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    R q[4];
-                    ld_vec<R, 4>(q, sP + l * 12 + 4 * r);
-                    acc[r] += q[0] * d[0] + q[1] * d[1] + q[2] * d[2];
-                }
+            for (int r = 0; r < D; ++r) {
+                R sum = R(0);
+#pragma unroll
+                for (int c = 0; c < D; ++c) sum += q[3 + D * r + c] * d[c];
+                acc[r] += sum;
             }
         });
 #pragma unroll
@@ -331,12 +351,9 @@ template <class R> __device__ __forceinline__ R fast_div(R a, R b) { return a / 
 template <> __device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
 
 template <class R, int D>
-__device__ __forceinline__ void damp_pair(uint32_t w, R g, unsigned char *svb, const uint8_t *sf,
-                                          R hcim, R im) {
+__device__ __forceinline__ void damp_apply(R *pa, R *pb, R g, const uint8_t *sf, uint32_t ia,
+                                           uint32_t ib, R hcim) {
     constexpr int P = Pad<D>::v;
-    constexpr int BPS = P * (int)sizeof(R);
-    R *pa = reinterpret_cast<R *>(svb + (w & 0xffffu));
-    R *pb = reinterpret_cast<R *>(svb + (w >> 16));
     R va[P], vb[P];
     ld_vec<R, P>(va, pa);
     ld_vec<R, P>(vb, pb);
@@ -355,7 +372,7 @@ __device__ __forceinline__ void damp_pair(uint32_t w, R g, unsigned char *svb, c
         const R xm = -hcim * g;
         const R f2 = fast_div<R>(xm, R(1) + R(2) * xm);
         const R f1 = fast_div<R>(xm, R(1) + xm);
-        const uint8_t fa = sf[(w & 0xffffu) / BPS], fb = sf[(w >> 16) / BPS];
+        const uint8_t fa = sf[ia], fb = sf[ib];
 #pragma unroll
         for (int q = 0; q < D; ++q) {
             const bool a_free = !((fa >> q) & 1), b_free = !((fb >> q) & 1);
@@ -368,6 +385,15 @@ __device__ __forceinline__ void damp_pair(uint32_t w, R g, unsigned char *svb, c
     }
     st_vec<R, P>(pa, va);
     st_vec<R, P>(pb, vb);
+}
+
+template <class R, int D>
+__device__ __forceinline__ void damp_pair(uint32_t w, R g, unsigned char *svb, const uint8_t *sf,
+                                          R hcim, R /*im*/) {
+    constexpr int BPS = Pad<D>::v * (int)sizeof(R);
+    const uint32_t oa = w & 0xffffu, ob = w >> 16;
+    damp_apply<R, D>(reinterpret_cast<R *>(svb + oa), reinterpret_cast<R *>(svb + ob), g, sf,
+                     oa / BPS, ob / BPS, hcim);
 }
 
 template <class R, int D>
@@ -455,6 +481,156 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
             ld_vec<R, P>(vv, sv + (e * mb + t) * P);
             st_vec<R, P>(A.v + (long long)(ts[e] + t) * P, vv);
         }
+}
+
+// ------------------------------------------------- damping, wide layout
+// One CTA per owner group.  Shared memory: the touched blocks' velocities and
+// flags (gathered through the block-sorted permutation), the group's level
+// offsets, and a ring of three level buffers (pair words with 16-bit slot
+// indices, signed coefficients) filled by cp.async two levels ahead of the
+// level being applied; one barrier per level.
+__host__ __device__ inline void wide_offsets(int slots, int maxl, int lc, int P, int rs,
+                                             size_t off[4], size_t *total) {
+    auto r16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    off[0] = r16((size_t)slots * P * rs);          // flags
+    off[1] = off[0] + r16((size_t)slots);           // level offsets
+    off[2] = off[1] + r16((size_t)(maxl + 1) * 4);  // ring of pair words
+    off[3] = off[2] + r16((size_t)kWideRing * lc * 4);   // ring of coefficients
+    *total = off[3] + r16((size_t)kWideRing * lc * rs);
+}
+
+template <class R, int D>
+__device__ __forceinline__ void wide_sweep(bool fwd, int nl, const int32_t *slv, long long p0,
+                                           const uint32_t *gw, const R *gg, uint32_t *sw, R *sgr,
+                                           int lc, R *sv, const uint8_t *sf, R hcim) {
+    constexpr int P = Pad<D>::v;
+    const int tid = threadIdx.x;
+    auto issue = [&](int i) {
+        if (i < nl) {
+            const int L = fwd ? i : nl - 1 - i;
+            const int s0 = slv[L], cnt = slv[L + 1] - s0;
+            const int buf = (i % kWideRing) * lc;
+            for (int k = tid; k < cnt; k += kWideThreads) {
+                cp_async(sw + buf + k, gw + p0 + s0 + k, 4);
+                cp_async(sgr + buf + k, gg + p0 + s0 + k, (int)sizeof(R));
+            }
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int i = 0; i < kWideRing - 1; ++i) issue(i);
+    for (int i = 0; i < nl; ++i) {
+        cp_async_wait_group<kWideRing - 2>();   // level i has landed (later ones may be in flight)
+        __syncthreads();            // ... for every thread; level i - 1 applied everywhere
+        issue(i + kWideRing - 1);   // into the buffer level i - 1 used
+        const int L = fwd ? i : nl - 1 - i;
+        const int cnt = slv[L + 1] - slv[L];
+        const int buf = (i % kWideRing) * lc;
+        for (int k = tid; k < cnt; k += kWideThreads) {
+            const uint32_t w = sw[buf + k];
+            const R gc = sgr[buf + k];
+            const uint32_t ia = w & 0xffffu, ib = w >> 16;
+            damp_apply<R, D>(sv + (size_t)ia * P, sv + (size_t)ib * P, gc, sf, ia, ib, hcim);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+}
+
+template <class R, int D>
+__global__ void __launch_bounds__(kWideThreads) k_damp_wide(Args<R> A, long long g_begin, int mode) {
+    if (A.ctrl->done) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int P = Pad<D>::v;
+    constexpr int NB = 1 << D;
+    const long long g = g_begin + blockIdx.x;
+    const int tid = threadIdx.x;
+    const int mb = A.mb, nbw = A.nbw, lc = A.max_level_pairs;
+    size_t off[4], smem_total;
+    wide_offsets(nbw * mb, A.max_group_levels, lc, P, (int)sizeof(R), off, &smem_total);
+    R *sv = reinterpret_cast<R *>(smem);
+    uint8_t *sf = smem + off[0];
+    int32_t *slv = reinterpret_cast<int32_t *>(smem + off[1]);
+    uint32_t *sw = reinterpret_cast<uint32_t *>(smem + off[2]);
+    R *sgr = reinterpret_cast<R *>(smem + off[3]);
+    // touched blocks, flattened: entry j < total lies in block e with
+    // pre[e] <= j < pre[e + 1]
+    int ts[NB], pre[NB + 1];
+    pre[0] = 0;
+#pragma unroll
+    for (int e = 0; e < NB; ++e) {
+        ts[e] = e < nbw ? __ldg(A.touch_start + g * NB + e) : 0;
+        pre[e + 1] = pre[e] + (e < nbw ? __ldg(A.touch_cnt + g * NB + e) : 0);
+    }
+    const int total = pre[NB];
+    auto locate = [&](int j, int &src, int &slot) {
+#pragma unroll
+        for (int e = 0; e < NB; ++e)
+            if (j >= pre[e]) {
+                src = ts[e] + (j - pre[e]);
+                slot = e * mb + (j - pre[e]);
+            }
+    };
+    const int l0 = __ldg(A.grp_lvl + g), l1 = __ldg(A.grp_lvl + g + 1);
+    const int nl = l1 - l0;
+    const long long p0 = __ldg(A.lvl_pair + l0);
+    // gather in batches of kSB per thread: indices and flags (block-sorted,
+    // contiguous) first, then the velocity copies that depend on them
+    constexpr int kSB = 8;
+    for (int j0 = 0; j0 < total; j0 += kSB * kWideThreads) {
+        int pp[kSB], sl[kSB];
+        uint8_t ff[kSB];
+#pragma unroll
+        for (int u = 0; u < kSB; ++u) {
+            const int j = j0 + u * kWideThreads + tid;
+            sl[u] = -1;
+            if (j < total) {
+                int src = 0;
+                locate(j, src, sl[u]);
+                pp[u] = __ldg(A.bperm + src);
+                ff[u] = __ldg(A.bflags + src);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kSB; ++u)
+            if (sl[u] >= 0) {
+                cp_async_reals<R, P>(sv + (size_t)sl[u] * P, A.v + (long long)pp[u] * P);
+                sf[sl[u]] = ff[u];
+            }
+    }
+    for (int t = tid; t <= nl; t += kWideThreads) slv[t] = (int)(__ldg(A.lvl_pair + l0 + t) - p0);
+    cp_async_wait_all();
+    __syncthreads();
+    const R hcim = (R)(0.5 * A.ctrl->dt) * A.eta * (R)(1.0 / A.mass);   // (dt/2) eta / m
+    if (mode & 1) wide_sweep<R, D>(true, nl, slv, p0, A.pair_ab, A.pair_g, sw, sgr, lc, sv, sf, hcim);
+    if (mode & 2) wide_sweep<R, D>(false, nl, slv, p0, A.pair_ab, A.pair_g, sw, sgr, lc, sv, sf, hcim);
+    for (int j0 = 0; j0 < total; j0 += kSB * kWideThreads) {
+        int pp[kSB], sl[kSB];
+#pragma unroll
+        for (int u = 0; u < kSB; ++u) {
+            const int j = j0 + u * kWideThreads + tid;
+            sl[u] = -1;
+            if (j < total) {
+                int src = 0;
+                locate(j, src, sl[u]);
+                pp[u] = __ldg(A.bperm + src);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kSB; ++u)
+            if (sl[u] >= 0) {
+                R vv[P];
+                ld_vec<R, P>(vv, sv + (size_t)sl[u] * P);
+                st_vec<R, P>(A.v + (long long)pp[u] * P, vv);
+            }
+    }
+}
+
+// flags in block-sorted order (the wide damping kernel's contiguous reads)
+__global__ void k_gather_flags(const uint8_t *flags, const int32_t *bperm, long long n,
+                               uint8_t *bflags) {
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s < n) bflags[s] = flags[bperm[s]];
 }
 
 // pair coefficients: negative when either particle has a constrained axis
@@ -763,7 +939,8 @@ __global__ void k_field_out(Args<R> A, int field, const long long *perm, const d
     case MTS_F_PB:
         for (int r = 0; r < D; ++r)
             for (int c = 0; c < D; ++c)
-                out[i * D * D + r * D + c] = (double)A.PB[s * MatS<D>::v + r * P + c];
+                out[i * D * D + r * D + c] =
+                    (double)A.PB[s * MatS<D>::v + (D == 3 ? 3 + 3 * r + c : r * P + c)];
         break;
     case MTS_F_C: out[i] = (double)A.c[s]; break;
     case MTS_F_ALPHA: out[i] = (double)A.cp[s * 8 + 6]; break;
@@ -884,7 +1061,11 @@ Args<R> make_args(mts_body *b) {
     A.grp_lvl = b->grp_lvl;
     A.touch_start = b->touch_start;
     A.touch_cnt = b->touch_cnt;
+    A.bperm = b->bperm;
+    A.bflags = b->bflags;
     A.mb = b->mb;
+    A.nbw = b->nbw;
+    A.max_level_pairs = b->max_level_pairs;
     A.cond = b->cond;
     A.use_cond = b->use_cond;
     A.ctrl = b->ctrl;
@@ -897,6 +1078,7 @@ template <class R, int D> size_t smem_stress(const mts_body *b) {
     return second_off<R, Pad<D>::v>(b->max_halo) + (size_t)b->max_halo * Pad<D>::v * sizeof(R);
 }
 template <class R, int D> size_t smem_force(const mts_body *b) {
+    if (D == 3) return (size_t)b->max_halo * 12 * sizeof(R);
     return second_off<R, Pad<D>::v>(b->max_halo) + (size_t)b->max_halo * MatS<D>::v * sizeof(R);
 }
 template <class R, int D> size_t smem_diffuse(const mts_body *b) {
@@ -936,22 +1118,30 @@ mts_status damping_t(mts_body *b, long long *nlaunch) {
     if (nlaunch) *nlaunch = 0;
     if (b->eta == 0.0 || b->npairs == 0) return MTS_OK;
     Args<R> A = make_args<R>(b);
-    const size_t smem = smem_damp<R, D>(b);
+    const bool wide = b->damp_layout == MTS_DAMP_WIDE;
+    const size_t smem = wide ? damp_wide_smem(b) : smem_damp<R, D>(b);
     const int W = damp_warps<R, D>(b);
-    const int ncol = 1 << D;
+    int cols[8], nc = 0;
+    for (int c = 0; c < (1 << D); ++c)
+        if (b->col_off[c + 1] > b->col_off[c]) cols[nc++] = c;
     auto launch = [&](int c, int mode) -> mts_status {
         const long long g0 = b->col_off[c], g1 = b->col_off[c + 1];
-        if (g1 <= g0) return MTS_OK;
-        const unsigned grid = (unsigned)((g1 - g0 + W - 1) / W);
-        k_damp<R, D><<<grid, W * 32, smem, b->ctx->stream>>>(A, g0, g1, mode);
+        if (wide) {
+            k_damp_wide<R, D><<<(unsigned)(g1 - g0), kWideThreads, smem, b->ctx->stream>>>(A, g0, mode);
+        } else {
+            const unsigned grid = (unsigned)((g1 - g0 + W - 1) / W);
+            k_damp<R, D><<<grid, W * 32, smem, b->ctx->stream>>>(A, g0, g1, mode);
+        }
         MTS_CUDA(cudaGetLastError());
         if (nlaunch) ++*nlaunch;
         return MTS_OK;
     };
-    // symmetric sweep: forward 0..C-2, fused forward+reverse on C-1, reverse C-2..0
-    for (int c = 0; c < ncol - 1; ++c) MTS_TRY(launch(c, 1));
-    MTS_TRY(launch(ncol - 1, 3));
-    for (int c = ncol - 2; c >= 0; --c) MTS_TRY(launch(c, 2));
+    // symmetric sweep over the non-empty colours: forward on all but the
+    // last, forward + reverse fused on the last, then reverse
+    if (nc == 0) return MTS_OK;
+    for (int i = 0; i < nc - 1; ++i) MTS_TRY(launch(cols[i], 1));
+    MTS_TRY(launch(cols[nc - 1], 3));
+    for (int i = nc - 2; i >= 0; --i) MTS_TRY(launch(cols[i], 2));
     return MTS_OK;
 }
 
@@ -960,7 +1150,9 @@ mts_status damping_t(mts_body *b, long long *nlaunch) {
 template <class R, int D>
 mts_status prepare_t(mts_body *b) {
     const size_t lim = 227 * 1024;
-    const size_t sd = smem_damp<R, D>(b), sa = smem_stress<R, D>(b), sf = smem_force<R, D>(b),
+    const bool wide = b->damp_layout == MTS_DAMP_WIDE;
+    const size_t sd = wide ? damp_wide_smem(b) : smem_damp<R, D>(b), sa = smem_stress<R, D>(b),
+                 sf = smem_force<R, D>(b),
                  sc = smem_diffuse<R, D>(b);
     if (sd > lim || sa > lim || sf > lim || sc > lim) {
         set_error("shared-memory staging too large (damping %zu, stress %zu, force %zu bytes; "
@@ -971,7 +1163,10 @@ mts_status prepare_t(mts_body *b) {
         return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)std::max<size_t>(bytes, 48 * 1024));
     };
-    MTS_CUDA(attr((const void *)k_damp<R, D>, sd));
+    if (wide)
+        MTS_CUDA(attr((const void *)k_damp_wide<R, D>, sd));
+    else
+        MTS_CUDA(attr((const void *)k_damp<R, D>, sd));
     MTS_CUDA(attr((const void *)k_stress<R, D, MTS_ELASTIC_SVK>, sa));
     MTS_CUDA(attr((const void *)k_stress<R, D, MTS_NEOHOOKE_J2>, sa));
     MTS_CUDA(attr((const void *)k_defgrad<R, D>, sa));
@@ -1051,7 +1246,17 @@ mts_status launch_damping(mts_body *b, long long *launches) { return DISPATCH(da
 mts_status launch_drift(mts_body *b) { return DISPATCH(drift_t, b); }
 mts_status prepare_kernels(mts_body *b) { return DISPATCH(prepare_t, b); }
 
+size_t damp_wide_smem(const mts_body *b) {
+    size_t off[4], total = 0;
+    wide_offsets(b->nbw * b->mb, b->max_group_levels, b->max_level_pairs, b->dim == 2 ? 2 : 4,
+                 (int)b->rsize, off, &total);
+    return total;
+}
+
 mts_status update_pair_fixbits(mts_body *b) {
+    if (b->bflags)
+        k_gather_flags<<<(unsigned)((b->n + 255) / 256), 256, 0, b->ctx->stream>>>(
+            b->flags, b->bperm, b->n, b->bflags);
     if (b->npairs == 0) return MTS_OK;
     const unsigned grid = (unsigned)((b->npairs + 255) / 256);
     if (b->precision == MTS_FP64)

@@ -26,6 +26,8 @@ OK = 0
 ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_SINGULAR_B, ERR_NONFINITE, ERR_TIMEOUT, \
     ERR_UNSTABLE_DT, ERR_STATE = range(1, 9)
 FP64, MIXED = 0, 1
+DAMP_AUTO, DAMP_BLOCKS, DAMP_WIDE = 0, 1, 2
+WHOLE_AXIS = 62
 ELASTIC_SVK, NEOHOOKE_J2 = 0, 1
 F_U, F_X, F_V, F_DEFGRAD, F_PB, F_C, F_ALPHA, F_CPINV, F_ACC = range(9)
 
@@ -60,7 +62,8 @@ class Allocator(C.Structure):
 
 class BodyDesc(C.Structure):
     _fields_ = [("dim", C.c_int32), ("precision", C.c_int32), ("n", C.c_int64),
-                ("X", C.c_void_p), ("dx", C.c_double), ("h_over_dx", C.c_double)]
+                ("X", C.c_void_p), ("dx", C.c_double), ("h_over_dx", C.c_double),
+                ("damp_layout", C.c_int32), ("reserved", C.c_int32)]
 
 
 class StepParams(C.Structure):
@@ -102,6 +105,7 @@ def lib():
         "mts_body_create": [vp, C.POINTER(BodyDesc), C.POINTER(vp)],
         "mts_body_destroy": [vp],
         "mts_body_permutation": [vp, vp],
+        "mts_body_damping_layout": [vp, vp, C.POINTER(i32)],
         "mts_body_neighbors": [vp, C.POINTER(i64), vp, vp],
         "mts_body_colouring": [vp, C.POINTER(i64), vp, vp, vp, vp, vp],
         "mts_set_material": [vp, C.c_int, d, d, d, d, d, d, d],
@@ -200,12 +204,12 @@ class Body:
     """mts_body: a particle body with its fixed neighbourhood on the GPU."""
 
     def __init__(self, ctx: Context, X: np.ndarray, dx: float, h_over_dx: float = 1.3,
-                 precision: int = FP64):
+                 precision: int = FP64, damp_layout: int = DAMP_AUTO):
         X = np.ascontiguousarray(X, dtype=np.float64)
         self.n, self.dim = X.shape
         self.ctx = ctx
         self.precision = precision
-        desc = BodyDesc(self.dim, precision, self.n, X.ctypes.data, dx, h_over_dx)
+        desc = BodyDesc(self.dim, precision, self.n, X.ctypes.data, dx, h_over_dx, damp_layout, 0)
         h = C.c_void_p()
         _check(lib().mts_body_create(ctx.handle, C.byref(desc), C.byref(h)), "mts_body_create")
         self._h = h
@@ -229,6 +233,14 @@ class Body:
         p = np.zeros(self.n, np.int64)
         _check(lib().mts_body_permutation(self._h, _ptr(p)), "mts_body_permutation")
         return p
+
+    def damping_layout(self):
+        """(per-axis block shifts, level cap) of the damping order in use."""
+        sh = np.zeros(3, np.int32)
+        cap = C.c_int32()
+        _check(lib().mts_body_damping_layout(self._h, _ptr(sh), C.byref(cap)),
+               "mts_body_damping_layout")
+        return tuple(int(x) for x in sh[:self.dim]), int(cap.value)
 
     def neighbors(self):
         nnz = C.c_int64()
@@ -319,9 +331,9 @@ class Body:
         _check(lib().mts_write_field(self._h, field, _ptr(a), a.size), "mts_write_field")
 
 
-def body_from_case(ctx: Context, case, precision: int = FP64) -> Body:
+def body_from_case(ctx: Context, case, precision: int = FP64, damp_layout: int = DAMP_AUTO) -> Body:
     """Body with the material, damping, diffusion and BCs of a synth Case."""
-    b = Body(ctx, case.X, case.dx, case.h_over_dx, precision)
+    b = Body(ctx, case.X, case.dx, case.h_over_dx, precision, damp_layout)
     m = case.material
     b.set_material(ELASTIC_SVK if m.model == "svk" else NEOHOOKE_J2, m.rho0, m.E, m.nu,
                    m.sigma0, m.sigma_inf, m.delta, m.H)

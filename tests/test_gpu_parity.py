@@ -42,8 +42,10 @@ def small_strip(nx=120, ny=20):
     return c
 
 
-def pair(ctx, case, precision=M.FP64):
-    return O.body_from_case(case), M.body_from_case(ctx, case, precision)
+def pair(ctx, case, precision=M.FP64, layout=M.DAMP_AUTO):
+    """Library body and an oracle body with the same damping-order layout."""
+    gb = M.body_from_case(ctx, case, precision, layout)
+    return O.body_from_case(case, damp_layout=gb.damping_layout()), gb
 
 
 CASES = {
@@ -64,12 +66,21 @@ def _irregular3d():
 
 
 # ---------------------------------------------------------------- setup
+LAYOUTS = {"auto": M.DAMP_AUTO, "blocks": M.DAMP_BLOCKS, "wide": M.DAMP_WIDE}
+
+
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("precision", [M.FP64, M.MIXED])
-def test_setup_products_bit_exact(ctx, name, precision):
+@pytest.mark.parametrize("layout", list(LAYOUTS))
+def test_setup_products_bit_exact(ctx, name, precision, layout):
     case = CASES[name]()
-    ob = O.OracleBody(case.X, case.dx, case.h_over_dx)
-    gb = M.Body(ctx, case.X, case.dx, case.h_over_dx, precision)
+    gb = M.Body(ctx, case.X, case.dx, case.h_over_dx, precision, LAYOUTS[layout])
+    shifts, cap = gb.damping_layout()
+    if layout == "blocks":
+        assert cap == 32 and M.WHOLE_AXIS not in shifts
+    if layout == "wide":
+        assert cap == 0 and list(shifts).count(M.WHOLE_AXIS) == 1
+    ob = O.OracleBody(case.X, case.dx, case.h_over_dx, damp_layout=(shifts, cap))
     assert np.array_equal(gb.permutation(), ob.perm())
     go, gi = gb.neighbors()
     oo, oi = ob.neighbors()
@@ -91,6 +102,10 @@ def test_setup_rejects_bad_bodies(ctx):
     with pytest.raises(M.MtsError) as e:
         M.Body(ctx, np.zeros((1, 3)), 1.0)
     assert e.value.status == M.ERR_INVALID_ARG
+    c = B.bar2d(nx=12, ny=5)
+    with pytest.raises(M.MtsError) as e:
+        M.Body(ctx, c.X, c.dx, damp_layout=3)
+    assert e.value.status == M.ERR_INVALID_ARG
 
 
 # ---------------------------------------------------------------- one substep
@@ -103,7 +118,8 @@ def _state(case, seed, ustrain):
 
 @pytest.mark.parametrize("name,ustrain", [("bar2d", 1e-3), ("cyl3d", 2e-2), ("strip2d", 1e-3),
                                           ("box3d_irregular", 1e-3)])
-def test_fp64_single_substep_every_stage(ctx, name, ustrain):
+@pytest.mark.parametrize("layout", ["blocks", "wide"])
+def test_fp64_single_substep_every_stage(ctx, name, ustrain, layout):
     case = CASES[name]()
     U, V = _state(case, 5, ustrain)
     dt = 0.6 * case.h_over_dx * case.dx / math.sqrt(
@@ -111,7 +127,7 @@ def test_fp64_single_substep_every_stage(ctx, name, ustrain):
     rng = np.random.default_rng(3)
     C0 = rng.uniform(0, 1, case.n) if case.diffusion else None
     for upto in (1, 2, 3, 4):
-        ob, gb = pair(ctx, case)
+        ob, gb = pair(ctx, case, layout=LAYOUTS[layout])
         for b in (ob, gb):
             b.write(M.F_U, U)
             b.write(M.F_V, V)
@@ -145,8 +161,9 @@ def test_affine_field_exact_F(ctx):
 
 
 # ---------------------------------------------------------------- slow steps
-def _run_both(ctx, case, nslow, nsub, precision=M.FP64, ke_tol=-1.0, dt_slow=0.0):
-    ob, gb = pair(ctx, case, precision)
+def _run_both(ctx, case, nslow, nsub, precision=M.FP64, ke_tol=-1.0, dt_slow=0.0,
+              layout=M.DAMP_AUTO):
+    ob, gb = pair(ctx, case, precision, layout)
     reps = []
     for l in range(1, nslow + 1):
         ramp = l / max(case.plan.n_ramp, 1)
@@ -169,8 +186,9 @@ def test_device_loop_counts_and_launches(ctx):
     assert r2.substeps == 37 and r2.kernel_launches == 4 + 40 * per   # 5 chunks of 8
 
 
-def test_fp64_slow_steps_bar2d(ctx):
-    ob, gb, reps = _run_both(ctx, B.bar2d(), 3, 300)
+@pytest.mark.parametrize("layout", ["blocks", "wide"])
+def test_fp64_slow_steps_bar2d(ctx, layout):
+    ob, gb, reps = _run_both(ctx, B.bar2d(), 3, 300, layout=LAYOUTS[layout])
     assert rel(gb.read(M.F_U), ob.read(O.F_U)) < 1e-9
     assert rel(gb.read(M.F_V), ob.read(O.F_V)) < 1e-9
     for rg, ro in reps:
@@ -181,9 +199,10 @@ def test_fp64_slow_steps_bar2d(ctx):
         assert abs(rg.dt_last - ro.dt_last) < 1e-12 * ro.dt_last
 
 
-def test_fp64_slow_steps_j2_cylinder(ctx):
+@pytest.mark.parametrize("layout", ["blocks", "wide"])
+def test_fp64_slow_steps_j2_cylinder(ctx, layout):
     case = small_cylinder()
-    ob, gb, reps = _run_both(ctx, case, 4, 150)
+    ob, gb, reps = _run_both(ctx, case, 4, 150, layout=LAYOUTS[layout])
     assert ob.read(O.F_ALPHA).max() > 0
     assert rel(gb.read(M.F_U), ob.read(O.F_U)) < 1e-9
     assert rel(gb.read(M.F_ALPHA), ob.read(O.F_ALPHA)) < 1e-9
@@ -237,19 +256,23 @@ def test_mixed_precision_concentration(ctx):
     assert rel(gb.read(M.F_C), ob.read(O.F_C)) < 1e-5
 
 
-def test_mixed_precision_j2_cylinder(ctx):
+@pytest.mark.parametrize("layout", ["blocks", "wide"])
+def test_mixed_precision_j2_cylinder(ctx, layout):
     case = small_cylinder()
-    ob, gb, reps = _run_both(ctx, case, 3, 300, precision=M.MIXED)
+    ob, gb, reps = _run_both(ctx, case, 3, 300, precision=M.MIXED, layout=LAYOUTS[layout])
     assert rel(gb.read(M.F_U), ob.read(O.F_U)) < 1e-4
 
 
 # ---------------------------------------------------------------- full size
-@pytest.mark.parametrize("precision,tol", [(M.FP64, 1e-12), (M.MIXED, 1e-4)])
-def test_full_size_cylinder_first_substeps(ctx, precision, tol):
+@pytest.mark.parametrize("precision,tol,layout", [(M.FP64, 1e-12, "auto"), (M.MIXED, 1e-4, "auto"),
+                                                 (M.FP64, 1e-12, "blocks")])
+def test_full_size_cylinder_first_substeps(ctx, precision, tol, layout):
     """The benchmark workload (3D J2 cylinder, 252,800 particles) at full size:
     setup products bit-exact, then two substeps after the first load jump."""
     case = B.cylinder3d()
-    ob, gb = pair(ctx, case, precision)
+    ob, gb = pair(ctx, case, precision, LAYOUTS[layout])
+    if layout == "auto":      # 200 x 40 x 40 cells: the last short axis is unblocked
+        assert gb.damping_layout() == ((2, 2, M.WHOLE_AXIS), 0)
     off_g, idx_g = gb.neighbors()
     off_o, idx_o = ob.neighbors()
     assert np.array_equal(off_g, off_o) and np.array_equal(idx_g, idx_o)
