@@ -161,27 +161,10 @@ def cylinder_case():
     return B.cylinder3d()
 
 
-def auto_layout(case):
-    """Damping-order layout that the library's automatic choice gives this body:
-    the shortest axis (ties to the higher one) unblocked with no level cap when
-    it spans at most 64 cells in 3D / 256 in 2D, else blocks on every axis with
-    32 pairs per level.  (The library also requires an owner group to fit one
-    CTA's shared memory, which holds for the workloads here.)"""
-    import numpy as np
-
-    import oracle
-    d = case.X.shape[1]
-    cells = np.floor((case.X - case.X.min(axis=0)) / case.dx).max(axis=0).astype(int) + 1
-    k = max(range(d), key=lambda a: (-cells[a], a))
-    if cells[k] <= (64 if d == 3 else 256):
-        return tuple(oracle.WHOLE_AXIS if a == k else -1 for a in range(d)), 0
-    return tuple(-1 for _ in range(d)), 32
-
-
 def oracle_sample(case, substeps: int, layout=None):
     """Oracle particle-substeps/s on the host cores (setup not timed)."""
     import oracle
-    ob = oracle.body_from_case(case, damp_layout=layout or auto_layout(case))
+    ob = oracle.body_from_case(case, damp_layout=layout)
     t0 = time.perf_counter()
     ob.advance(ramp=1.0 / case.plan.n_ramp, ke_tol=-1.0, max_substeps=substeps)
     dt = time.perf_counter() - t0
@@ -193,7 +176,7 @@ def run_reference(args, rank):
         return
     import oracle
     case = cylinder_case()
-    ob = oracle.body_from_case(case, damp_layout=auto_layout(case))
+    ob = oracle.body_from_case(case)   # the library's default order: blocks, 32 per level
     total, t_all = 0, 0.0
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()

@@ -50,6 +50,7 @@ typedef enum { MTS_ELASTIC_SVK = 0, MTS_NEOHOOKE_J2 = 1 } mts_material_model;
 
 typedef struct mts_ctx mts_ctx;
 typedef struct mts_body mts_body;
+typedef struct mts_batch mts_batch;
 
 /* Device allocator hook.  alloc returns a device pointer (NULL on failure),
  * release frees it.  Pass NULL to mts_ctx_create to use cudaMalloc/cudaFree.
@@ -78,11 +79,13 @@ int mts_version(void);
 /* reference configuration).                                             */
 /* ------------------------------------------------------------------ */
 typedef enum {
-    MTS_DAMP_AUTO = 0,       /* library's choice (reported by mts_body_damping_layout) */
+    MTS_DAMP_AUTO = 0,       /* library's choice (reported by mts_body_damping_layout): */
+                             /* currently BLOCKS, the faster kernel where measured      */
     MTS_DAMP_BLOCKS = 1,     /* blocks on every axis, one warp per owner block,       */
                              /* at most 32 pairs per sub-colour                       */
     MTS_DAMP_WIDE = 2        /* shortest axis unblocked, one CTA per owner block,     */
-                             /* no cap on pairs per sub-colour                        */
+                             /* no cap on pairs per sub-colour (MTS_ERR_INVALID_ARG   */
+                             /* when an owner group does not fit one CTA)             */
 } mts_damp_layout;
 
 typedef struct {
@@ -211,6 +214,24 @@ typedef struct {
 mts_status mts_advance_slow_step(mts_body *body, const mts_step_params *params,
                                  mts_step_report *report);
 
+/* Batches: many independent bodies advanced by one graph launch per slow
+ * step (the batched multi-instance mode of the method).  The graph holds one
+ * conditional WHILE node per body with no dependencies between them, so the
+ * bodies' substep loops run concurrently on the GPU and each stops on its own
+ * kinetic-energy criterion; every body computes exactly what
+ * mts_advance_slow_step would compute for it (same kernels, same order).
+ * mts_batch_create: `count` >= 1 distinct bodies of one context, borrowed
+ * (destroy the batch before any of its bodies).  mts_batch_advance: params
+ * and reports are arrays of `count`, in body order; params[i].check_every is
+ * ignored (the loops always run on the device); each body's load jump and
+ * diffusion step run before the launch.  Errors as mts_advance_slow_step for
+ * the first failing body (its index in the message); the reports of all
+ * bodies are filled as far as they ran. */
+mts_status mts_batch_create(mts_ctx *ctx, int32_t count, mts_body *const *bodies, mts_batch **out);
+mts_status mts_batch_advance(mts_batch *batch, const mts_step_params *params,
+                             mts_step_report *reports);
+void mts_batch_destroy(mts_batch *batch);
+
 /* Time one stage of every substep with CUDA events recorded inside the
  * captured graph, on the library stream: 0 = off, 1 = stress (deformation
  * gradient, stress, P B0), 2 = force and kick, 3 = the whole damping sweep
@@ -241,6 +262,57 @@ typedef enum {
  * (n times the field width), original order.  Writes: U, V, C, ALPHA, CPINV. */
 mts_status mts_read_field(mts_body *body, int32_t field, double *host_out, int64_t len);
 mts_status mts_write_field(mts_body *body, int32_t field, const double *host_in, int64_t len);
+
+/* Checkpoint / resume of the evolving state (u, its FP32 gather copy in mixed
+ * precision, v, the last acceleration, the plastic state C-bar_p^-1 and alpha,
+ * the concentration), in the library's own sorted order and storage precision,
+ * so that a load followed by the same slow steps reproduces the saved run bit
+ * for bit.  Configuration (material, damping, diffusion, BCs) is not part of
+ * the state.  mts_save_state: with host_buf == NULL only *bytes is set (the
+ * size needed); otherwise *bytes must be at least that size and receives the
+ * bytes written.  mts_load_state: the buffer must come from mts_save_state of
+ * a body with the same n, dim and precision (checked against the header:
+ * MTS_ERR_INVALID_ARG otherwise).  Both synchronise the context stream. */
+mts_status mts_save_state(const mts_body *body, void *host_buf, size_t *bytes);
+mts_status mts_load_state(mts_body *body, const void *host_buf, size_t bytes);
+
+/* ------------------------------------------------------------------ */
+/* Reverse mode (derivatives of slow steps), FP64 bodies                */
+/* ------------------------------------------------------------------ */
+/* With the substep sizes and counts of a forward run held fixed (the size
+ * rule of Sec. 4.1 and the kinetic-energy stop of Sec. 4.2 are not
+ * differentiated), a slow step is a fixed composition of maps; these calls
+ * apply its transpose to an adjoint state (u-bar, v-bar, C-bar_p^-1-bar,
+ * alpha-bar, c-bar) and accumulate the derivatives with respect to the
+ * parameters theta = (E at fixed nu, sigma_0, sigma_inf, delta, H of the
+ * hardening law App. A.3, D of Sec. 2.2, beta of App. B.2).
+ *
+ * mts_adjoint_enable: allocate the tape for up to max_substeps substeps of one
+ *   slow step (n x 12 doubles per substep in 3D) and a zero adjoint state;
+ *   MTS_ERR_STATE for a mixed-precision body.
+ * mts_adjoint_reset: zero the adjoint state and the pending seeds.
+ * mts_adjoint_seed: add to the adjoint state the derivative of an objective
+ *   with respect to the outputs of the step about to be reversed: u_bar
+ *   (host, n x dim, original order, or NULL) with respect to u at the end of
+ *   the step, tip_bar[dim] with respect to the reported tip deflection (or
+ *   NULL), force_bar[dim] with respect to the reported end force (or NULL).
+ * mts_adjoint_slow_step: precondition: the body's state is the one at the
+ *   start of the slow step to reverse (mts_load_state of a checkpoint) and
+ *   params / substeps are those of its forward run.  Recomputes the step with
+ *   a tape (leaving the body at its end, as the forward run did), then applies
+ *   the transpose; afterwards the adjoint state is that of the state at the
+ *   start of the step, and theta_bar[0..6] (host) has the step's parameter
+ *   derivatives ADDED.  MTS_ERR_STATE if the recomputed step does not run
+ *   exactly `substeps` substeps.
+ * mts_read_adjoint: the adjoint of a state field (U, V, C, ALPHA, CPINV), host,
+ *   original order, as mts_read_field. */
+mts_status mts_adjoint_enable(mts_body *body, int64_t max_substeps);
+mts_status mts_adjoint_reset(mts_body *body);
+mts_status mts_adjoint_seed(mts_body *body, const double *u_bar, const double *tip_bar,
+                            const double *force_bar);
+mts_status mts_adjoint_slow_step(mts_body *body, const mts_step_params *params, int64_t substeps,
+                                 double *theta_bar);
+mts_status mts_read_adjoint(mts_body *body, int32_t field, double *host_out, int64_t len);
 
 /* ------------------------------------------------------------------ */
 /* Allocation-free reduction                                            */

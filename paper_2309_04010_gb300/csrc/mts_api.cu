@@ -91,7 +91,11 @@ void body_free(mts_body *b) {
                      (void **)&b->halo_idx, (void **)&b->lself, (void **)&b->lell,
                      (void **)&b->lell_off, (void **)&b->tile_w, (void **)&b->pair_slot,
                      (void **)&b->kpad_ab, (void **)&b->kpad_g, (void **)&b->bperm,
-                     (void **)&b->bflags};
+                     (void **)&b->bflags, (void **)&b->tape_u, (void **)&b->tape_cp,
+                     (void **)&b->tape_dt, (void **)&b->tape_c, (void **)&b->adj_u,
+                     (void **)&b->adj_v, (void **)&b->adj_cp, (void **)&b->adj_c,
+                     (void **)&b->adj_a, (void **)&b->adj_G, (void **)&b->adj_theta,
+                     (void **)&b->adj_part, (void **)&b->adj_ctrl};
     for (void **pp : ptrs) {
         dfree(b->ctx, *pp);
         *pp = nullptr;
@@ -282,6 +286,136 @@ mts_status capture_chunk(mts_body *b, int chunk) {
     return MTS_OK;
 }
 
+// Validation, load jump and diffusion step of one slow step (before its substeps).
+mts_status slow_step_begin(mts_body *b, const mts_step_params *p, long long *launches,
+                           double *c_tape = nullptr) {
+    if (!b->has_material) {
+        set_error("mts_advance_slow_step: no material set");
+        return MTS_ERR_STATE;
+    }
+    if (p->max_substeps < 1 || !std::isfinite(p->ramp_value) || !(p->dt_slow >= 0) ||
+        !std::isfinite(p->dt_slow) || !(p->dt_sub_override >= 0) || !std::isfinite(p->ke_ref) ||
+        !std::isfinite(p->ke_tol) || (p->ke_mode != 0 && p->ke_mode != 1)) {
+        set_error("mts_advance_slow_step: invalid step parameters");
+        return MTS_ERR_INVALID_ARG;
+    }
+    MTS_CUDA(cudaSetDevice(b->ctx->device));
+    if (p->dt_slow > 0) {
+        if (!b->has_diff) {
+            set_error("mts_advance_slow_step: dt_slow > 0 without diffusion");
+            return MTS_ERR_STATE;
+        }
+        double dtp, dts;
+        MTS_TRY(mts_diffusion_dt(b, &dtp, &dts));
+        if (p->dt_slow > dts * (1.0 + 1e-12) && !p->force_dt) {
+            set_error("diffusion step %g above the stable limit %g (paper's 0.5 h^2/D = %g)",
+                      p->dt_slow, dts, dtp);
+            return MTS_ERR_UNSTABLE_DT;
+        }
+    }
+    const double cs = std::sqrt(b->K / b->rho0);
+    const double dt0 = p->dt_sub_override > 0 ? p->dt_sub_override : 0.6 * b->h / cs;
+    const int use_tol = p->ke_tol >= 0 ? 1 : 0;
+    MTS_TRY(launch_reset_ctrl(b, dt0, p->dt_sub_override, p->ramp_value, p->max_substeps,
+                              p->ke_tol * p->ke_ref, p->ke_mode, use_tol));
+    MTS_TRY(launch_slow_begin(b));
+    *launches = 2;
+    if (p->dt_slow > 0) {
+        if (c_tape)   // concentration before the step, for the adjoint's D derivative
+            MTS_CUDA(cudaMemcpyAsync(c_tape, b->c, b->n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     b->ctx->stream));
+        MTS_TRY(launch_diffusion(b, p->dt_slow));
+        *launches += 2;
+    }
+    return MTS_OK;
+}
+
+// Report of a finished slow step from the host copy of the control block.
+mts_status slow_step_report(mts_body *b, mts_step_report *rep, long long launches) {
+    const Control &C = *b->h_ctrl;
+    rep->substeps = C.nsub;
+    rep->converged = C.converged;
+    rep->status = C.status;
+    rep->ke_final = C.ke;
+    rep->max_v = C.vmax;
+    rep->max_a = C.amax;
+    rep->dt_last = C.dt_last;
+    for (int k = 0; k < 3; ++k) rep->end_force[k] = k < b->dim ? C.end_force[k] : 0.0;
+    double tip[3] = {0, 0, 0};
+    if (b->tip_count > 0) {
+        MTS_TRY(launch_tip(b, tip));
+        launches += 2;
+    }
+    rep->kernel_launches = launches;
+    for (int k = 0; k < 3; ++k) rep->tip_deflection[k] = tip[k];
+    if (C.status != MTS_OK) {
+        set_error("non-finite kinetic energy after substep %lld", (long long)C.nsub);
+        return (mts_status)C.status;
+    }
+    return MTS_OK;
+}
+
+// One graph for a batch: a conditional WHILE node per body, no edges between
+// them; each body graph is that body's substep, captured with the node's own
+// conditional handle (the body's drift kernel ends only its own loop).
+mts_status capture_batch(mts_batch *bt) {
+    const int nb = (int)bt->bodies.size();
+    bool fresh = bt->graph != nullptr && (int)bt->gens.size() == nb;
+    for (int i = 0; fresh && i < nb; ++i) fresh = bt->gens[i] == bt->bodies[i]->graph_gen;
+    if (fresh) return MTS_OK;
+    if (bt->graph) {
+        cudaGraphExecDestroy(bt->graph);
+        bt->graph = nullptr;
+    }
+    cudaStream_t st = bt->ctx->stream;
+    cudaGraph_t g = nullptr;
+    MTS_CUDA(cudaGraphCreate(&g, 0));
+    mts_status s = MTS_OK;
+    for (int i = 0; i < nb && s == MTS_OK; ++i) {
+        mts_body *b = bt->bodies[i];
+        s = prepare_kernels(b);
+        if (s != MTS_OK) break;
+        cudaGraphConditionalHandle h;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) { s = cuda_fail(e, "cudaGraphConditionalHandleCreate"); break; }
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+        if (e != cudaSuccess) { s = cuda_fail(e, "cudaGraphAddNode(conditional)"); break; }
+        e = cudaStreamBeginCaptureToGraph(st, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { s = cuda_fail(e, "cudaStreamBeginCaptureToGraph"); break; }
+        const cudaGraphConditionalHandle own = b->cond;
+        b->cond = h;
+        b->use_cond = 1;
+        long long ndamp = 0;
+        s = launch_stress(b);
+        if (s == MTS_OK) s = launch_force(b);
+        if (s == MTS_OK) s = launch_damping(b, &ndamp);
+        if (s == MTS_OK) s = launch_drift(b);
+        b->use_cond = 0;
+        b->cond = own;
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(st, &captured);
+        if (s == MTS_OK && e != cudaSuccess) s = cuda_fail(e, "cudaStreamEndCapture");
+        b->launches_per_substep = 3 + ndamp;
+    }
+    if (s != MTS_OK) {
+        cudaGraphDestroy(g);
+        return s;
+    }
+    cudaError_t e = cudaGraphInstantiate(&bt->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(batch)");
+    bt->gens.resize(nb);
+    for (int i = 0; i < nb; ++i) bt->gens[i] = bt->bodies[i]->graph_gen;
+    return MTS_OK;
+}
+
 bool valid_field(int f) { return f >= MTS_F_U && f <= MTS_F_ACC; }
 
 }  // namespace
@@ -370,6 +504,7 @@ mts_status mts_body_create(mts_ctx *ctx, const mts_body_desc *desc, mts_body **o
     b->damp_req = desc->damp_layout;
     b->rsize = b->precision == MTS_FP64 ? 8 : 4;
     b->graph_dirty = true;
+    ++b->graph_gen;
     const long long n = b->n;
     const int pad = b->dim == 2 ? 2 : 4;
     const int ms = b->dim == 2 ? 4 : 12;
@@ -511,6 +646,7 @@ mts_status mts_set_material(mts_body *b, mts_material_model model, double rho0, 
     b->delta = delta;
     b->Hlin = H;
     b->graph_dirty = true;
+    ++b->graph_gen;
     return MTS_OK;
 }
 
@@ -521,6 +657,7 @@ mts_status mts_set_damping(mts_body *b, double eta) {
     }
     b->eta = eta;
     b->graph_dirty = true;
+    ++b->graph_gen;
     return MTS_OK;
 }
 
@@ -534,6 +671,7 @@ mts_status mts_set_diffusion(mts_body *b, double D, double beta, double c0) {
     b->beta = beta;
     b->c0 = c0;
     b->graph_dirty = true;
+    ++b->graph_gen;
     k_set_c<<<(unsigned)((b->n + 255) / 256), 256, 0, b->ctx->stream>>>(b->c, b->c_held, b->flags, b->n,
                                                                         c0, (int)b->rsize, 0);
     MTS_CUDA(cudaGetLastError());
@@ -573,6 +711,7 @@ mts_status mts_set_bc_displacement(mts_body *b, int64_t count, const int64_t *id
         if (report_force) b->h_flags[s] |= kForceBit;
     }
     b->graph_dirty = true;
+    ++b->graph_gen;
     return upload_bc(b, uu);
 }
 
@@ -649,42 +788,9 @@ mts_status mts_advance_slow_step(mts_body *b, const mts_step_params *p, mts_step
         return MTS_ERR_INVALID_ARG;
     }
     memset(rep, 0, sizeof(*rep));
-    if (!b->has_material) {
-        set_error("mts_advance_slow_step: no material set");
-        return MTS_ERR_STATE;
-    }
-    if (p->max_substeps < 1 || !std::isfinite(p->ramp_value) || !(p->dt_slow >= 0) ||
-        !std::isfinite(p->dt_slow) || !(p->dt_sub_override >= 0) || !std::isfinite(p->ke_ref) ||
-        !std::isfinite(p->ke_tol) || (p->ke_mode != 0 && p->ke_mode != 1)) {
-        set_error("mts_advance_slow_step: invalid step parameters");
-        return MTS_ERR_INVALID_ARG;
-    }
-    MTS_CUDA(cudaSetDevice(b->ctx->device));
+    long long launches = 0;
+    MTS_TRY(slow_step_begin(b, p, &launches));
     cudaStream_t st = b->ctx->stream;
-    if (p->dt_slow > 0) {
-        if (!b->has_diff) {
-            set_error("mts_advance_slow_step: dt_slow > 0 without diffusion");
-            return MTS_ERR_STATE;
-        }
-        double dtp, dts;
-        MTS_TRY(mts_diffusion_dt(b, &dtp, &dts));
-        if (p->dt_slow > dts * (1.0 + 1e-12) && !p->force_dt) {
-            set_error("diffusion step %g above the stable limit %g (paper's 0.5 h^2/D = %g)",
-                      p->dt_slow, dts, dtp);
-            return MTS_ERR_UNSTABLE_DT;
-        }
-    }
-    const double cs = std::sqrt(b->K / b->rho0);
-    const double dt0 = p->dt_sub_override > 0 ? p->dt_sub_override : 0.6 * b->h / cs;
-    const int use_tol = p->ke_tol >= 0 ? 1 : 0;
-    MTS_TRY(launch_reset_ctrl(b, dt0, p->dt_sub_override, p->ramp_value, p->max_substeps,
-                              p->ke_tol * p->ke_ref, p->ke_mode, use_tol));
-    MTS_TRY(launch_slow_begin(b));
-    long long launches = 2;
-    if (p->dt_slow > 0) {
-        MTS_TRY(launch_diffusion(b, p->dt_slow));
-        launches += 2;
-    }
     long long done_before = 0;
     double prof_ms = 0.0;
     long long prof_n = 0;
@@ -717,27 +823,81 @@ mts_status mts_advance_slow_step(mts_body *b, const mts_step_params *p, mts_step
     }
     rep->prof_ms = prof_ms;
     rep->prof_count = prof_n;
-    const Control &C = *b->h_ctrl;
-    rep->substeps = C.nsub;
-    rep->converged = C.converged;
-    rep->status = C.status;
-    rep->ke_final = C.ke;
-    rep->max_v = C.vmax;
-    rep->max_a = C.amax;
-    rep->dt_last = C.dt_last;
-    for (int k = 0; k < 3; ++k) rep->end_force[k] = k < b->dim ? C.end_force[k] : 0.0;
-    double tip[3] = {0, 0, 0};
-    if (b->tip_count > 0) {
-        MTS_TRY(launch_tip(b, tip));
-        launches += 2;
+    return slow_step_report(b, rep, launches);
+}
+
+mts_status mts_batch_create(mts_ctx *ctx, int32_t count, mts_body *const *bodies, mts_batch **out) {
+    if (!ctx || !bodies || !out || count < 1) {
+        set_error("mts_batch_create: NULL argument or count < 1");
+        return MTS_ERR_INVALID_ARG;
     }
-    rep->kernel_launches = launches;
-    for (int k = 0; k < 3; ++k) rep->tip_deflection[k] = tip[k];
-    if (C.status != MTS_OK) {
-        set_error("non-finite kinetic energy after substep %lld", (long long)C.nsub);
-        return (mts_status)C.status;
+    *out = nullptr;
+    std::vector<mts_body *> v(bodies, bodies + count);
+    for (int i = 0; i < count; ++i) {
+        if (!v[i] || v[i]->ctx != ctx) {
+            set_error("mts_batch_create: body %d is NULL or belongs to another context", i);
+            return MTS_ERR_INVALID_ARG;
+        }
+        for (int j = 0; j < i; ++j)
+            if (v[j] == v[i]) {
+                set_error("mts_batch_create: body %d appears twice (%d)", i, j);
+                return MTS_ERR_INVALID_ARG;
+            }
     }
+    mts_batch *bt = new (std::nothrow) mts_batch();
+    if (!bt) return MTS_ERR_OOM;
+    bt->ctx = ctx;
+    bt->bodies = std::move(v);
+    bt->graph = nullptr;
+    *out = bt;
     return MTS_OK;
+}
+
+void mts_batch_destroy(mts_batch *bt) {
+    if (!bt) return;
+    if (bt->graph) {
+        cudaStreamSynchronize(bt->ctx->stream);
+        cudaGraphExecDestroy(bt->graph);
+    }
+    delete bt;
+}
+
+mts_status mts_batch_advance(mts_batch *bt, const mts_step_params *p, mts_step_report *rep) {
+    if (!bt || !p || !rep) {
+        set_error("mts_batch_advance: NULL argument");
+        return MTS_ERR_INVALID_ARG;
+    }
+    const int nb = (int)bt->bodies.size();
+    for (int i = 0; i < nb; ++i) memset(rep + i, 0, sizeof(*rep));
+    std::vector<long long> launches(nb, 0);
+    for (int i = 0; i < nb; ++i) {
+        const mts_status s = slow_step_begin(bt->bodies[i], p + i, &launches[i]);
+        if (s != MTS_OK) {
+            char msg[512];
+            snprintf(msg, sizeof msg, "batch body %d: %s", i, mts_last_error());
+            set_error("%s", msg);
+            return s;
+        }
+    }
+    MTS_TRY(capture_batch(bt));
+    cudaStream_t st = bt->ctx->stream;
+    MTS_CUDA(cudaGraphLaunch(bt->graph, st));
+    for (mts_body *b : bt->bodies)
+        MTS_CUDA(cudaMemcpyAsync(b->h_ctrl, b->ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+    MTS_CUDA(cudaStreamSynchronize(st));
+    mts_status first = MTS_OK;
+    for (int i = 0; i < nb; ++i) {
+        mts_body *b = bt->bodies[i];
+        const mts_status s =
+            slow_step_report(b, rep + i, launches[i] + b->h_ctrl->nsub * b->launches_per_substep);
+        if (s != MTS_OK && first == MTS_OK) {
+            char msg[512];
+            snprintf(msg, sizeof msg, "batch body %d: %s", i, mts_last_error());
+            set_error("%s", msg);
+            first = s;
+        }
+    }
+    return first;
 }
 
 mts_status mts_set_profiling(mts_body *b, int32_t stage) {
@@ -805,6 +965,265 @@ mts_status mts_write_field(mts_body *b, int32_t field, const double *in, int64_t
     MTS_CUDA(cudaSetDevice(b->ctx->device));
     MTS_CUDA(cudaMemcpyAsync(b->scratch, in, len * 8, cudaMemcpyHostToDevice, b->ctx->stream));
     MTS_TRY(scratch_to_field(b, field));
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    return MTS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- state
+namespace {
+constexpr uint32_t kStateMagic = 0x3153544du;   // "MTS1"
+
+struct StateHeader {
+    uint32_t magic;
+    int32_t dim, precision, narrays;
+    int64_t n;
+};
+
+// the state arrays of a body: device pointer and byte count
+int state_arrays(const mts_body *b, void **ptr, size_t *len) {
+    const size_t n = (size_t)b->n, R = b->rsize, pad = b->dim == 2 ? 2 : 4;
+    int k = 0;
+    ptr[k] = b->u;   len[k++] = n * pad * 8;
+    if (R == 4) { ptr[k] = b->uf; len[k++] = n * pad * R; }
+    ptr[k] = b->v;   len[k++] = n * pad * R;
+    ptr[k] = b->acc; len[k++] = n * pad * R;
+    ptr[k] = b->cp;  len[k++] = n * 8 * R;
+    ptr[k] = b->c;   len[k++] = n * R;
+    return k;
+}
+}  // namespace
+
+extern "C" {
+
+mts_status mts_save_state(const mts_body *b, void *buf, size_t *bytes) {
+    if (!b || !bytes) {
+        set_error("mts_save_state: NULL argument");
+        return MTS_ERR_INVALID_ARG;
+    }
+    void *ptr[8];
+    size_t len[8];
+    const int na = state_arrays(b, ptr, len);
+    size_t need = sizeof(StateHeader);
+    for (int k = 0; k < na; ++k) need += len[k];
+    if (!buf) {
+        *bytes = need;
+        return MTS_OK;
+    }
+    if (*bytes < need) {
+        set_error("mts_save_state: buffer of %zu bytes, %zu needed", *bytes, need);
+        return MTS_ERR_INVALID_ARG;
+    }
+    MTS_CUDA(cudaSetDevice(b->ctx->device));
+    StateHeader h{kStateMagic, b->dim, b->precision, na, b->n};
+    char *o = static_cast<char *>(buf);
+    std::memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    for (int k = 0; k < na; ++k) {
+        MTS_CUDA(cudaMemcpyAsync(o, ptr[k], len[k], cudaMemcpyDeviceToHost, b->ctx->stream));
+        o += len[k];
+    }
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    *bytes = need;
+    return MTS_OK;
+}
+
+mts_status mts_load_state(mts_body *b, const void *buf, size_t bytes) {
+    if (!b || !buf) {
+        set_error("mts_load_state: NULL argument");
+        return MTS_ERR_INVALID_ARG;
+    }
+    void *ptr[8];
+    size_t len[8];
+    const int na = state_arrays(b, ptr, len);
+    size_t need = sizeof(StateHeader);
+    for (int k = 0; k < na; ++k) need += len[k];
+    StateHeader h{};
+    if (bytes >= sizeof(h)) std::memcpy(&h, buf, sizeof(h));
+    if (bytes != need || h.magic != kStateMagic || h.dim != b->dim || h.precision != b->precision ||
+        h.n != b->n || h.narrays != na) {
+        set_error("mts_load_state: buffer does not hold the state of a body like this one "
+                  "(%zu bytes, %zu expected)", bytes, need);
+        return MTS_ERR_INVALID_ARG;
+    }
+    MTS_CUDA(cudaSetDevice(b->ctx->device));
+    const char *in = static_cast<const char *>(buf) + sizeof(h);
+    for (int k = 0; k < na; ++k) {
+        MTS_CUDA(cudaMemcpyAsync(ptr[k], in, len[k], cudaMemcpyHostToDevice, b->ctx->stream));
+        in += len[k];
+    }
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    return MTS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- reverse mode
+namespace {
+void free_adjoint(mts_body *b) {
+    void **ptrs[] = {(void **)&b->tape_u, (void **)&b->tape_cp, (void **)&b->tape_dt,
+                     (void **)&b->tape_c, (void **)&b->adj_u, (void **)&b->adj_v,
+                     (void **)&b->adj_cp, (void **)&b->adj_c, (void **)&b->adj_a,
+                     (void **)&b->adj_G, (void **)&b->adj_theta, (void **)&b->adj_part,
+                     (void **)&b->adj_ctrl};
+    for (void **pp : ptrs) {
+        dfree(b->ctx, *pp);
+        *pp = nullptr;
+    }
+    b->adj_cap = 0;
+}
+
+mts_status zero_adjoint(mts_body *b) {
+    cudaStream_t st = b->ctx->stream;
+    const size_t n = (size_t)b->n, pad = b->dim == 2 ? 2 : 4;
+    MTS_CUDA(cudaMemsetAsync(b->adj_u, 0, n * pad * 8, st));
+    MTS_CUDA(cudaMemsetAsync(b->adj_v, 0, n * pad * 8, st));
+    MTS_CUDA(cudaMemsetAsync(b->adj_cp, 0, n * 8 * 8, st));
+    MTS_CUDA(cudaMemsetAsync(b->adj_c, 0, n * 8, st));
+    MTS_CUDA(cudaMemsetAsync(b->adj_theta, 0, 8 * 8, st));
+    MTS_CUDA(cudaMemsetAsync(b->adj_ctrl, 0, sizeof(Control), st));
+    for (int k = 0; k < 3; ++k) b->adj_force_seed[k] = 0.0;
+    return MTS_OK;
+}
+
+mts_status adjoint_ready(mts_body *b, const char *who) {
+    if (!b) {
+        set_error("%s: NULL body", who);
+        return MTS_ERR_INVALID_ARG;
+    }
+    if (b->adj_cap <= 0) {
+        set_error("%s: reverse mode not enabled (mts_adjoint_enable)", who);
+        return MTS_ERR_STATE;
+    }
+    MTS_CUDA(cudaSetDevice(b->ctx->device));
+    return MTS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+mts_status mts_adjoint_enable(mts_body *b, int64_t max_substeps) {
+    if (!b || max_substeps < 1) {
+        set_error("mts_adjoint_enable: NULL body or max_substeps < 1");
+        return MTS_ERR_INVALID_ARG;
+    }
+    if (b->precision != MTS_FP64) {
+        set_error("mts_adjoint_enable: the reverse mode runs on FP64 bodies only");
+        return MTS_ERR_STATE;
+    }
+    MTS_CUDA(cudaSetDevice(b->ctx->device));
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    free_adjoint(b);
+    const size_t n = (size_t)b->n, pad = b->dim == 2 ? 2 : 4, ms = b->dim == 2 ? 4 : 12;
+    const size_t K = (size_t)max_substeps;
+    mts_status s = MTS_OK;
+    auto A = [&](void **p, size_t bytes) {
+        if (s == MTS_OK) s = dalloc_into(b->ctx, p, bytes + 16);
+    };
+    A((void **)&b->tape_u, K * n * pad * 8);
+    A((void **)&b->tape_cp, K * n * 8 * 8);
+    A((void **)&b->tape_dt, K * 8);
+    A((void **)&b->tape_c, n * 8);
+    A((void **)&b->adj_u, n * pad * 8);
+    A((void **)&b->adj_v, n * pad * 8);
+    A((void **)&b->adj_cp, n * 8 * 8);
+    A((void **)&b->adj_c, n * 8);
+    A((void **)&b->adj_a, n * pad * 8);
+    A((void **)&b->adj_G, n * ms * 8);
+    A((void **)&b->adj_theta, 8 * 8);
+    A((void **)&b->adj_part, (size_t)b->ntiles * 8 * 8);
+    A((void **)&b->adj_ctrl, sizeof(Control));
+    if (s != MTS_OK) {
+        free_adjoint(b);
+        return s;
+    }
+    b->adj_cap = max_substeps;
+    MTS_TRY(zero_adjoint(b));
+    MTS_TRY(adjoint_prepare(b));
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    return MTS_OK;
+}
+
+mts_status mts_adjoint_reset(mts_body *b) {
+    MTS_TRY(adjoint_ready(b, "mts_adjoint_reset"));
+    MTS_TRY(zero_adjoint(b));
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    return MTS_OK;
+}
+
+mts_status mts_adjoint_seed(mts_body *b, const double *u_bar, const double *tip_bar,
+                            const double *force_bar) {
+    MTS_TRY(adjoint_ready(b, "mts_adjoint_seed"));
+    if (u_bar)
+        MTS_CUDA(cudaMemcpyAsync(b->scratch, u_bar, (size_t)b->n * b->dim * 8,
+                                 cudaMemcpyHostToDevice, b->ctx->stream));
+    MTS_TRY(adjoint_seed(b, u_bar ? b->scratch : nullptr, tip_bar));
+    if (force_bar)
+        for (int k = 0; k < b->dim; ++k) b->adj_force_seed[k] += force_bar[k];
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    return MTS_OK;
+}
+
+mts_status mts_adjoint_slow_step(mts_body *b, const mts_step_params *p, int64_t substeps,
+                                 double *theta_bar) {
+    MTS_TRY(adjoint_ready(b, "mts_adjoint_slow_step"));
+    if (!p || !theta_bar || substeps < 1 || substeps > b->adj_cap) {
+        set_error("mts_adjoint_slow_step: NULL argument or substeps %lld outside [1, %lld]",
+                  (long long)substeps, (long long)b->adj_cap);
+        return MTS_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = b->ctx->stream;
+    // recompute the slow step from its start, taping every substep's input
+    mts_step_params q = *p;
+    q.max_substeps = substeps;
+    q.ke_tol = -1.0;
+    long long launches = 0;
+    MTS_TRY(slow_step_begin(b, &q, &launches, b->tape_c));
+    MTS_TRY(prepare_kernels(b));
+    b->use_cond = 0;
+    for (long long k = 0; k < substeps; ++k) {
+        MTS_TRY(adjoint_tape(b, k));
+        MTS_TRY(launch_stress(b));
+        MTS_TRY(launch_force(b));
+        MTS_TRY(launch_damping(b));
+        MTS_TRY(launch_drift(b));
+    }
+    MTS_CUDA(cudaMemcpyAsync(b->h_ctrl, b->ctrl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+    MTS_CUDA(cudaStreamSynchronize(st));
+    if (b->h_ctrl->nsub != substeps || b->h_ctrl->status != MTS_OK) {
+        set_error("mts_adjoint_slow_step: the recomputed step ran %lld substeps (status %d), "
+                  "expected %lld", (long long)b->h_ctrl->nsub, b->h_ctrl->status,
+                  (long long)substeps);
+        return MTS_ERR_STATE;
+    }
+    // reverse
+    for (long long k = substeps - 1; k >= 0; --k) MTS_TRY(adjoint_substep(b, k, k == substeps - 1));
+    if (q.dt_slow > 0) MTS_TRY(adjoint_diffusion(b, q.dt_slow));
+    MTS_TRY(adjoint_load(b));
+    double th[8];
+    MTS_CUDA(cudaMemcpyAsync(th, b->adj_theta, sizeof(th), cudaMemcpyDeviceToHost, st));
+    MTS_CUDA(cudaMemsetAsync(b->adj_theta, 0, sizeof(th), st));
+    MTS_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < 7; ++k) theta_bar[k] += th[k];
+    for (int k = 0; k < 3; ++k) b->adj_force_seed[k] = 0.0;
+    return MTS_OK;
+}
+
+mts_status mts_read_adjoint(mts_body *b, int32_t field, double *out, int64_t len) {
+    MTS_TRY(adjoint_ready(b, "mts_read_adjoint"));
+    if (!out || !(field == MTS_F_U || field == MTS_F_V || field == MTS_F_C ||
+                  field == MTS_F_ALPHA || field == MTS_F_CPINV)) {
+        set_error("mts_read_adjoint: invalid arguments (fields U, V, C, ALPHA, CPINV)");
+        return MTS_ERR_INVALID_ARG;
+    }
+    const int w = field_width(b, field);
+    if (len != b->n * w) {
+        set_error("mts_read_adjoint: len %lld, expected %lld", (long long)len, (long long)(b->n * w));
+        return MTS_ERR_INVALID_ARG;
+    }
+    MTS_TRY(adjoint_out(b, field, b->scratch));
+    MTS_CUDA(cudaMemcpyAsync(out, b->scratch, len * 8, cudaMemcpyDeviceToHost, b->ctx->stream));
     MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
     return MTS_OK;
 }

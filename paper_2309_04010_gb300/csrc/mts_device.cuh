@@ -5,6 +5,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "mts_dual.cuh"
+
 namespace mts {
 
 template <int D> struct Pad { static constexpr int v = (D == 2) ? 2 : 4; };
@@ -256,7 +258,7 @@ __device__ __forceinline__ void stress_j2(const R (&F)[3][3], R (&cp)[7], R K, R
     if (f > R(0)) {
         R mubar = mu * trb / R(3);
         R dg = R(0);
-        const R tol = (sizeof(R) == 8) ? R(1e-13) : R(1e-6);
+        const R tol = R(NewtonTol<R>::value);
         for (int it = 0; it < 30; ++it) {
             R g = sn - r23 * hard_k(al + r23 * dg, s0, sinf, delta, H) - R(2) * mubar * dg;
             if (dabs(g) <= tol * r23 * kal) break;

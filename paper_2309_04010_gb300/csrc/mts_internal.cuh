@@ -110,6 +110,7 @@ struct Args {
     const int32_t *touch_cnt;
     const int32_t *bperm;        // block-sorted position -> particle
     const uint8_t *bflags;       // flags in block-sorted order (wide layout)
+    int transpose;               // damping: apply the transposed pair updates (adjoint)
     int mb;                      // max particles per damping block (local stride)
     int nbw;                     // touched blocks per owner group (2^blocked axes)
     int max_group_pairs;         // largest pair list of one owner group
@@ -233,6 +234,24 @@ struct mts_body {
     int use_cond;
     std::vector<cudaEvent_t> prof_ev;   // 2 per substep of a chunk
     long long launches_per_substep;
+    long long graph_gen;          // bumped whenever captured kernel arguments go stale
+
+    // reverse mode (FP64 bodies; mts_adjoint_enable)
+    long long adj_cap;            // substeps the tape holds (0 = off)
+    double *tape_u, *tape_cp, *tape_dt, *tape_c;   // per substep u (n x PAD), C_p^-1 and
+                                                   // alpha (n x 8), dt; c before diffusion
+    double *adj_u, *adj_v, *adj_cp, *adj_c;        // adjoint state (sorted order)
+    double *adj_a, *adj_G;        // scratch: acceleration adjoint, per-particle d x d
+    double *adj_theta, *adj_part; // 8 parameter accumulators, per-tile partials
+    mts::Control *adj_ctrl;       // dt of the substep being reversed
+    double adj_force_seed[3];     // pending end-force adjoint of the next reversed step
+};
+
+struct mts_batch {
+    mts_ctx *ctx;
+    std::vector<mts_body *> bodies;
+    std::vector<long long> gens;  // graph_gen of each body at capture
+    cudaGraphExec_t graph;
 };
 
 namespace mts {
@@ -252,6 +271,18 @@ mts_status build_body(mts_body *b, const double *hX);
 mts_status launch_stress(mts_body *b);
 mts_status launch_force(mts_body *b);
 mts_status launch_damping(mts_body *b, long long *launches = nullptr);
+// the damping sweep transposed, on an FP64 adjoint velocity array, dt from ctrl
+mts_status launch_damping_adjoint(mts_body *b, double *vbar, Control *ctrl);
+// kernel arguments of a body (mts_substep.cu)
+template <class R> Args<R> make_args(mts_body *b);
+// reverse mode (mts_adjoint.cu), FP64 bodies
+mts_status adjoint_prepare(mts_body *b);
+mts_status adjoint_tape(mts_body *b, long long k);
+mts_status adjoint_substep(mts_body *b, long long k, bool last);
+mts_status adjoint_diffusion(mts_body *b, double dt);
+mts_status adjoint_load(mts_body *b);
+mts_status adjoint_seed(mts_body *b, const double *ubar_orig_dev, const double tip[3]);
+mts_status adjoint_out(mts_body *b, int field, double *out_dev);
 mts_status launch_drift(mts_body *b);
 mts_status prepare_kernels(mts_body *b);
 // shared memory of the CTA-per-group damping kernel for this body's layout

@@ -1142,16 +1142,15 @@ mts_status build_typed(mts_body *b, const double *hX) {
     k_b0<R, D><<<grid_for(n), TPB, 0, st>>>(b->X64, b->nb_off, b->nb_idx, n, b->h, alpha, b->V,
                                              (R *)b->B0, b->ctrl);
 
-    // -- damping order.  AUTO takes the wide layout (shortest axis unblocked,
-    // ties to the higher axis) when that axis spans at most 64 cells in 3D or
-    // 256 in 2D and an owner group fits one CTA, else blocks on every axis.
+    // -- damping order.  AUTO and BLOCKS take blocks on every axis (the faster
+    // warp-per-group kernel on the workloads measured); WIDE unblocks the
+    // shortest axis (ties to the higher axis) when an owner group fits one CTA.
     {
         const long long cells[3] = {g0, g1, g2};
         int kmin = 0;
         for (int k = 1; k < D; ++k)
             if (cells[k] <= cells[kmin]) kmin = k;
-        const bool try_wide = b->damp_req == MTS_DAMP_WIDE ||
-                              (b->damp_req == MTS_DAMP_AUTO && cells[kmin] <= (D == 3 ? 64 : 256));
+        const bool try_wide = b->damp_req == MTS_DAMP_WIDE;
         bool built = false;
         if (try_wide) {
             set_layout(b, MTS_DAMP_WIDE, kmin);

@@ -21,72 +21,13 @@
 
 #include "mts_device.cuh"
 #include "mts_internal.cuh"
+#include "mts_tiles.cuh"
 
 namespace mts {
 
 namespace {
 
 inline unsigned grid_of(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
-
-// byte offset of the second staged array: rounded up to 16 bytes so that
-// 16-byte vector loads from it stay aligned for any halo size
-template <class R, int P>
-__host__ __device__ __forceinline__ size_t second_off(int max_halo) {
-    return ((size_t)max_halo * P * sizeof(R) + 15) & ~size_t(15);
-}
-
-// --------------------------------------------------------------------- tiles
-// A CTA owns one Morton tile of T = blockDim.x consecutive particles.  It
-// stages the reference positions and one more per-particle array of the tile's
-// halo (the tile and all its neighbours) in shared memory, then every
-// neighbour access reads shared memory through a 16-bit local slot.
-template <class R, int P, int NY>
-__device__ __forceinline__ int stage_halo(const Args<R> &A, R *sX, R *sY, const R *Y) {
-    const long long t = blockIdx.x;
-    const long long h0 = A.halo_off[t];
-    const int nh = (int)(A.halo_off[t + 1] - h0);
-    // indices first (independent loads), then asynchronous row copies
-    constexpr int U = 4;
-    for (int k0 = threadIdx.x; k0 < nh; k0 += U * blockDim.x) {
-        int g[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = k0 + u * blockDim.x;
-            g[u] = k < nh ? __ldg(A.halo_idx + h0 + k) : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = k0 + u * blockDim.x;
-            if (g[u] < 0) continue;
-            if (sX) cp_async_reals<R, P>(sX + (size_t)k * P, A.X + (size_t)g[u] * P);
-            if (sY) cp_async_reals<R, NY>(sY + (size_t)k * NY, Y + (size_t)g[u] * NY);
-        }
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    return nh;
-}
-
-// Visit the neighbour slots of one particle, reading the index stream 8
-// entries ahead into registers so that each warp keeps several index lines in
-// flight (the loop is unrolled by 8 so every register index is static).
-template <class Body>
-__device__ __forceinline__ void for_each_neighbour(const uint16_t *row, int T, int w, Body body) {
-    constexpr int K = 8;
-    int cur[K], nxt[K];
-#pragma unroll
-    for (int u = 0; u < K; ++u) cur[u] = u < w ? (int)__ldg(row + u * T) : 0;
-    for (int j0 = 0; j0 < w; j0 += K) {
-#pragma unroll
-        for (int u = 0; u < K; ++u)
-            nxt[u] = (j0 + K + u < w) ? (int)__ldg(row + (j0 + K + u) * T) : 0;
-#pragma unroll
-        for (int u = 0; u < K; ++u)
-            if (j0 + u < w) body(cur[u]);
-#pragma unroll
-        for (int u = 0; u < K; ++u) cur[u] = nxt[u];
-    }
-}
 
 // F_a = I + (sum_b V (u_b - u_a) (x) grad_a W_ab) B0_a, 3x3 with F_zz = 1 in 2D;
 // X and u of the halo are in shared memory.
@@ -352,7 +293,7 @@ template <> __device__ __forceinline__ float fast_div<float>(float a, float b) {
 
 template <class R, int D>
 __device__ __forceinline__ void damp_apply(R *pa, R *pb, R g, const uint8_t *sf, uint32_t ia,
-                                           uint32_t ib, R hcim) {
+                                           uint32_t ib, R hcim, bool transpose = false) {
     constexpr int P = Pad<D>::v;
     R va[P], vb[P];
     ld_vec<R, P>(va, pa);
@@ -378,9 +319,15 @@ __device__ __forceinline__ void damp_apply(R *pa, R *pb, R g, const uint8_t *sf,
             const bool a_free = !((fa >> q) & 1), b_free = !((fb >> q) & 1);
             const R ca = a_free ? (b_free ? f2 : f1) : R(0);
             const R cb = b_free ? (a_free ? f2 : f1) : R(0);
-            const R d = va[q] - vb[q];
-            va[q] -= ca * d;
-            vb[q] += cb * d;
+            if (transpose) {    // the transposed 2x2 update (adjoint sweep)
+                const R t = ca * va[q] - cb * vb[q];
+                va[q] -= t;
+                vb[q] += t;
+            } else {
+                const R d = va[q] - vb[q];
+                va[q] -= ca * d;
+                vb[q] += cb * d;
+            }
         }
     }
     st_vec<R, P>(pa, va);
@@ -389,11 +336,11 @@ __device__ __forceinline__ void damp_apply(R *pa, R *pb, R g, const uint8_t *sf,
 
 template <class R, int D>
 __device__ __forceinline__ void damp_pair(uint32_t w, R g, unsigned char *svb, const uint8_t *sf,
-                                          R hcim, R /*im*/) {
+                                          R hcim, bool transpose) {
     constexpr int BPS = Pad<D>::v * (int)sizeof(R);
     const uint32_t oa = w & 0xffffu, ob = w >> 16;
     damp_apply<R, D>(reinterpret_cast<R *>(svb + oa), reinterpret_cast<R *>(svb + ob), g, sf,
-                     oa / BPS, ob / BPS, hcim);
+                     oa / BPS, ob / BPS, hcim, transpose);
 }
 
 template <class R, int D>
@@ -445,6 +392,7 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     __syncwarp();
     const R im = (R)(1.0 / A.mass);
     const R hcim = (R)(0.5 * A.ctrl->dt) * A.eta * im;   // (dt/2) eta / m
+    const bool tr = A.transpose != 0;
     unsigned char *svb = reinterpret_cast<unsigned char *>(sv);
     if (nl > 0 && (mode & 1)) {
         uint32_t wn = sab[lane];
@@ -456,7 +404,7 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
                 wn = sab[32 * (l + 1) + lane];
                 gn = sg[32 * (l + 1) + lane];
             }
-            damp_pair<R, D>(w, gc, svb, sf, hcim, im);
+            damp_pair<R, D>(w, gc, svb, sf, hcim, tr);
             __syncwarp();
         }
     }
@@ -470,7 +418,7 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
                 wn = sab[32 * (l - 1) + lane];
                 gn = sg[32 * (l - 1) + lane];
             }
-            damp_pair<R, D>(w, gc, svb, sf, hcim, im);
+            damp_pair<R, D>(w, gc, svb, sf, hcim, tr);
             __syncwarp();
         }
     }
@@ -502,7 +450,8 @@ __host__ __device__ inline void wide_offsets(int slots, int maxl, int lc, int P,
 template <class R, int D>
 __device__ __forceinline__ void wide_sweep(bool fwd, int nl, const int32_t *slv, long long p0,
                                            const uint32_t *gw, const R *gg, uint32_t *sw, R *sgr,
-                                           int lc, R *sv, const uint8_t *sf, R hcim) {
+                                           int lc, R *sv, const uint8_t *sf, R hcim,
+                                           bool transpose) {
     constexpr int P = Pad<D>::v;
     const int tid = threadIdx.x;
     auto issue = [&](int i) {
@@ -530,7 +479,8 @@ __device__ __forceinline__ void wide_sweep(bool fwd, int nl, const int32_t *slv,
             const uint32_t w = sw[buf + k];
             const R gc = sgr[buf + k];
             const uint32_t ia = w & 0xffffu, ib = w >> 16;
-            damp_apply<R, D>(sv + (size_t)ia * P, sv + (size_t)ib * P, gc, sf, ia, ib, hcim);
+            damp_apply<R, D>(sv + (size_t)ia * P, sv + (size_t)ib * P, gc, sf, ia, ib, hcim,
+                             transpose);
         }
     }
     cp_async_wait_all();
@@ -602,8 +552,9 @@ __global__ void __launch_bounds__(kWideThreads) k_damp_wide(Args<R> A, long long
     cp_async_wait_all();
     __syncthreads();
     const R hcim = (R)(0.5 * A.ctrl->dt) * A.eta * (R)(1.0 / A.mass);   // (dt/2) eta / m
-    if (mode & 1) wide_sweep<R, D>(true, nl, slv, p0, A.pair_ab, A.pair_g, sw, sgr, lc, sv, sf, hcim);
-    if (mode & 2) wide_sweep<R, D>(false, nl, slv, p0, A.pair_ab, A.pair_g, sw, sgr, lc, sv, sf, hcim);
+    const bool tr = A.transpose != 0;
+    if (mode & 1) wide_sweep<R, D>(true, nl, slv, p0, A.pair_ab, A.pair_g, sw, sgr, lc, sv, sf, hcim, tr);
+    if (mode & 2) wide_sweep<R, D>(false, nl, slv, p0, A.pair_ab, A.pair_g, sw, sgr, lc, sv, sf, hcim, tr);
     for (int j0 = 0; j0 < total; j0 += kSB * kWideThreads) {
         int pp[kSB], sl[kSB];
 #pragma unroll
@@ -1012,6 +963,8 @@ __global__ void k_tip_final(const double *part, int nblk, double *out) {
 }
 
 // --------------------------------------------------------------------- args
+}  // namespace
+
 template <class R>
 Args<R> make_args(mts_body *b) {
     Args<R> A{};
@@ -1074,6 +1027,11 @@ Args<R> make_args(mts_body *b) {
     return A;
 }
 
+template Args<float> make_args<float>(mts_body *b);
+template Args<double> make_args<double>(mts_body *b);
+
+namespace {
+
 template <class R, int D> size_t smem_stress(const mts_body *b) {
     return second_off<R, Pad<D>::v>(b->max_halo) + (size_t)b->max_halo * Pad<D>::v * sizeof(R);
 }
@@ -1114,10 +1072,9 @@ mts_status force_t(mts_body *b) {
 }
 
 template <class R, int D>
-mts_status damping_t(mts_body *b, long long *nlaunch) {
+mts_status damping_run(mts_body *b, const Args<R> &A, long long *nlaunch) {
     if (nlaunch) *nlaunch = 0;
     if (b->eta == 0.0 || b->npairs == 0) return MTS_OK;
-    Args<R> A = make_args<R>(b);
     const bool wide = b->damp_layout == MTS_DAMP_WIDE;
     const size_t smem = wide ? damp_wide_smem(b) : smem_damp<R, D>(b);
     const int W = damp_warps<R, D>(b);
@@ -1145,33 +1102,59 @@ mts_status damping_t(mts_body *b, long long *nlaunch) {
     return MTS_OK;
 }
 
-// raise the dynamic shared-memory limit of the damping kernel (outside any
-// stream capture)
+template <class R, int D>
+mts_status damping_t(mts_body *b, long long *nlaunch) {
+    return damping_run<R, D>(b, make_args<R>(b), nlaunch);
+}
+
+// transposed sweep on an FP64 adjoint velocity array: the same pair order
+// (forward then reverse) with every 2x2 pair update transposed
+template <class R, int D>
+mts_status damping_adjoint_t(mts_body *b, double *vbar, Control *ctrl) {
+    if constexpr (sizeof(R) != 8) {
+        set_error("the adjoint runs on FP64 bodies only");
+        return MTS_ERR_STATE;
+    } else {
+        Args<R> A = make_args<R>(b);
+        A.v = vbar;
+        A.ctrl = ctrl;
+        A.transpose = 1;
+        return damping_run<R, D>(b, A, nullptr);
+    }
+}
+
+// Raise the dynamic shared-memory cap of the staging kernels (outside any
+// stream capture).  The cap is a per-kernel attribute shared by every body in
+// the process, so it is set to what the device allows next to the kernel's
+// static shared memory, not to this body's need: a later, smaller body must
+// not lower it under an earlier body's captured graphs.
 template <class R, int D>
 mts_status prepare_t(mts_body *b) {
-    const size_t lim = 227 * 1024;
+    int optin = 0;
+    MTS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->ctx->device));
     const bool wide = b->damp_layout == MTS_DAMP_WIDE;
-    const size_t sd = wide ? damp_wide_smem(b) : smem_damp<R, D>(b), sa = smem_stress<R, D>(b),
-                 sf = smem_force<R, D>(b),
-                 sc = smem_diffuse<R, D>(b);
-    if (sd > lim || sa > lim || sf > lim || sc > lim) {
-        set_error("shared-memory staging too large (damping %zu, stress %zu, force %zu bytes; "
-                  "halo %d particles, damping block %d particles)", sd, sa, sf, b->max_halo, b->mb);
-        return MTS_ERR_INVALID_ARG;
-    }
-    auto attr = [](const void *fn, size_t bytes) {
-        return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)std::max<size_t>(bytes, 48 * 1024));
+    auto attr = [&](const void *fn, size_t need, const char *what) -> mts_status {
+        cudaFuncAttributes fa{};
+        MTS_CUDA(cudaFuncGetAttributes(&fa, fn));
+        const size_t cap = (size_t)optin - fa.sharedSizeBytes;
+        if (need > cap) {
+            set_error("%s needs %zu bytes of shared memory, at most %zu fit (halo %d particles, "
+                      "damping block %d particles)", what, need, cap, b->max_halo, b->mb);
+            return MTS_ERR_INVALID_ARG;
+        }
+        MTS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+        return MTS_OK;
     };
     if (wide)
-        MTS_CUDA(attr((const void *)k_damp_wide<R, D>, sd));
+        MTS_TRY(attr((const void *)k_damp_wide<R, D>, damp_wide_smem(b), "damping (wide)"));
     else
-        MTS_CUDA(attr((const void *)k_damp<R, D>, sd));
-    MTS_CUDA(attr((const void *)k_stress<R, D, MTS_ELASTIC_SVK>, sa));
-    MTS_CUDA(attr((const void *)k_stress<R, D, MTS_NEOHOOKE_J2>, sa));
-    MTS_CUDA(attr((const void *)k_defgrad<R, D>, sa));
-    MTS_CUDA(attr((const void *)k_force<R, D>, sf));
-    MTS_CUDA(attr((const void *)k_diffuse<R, D>, sc));
+        MTS_TRY(attr((const void *)k_damp<R, D>, smem_damp<R, D>(b), "damping"));
+    const size_t sa = smem_stress<R, D>(b);
+    MTS_TRY(attr((const void *)k_stress<R, D, MTS_ELASTIC_SVK>, sa, "stress"));
+    MTS_TRY(attr((const void *)k_stress<R, D, MTS_NEOHOOKE_J2>, sa, "stress"));
+    MTS_TRY(attr((const void *)k_defgrad<R, D>, sa, "deformation gradient"));
+    MTS_TRY(attr((const void *)k_force<R, D>, smem_force<R, D>(b), "force"));
+    MTS_TRY(attr((const void *)k_diffuse<R, D>, smem_diffuse<R, D>(b), "diffusion"));
     return MTS_OK;
 }
 
@@ -1243,6 +1226,9 @@ mts_status field_in_t(mts_body *b, int field) {
 mts_status launch_stress(mts_body *b) { return DISPATCH(stress_t, b); }
 mts_status launch_force(mts_body *b) { return DISPATCH(force_t, b); }
 mts_status launch_damping(mts_body *b, long long *launches) { return DISPATCH(damping_t, b, launches); }
+mts_status launch_damping_adjoint(mts_body *b, double *vbar, Control *ctrl) {
+    return DISPATCH(damping_adjoint_t, b, vbar, ctrl);
+}
 mts_status launch_drift(mts_body *b) { return DISPATCH(drift_t, b); }
 mts_status prepare_kernels(mts_body *b) { return DISPATCH(prepare_t, b); }
 

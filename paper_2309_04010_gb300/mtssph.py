@@ -106,6 +106,11 @@ def lib():
         "mts_body_destroy": [vp],
         "mts_body_permutation": [vp, vp],
         "mts_body_damping_layout": [vp, vp, C.POINTER(i32)],
+        "mts_save_state": [vp, vp, C.POINTER(C.c_size_t)],
+        "mts_batch_create": [vp, i32, vp, C.POINTER(vp)],
+        "mts_batch_advance": [vp, vp, vp],
+        "mts_batch_destroy": [vp],
+        "mts_load_state": [vp, vp, C.c_size_t],
         "mts_body_neighbors": [vp, C.POINTER(i64), vp, vp],
         "mts_body_colouring": [vp, C.POINTER(i64), vp, vp, vp, vp, vp],
         "mts_set_material": [vp, C.c_int, d, d, d, d, d, d, d],
@@ -128,6 +133,7 @@ def lib():
         fn.restype = C.c_int
     L.mts_ctx_destroy.restype = None
     L.mts_body_destroy.restype = None
+    L.mts_batch_destroy.restype = None
     L.mts_last_error.restype = C.c_char_p
     _lib = L
     return L
@@ -213,10 +219,13 @@ class Body:
         h = C.c_void_p()
         _check(lib().mts_body_create(ctx.handle, C.byref(desc), C.byref(h)), "mts_body_create")
         self._h = h
+        self._batches: "weakref.WeakSet" = weakref.WeakSet()
         ctx._bodies.add(self)
 
     def close(self):
         if getattr(self, "_h", None):
+            for bt in list(self._batches):     # a batch borrows its bodies
+                bt.close()
             lib().mts_body_destroy(self._h)
             self._h = None
 
@@ -329,6 +338,61 @@ class Body:
         w = self._width(field)
         a = np.ascontiguousarray(values, dtype=np.float64).reshape(self.n * w)
         _check(lib().mts_write_field(self._h, field, _ptr(a), a.size), "mts_write_field")
+
+    def save_state(self) -> bytes:
+        """Snapshot of the evolving state (bit-exact resume with load_state)."""
+        nb = C.c_size_t()
+        _check(lib().mts_save_state(self._h, None, C.byref(nb)), "mts_save_state")
+        buf = C.create_string_buffer(nb.value)
+        _check(lib().mts_save_state(self._h, buf, C.byref(nb)), "mts_save_state")
+        return buf.raw[:nb.value]
+
+    def load_state(self, state: bytes):
+        buf = C.create_string_buffer(bytes(state), len(state))
+        _check(lib().mts_load_state(self._h, buf, len(state)), "mts_load_state")
+
+
+class Batch:
+    """mts_batch: bodies of one context advanced by one graph launch per slow step."""
+
+    def __init__(self, ctx: Context, bodies):
+        self.ctx = ctx
+        self.bodies = list(bodies)
+        arr = (C.c_void_p * len(self.bodies))(*[b._h.value if b._h else None for b in self.bodies])
+        h = C.c_void_p()
+        _check(lib().mts_batch_create(ctx.handle, len(self.bodies), arr, C.byref(h)),
+               "mts_batch_create")
+        self._h = h
+        for b in self.bodies:
+            b._batches.add(self)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mts_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def advance(self, params) -> list:
+        """One slow step of every body; params: one dict of advance_slow_step
+        keyword arguments per body (check_every is ignored)."""
+        if len(params) != len(self.bodies):
+            raise ValueError("one parameter set per body")
+        P = (StepParams * len(params))()
+        for i, kw in enumerate(params):
+            P[i] = StepParams(kw.get("dt_slow", 0.0), kw.get("ramp", 0.0), kw.get("dt_sub", 0.0),
+                              kw.get("ke_tol", -1.0), kw.get("ke_ref", 1.0),
+                              kw.get("max_substeps", 1), kw.get("ke_mode", 0), 0,
+                              int(kw.get("force_dt", False)), 0)
+        R = (StepReport * len(params))()
+        _check(lib().mts_batch_advance(self._h, P, R), "mts_batch_advance")
+        return list(R)
 
 
 def body_from_case(ctx: Context, case, precision: int = FP64, damp_layout: int = DAMP_AUTO) -> Body:

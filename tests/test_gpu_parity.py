@@ -265,14 +265,14 @@ def test_mixed_precision_j2_cylinder(ctx, layout):
 
 # ---------------------------------------------------------------- full size
 @pytest.mark.parametrize("precision,tol,layout", [(M.FP64, 1e-12, "auto"), (M.MIXED, 1e-4, "auto"),
-                                                 (M.FP64, 1e-12, "blocks")])
+                                                 (M.FP64, 1e-12, "wide")])
 def test_full_size_cylinder_first_substeps(ctx, precision, tol, layout):
     """The benchmark workload (3D J2 cylinder, 252,800 particles) at full size:
     setup products bit-exact, then two substeps after the first load jump."""
     case = B.cylinder3d()
     ob, gb = pair(ctx, case, precision, LAYOUTS[layout])
-    if layout == "auto":      # 200 x 40 x 40 cells: the last short axis is unblocked
-        assert gb.damping_layout() == ((2, 2, M.WHOLE_AXIS), 0)
+    if layout == "auto":      # blocks of 4 cells (4 dx > 2h) on every axis, 32 pairs per level
+        assert gb.damping_layout() == ((2, 2, 2), 32)
     off_g, idx_g = gb.neighbors()
     off_o, idx_o = ob.neighbors()
     assert np.array_equal(off_g, off_o) and np.array_equal(idx_g, idx_o)
@@ -308,3 +308,26 @@ def test_api_errors(ctx):
     gb.set_bc_displacement(np.zeros(0, np.int64), 1)      # empty set is fine
     r = gb.advance_slow_step(max_substeps=1)
     assert r.substeps == 1 and r.converged == 0
+
+
+# ---------------------------------------------------------------- checkpoint / resume
+@pytest.mark.parametrize("precision", [M.FP64, M.MIXED])
+def test_save_load_state_resumes_bit_exact(ctx, precision):
+    case = small_cylinder()
+    gb = M.body_from_case(ctx, case, precision)
+    kw = dict(ke_tol=case.plan.ke_tol, ke_ref=case.plan.ke_ref, max_substeps=400)
+    gb.advance_slow_step(ramp=1 / case.plan.n_ramp, **kw)
+    state = gb.save_state()
+    r1 = gb.advance_slow_step(ramp=2 / case.plan.n_ramp, **kw)
+    u1, a1 = gb.read(M.F_U), gb.read(M.F_ALPHA)
+    gb.advance_slow_step(ramp=3 / case.plan.n_ramp, **kw)        # move on, then rewind
+    gb.load_state(state)
+    r2 = gb.advance_slow_step(ramp=2 / case.plan.n_ramp, **kw)
+    assert r2.substeps == r1.substeps and r2.ke_final == r1.ke_final
+    assert np.array_equal(gb.read(M.F_U), u1) and np.array_equal(gb.read(M.F_ALPHA), a1)
+    other = M.body_from_case(ctx, B.bar2d(nx=12, ny=5), precision)
+    with pytest.raises(M.MtsError) as e:
+        other.load_state(state)
+    assert e.value.status == M.ERR_INVALID_ARG
+    with pytest.raises(M.MtsError):
+        gb.load_state(state[:-8])
