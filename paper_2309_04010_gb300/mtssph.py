@@ -108,6 +108,11 @@ def lib():
         "mts_body_damping_layout": [vp, vp, C.POINTER(i32)],
         "mts_save_state": [vp, vp, C.POINTER(C.c_size_t)],
         "mts_batch_create": [vp, i32, vp, C.POINTER(vp)],
+        "mts_adjoint_enable": [vp, i64],
+        "mts_adjoint_reset": [vp],
+        "mts_adjoint_seed": [vp, vp, vp, vp],
+        "mts_adjoint_slow_step": [vp, C.POINTER(StepParams), i64, vp],
+        "mts_read_adjoint": [vp, i32, vp, i64],
         "mts_batch_advance": [vp, vp, vp],
         "mts_batch_destroy": [vp],
         "mts_load_state": [vp, vp, C.c_size_t],
@@ -277,12 +282,69 @@ class Body:
                      sigma_inf: float = 0.0, delta: float = 0.0, H: float = 0.0):
         _check(lib().mts_set_material(self._h, model, rho0, E, nu, sigma0, sigma_inf, delta, H),
                "mts_set_material")
+        self._material = (model, rho0, E, nu, sigma0, sigma_inf, delta, H)
 
     def set_damping(self, eta: float):
         _check(lib().mts_set_damping(self._h, eta), "mts_set_damping")
 
     def set_diffusion(self, D: float, beta: float, c0: float):
         _check(lib().mts_set_diffusion(self._h, D, beta, c0), "mts_set_diffusion")
+        self._diffusion = (D, beta, c0)
+
+    # -- parameters of the reverse mode
+    def parameters(self) -> np.ndarray:
+        """theta = (E, sigma0, sigma_inf, delta, H, D, beta) as currently set."""
+        m = getattr(self, "_material", None)
+        if m is None:
+            raise RuntimeError("no material set")
+        D, beta, _ = getattr(self, "_diffusion", (0.0, 0.0, 0.0))
+        return np.array([m[2], m[4], m[5], m[6], m[7], D, beta])
+
+    def set_parameters(self, theta):
+        """Set theta (see parameters()); the concentration field is kept."""
+        th = [float(x) for x in theta]
+        m = self._material
+        self.set_material(m[0], m[1], th[0], m[3], th[1], th[2], th[3], th[4])
+        if getattr(self, "_diffusion", None) is not None:
+            c = self.read(F_C)
+            self.set_diffusion(th[5], th[6], self._diffusion[2])
+            self.write(F_C, c)
+
+    # -- reverse mode (FP64 bodies)
+    def adjoint_enable(self, max_substeps: int):
+        _check(lib().mts_adjoint_enable(self._h, int(max_substeps)), "mts_adjoint_enable")
+        self._adj_cap = int(max_substeps)
+
+    def adjoint_reset(self):
+        _check(lib().mts_adjoint_reset(self._h), "mts_adjoint_reset")
+
+    def adjoint_seed(self, u_bar=None, tip_bar=None, force_bar=None):
+        ub = None if u_bar is None else np.ascontiguousarray(u_bar, np.float64).reshape(self.n * self.dim)
+        tb = None if tip_bar is None else np.ascontiguousarray(
+            list(tip_bar) + [0.0] * (3 - len(tip_bar)), np.float64)
+        fb = None if force_bar is None else np.ascontiguousarray(
+            list(force_bar) + [0.0] * (3 - len(force_bar)), np.float64)
+        _check(lib().mts_adjoint_seed(self._h, None if ub is None else _ptr(ub),
+                                      None if tb is None else _ptr(tb),
+                                      None if fb is None else _ptr(fb)), "mts_adjoint_seed")
+
+    def adjoint_slow_step(self, substeps: int, dt_slow: float = 0.0, ramp: float = 0.0,
+                          ke_ref: float = 1.0, ke_mode: int = 0, dt_sub: float = 0.0,
+                          force_dt: bool = False, **_ignored) -> np.ndarray:
+        """Reverse one slow step (the body must hold the state at its start);
+        returns d objective / d theta contributed by the step."""
+        p = StepParams(dt_slow, ramp, dt_sub, -1.0, ke_ref, int(substeps), ke_mode, 0,
+                       int(force_dt), 0)
+        th = np.zeros(7)
+        _check(lib().mts_adjoint_slow_step(self._h, C.byref(p), int(substeps), _ptr(th)),
+               "mts_adjoint_slow_step")
+        return th
+
+    def read_adjoint(self, field: int) -> np.ndarray:
+        w = self._width(field)
+        out = np.zeros(self.n * w)
+        _check(lib().mts_read_adjoint(self._h, field, _ptr(out), out.size), "mts_read_adjoint")
+        return out.reshape(self.n, w) if w > 1 else out
 
     def set_bc_displacement(self, ids, axis_mask: int, u_unit=None, report_force: bool = False):
         ids = np.ascontiguousarray(ids, dtype=np.int64)
@@ -393,6 +455,50 @@ class Batch:
         R = (StepReport * len(params))()
         _check(lib().mts_batch_advance(self._h, P, R), "mts_batch_advance")
         return list(R)
+
+
+def slow_steps(body: Body, theta, steps):
+    """Run the slow steps `steps` (one dict of advance_slow_step arguments
+    each) with parameters theta = (E, sigma0, sigma_inf, delta, H, D, beta)
+    and return the tip deflection and end force of the last one as a torch
+    tensor [tip (dim), force (dim)], differentiable with respect to theta
+    through the library's reverse mode (FP64 bodies; substep sizes and counts
+    held at the forward run's values)."""
+    import torch
+
+    class _SlowSteps(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, th):
+            body.set_parameters(th.detach().cpu().numpy())
+            ckpts, counts = [], []
+            r = None
+            for p in steps:
+                ckpts.append(body.save_state())
+                r = body.advance_slow_step(**p)
+                counts.append(int(r.substeps))
+            ctx.ckpts, ctx.counts, ctx.final = ckpts, counts, body.save_state()
+            d = body.dim
+            return torch.tensor(list(r.tip_deflection[:d]) + list(r.end_force[:d]),
+                                dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gout):
+            d = body.dim
+            g = gout.detach().cpu().numpy()
+            need = max(ctx.counts)
+            if getattr(body, "_adj_cap", 0) < need:
+                body.adjoint_enable(need)
+            else:
+                body.adjoint_reset()
+            body.adjoint_seed(tip_bar=g[:d], force_bar=g[d:])
+            th = np.zeros(7)
+            for p, ck, k in zip(reversed(steps), reversed(ctx.ckpts), reversed(ctx.counts)):
+                body.load_state(ck)
+                th += body.adjoint_slow_step(k, **p)
+            body.load_state(ctx.final)
+            return torch.from_numpy(th).to(gout.dtype)
+
+    return _SlowSteps.apply(theta)
 
 
 def body_from_case(ctx: Context, case, precision: int = FP64, damp_layout: int = DAMP_AUTO) -> Body:

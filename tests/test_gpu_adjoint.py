@@ -1,0 +1,219 @@
+"""Reverse mode on the GPU (FP64) against the reverse-mode oracle
+(oracle/adjoint.py, itself pinned to the C oracle by central differences):
+parameter gradients and initial-state adjoints of an objective of the tip
+deflection, the end force and the final displacement, over slow steps with
+the substep sizes of the forward run held fixed."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import adjoint as A
+from paper_2309_04010_gb300 import mtssph as M
+from synth import bodies as B
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = M.Context(0)
+    yield c
+    c.close()
+
+
+def small_cylinder():
+    return B.cylinder3d(L=4e-3, R=1e-3, dx=0.25e-3, n_slow=10)
+
+
+def small_strip():
+    c = B.strip2d(nx=36, ny=10, dx=1e-5)
+    c.eta = 1.0
+    return c
+
+
+def small_bar():
+    return B.bar2d(nx=24, ny=6, n_slow=4)
+
+
+CASES = {"cyl3d_j2": (small_cylinder, 2, 8), "strip2d_swelling": (small_strip, 2, 6),
+         "bar2d_svk": (small_bar, 2, 12)}
+
+
+def _weights(case, seed=11):
+    rng = np.random.default_rng(seed)
+    d = case.dim
+    return rng.normal(size=d), rng.normal(size=d), rng.normal(size=(case.n, d))
+
+
+def _steps(case, gb, nslow, nsub):
+    dts = gb.diffusion_dt()[1] if case.diffusion is not None else 0.0
+    return [dict(dt_slow=dts, ramp=l / max(case.plan.n_ramp, 1), ke_tol=-1.0,
+                 ke_ref=case.plan.ke_ref, max_substeps=nsub, check_every=0)
+            for l in range(1, nslow + 1)]
+
+
+def _gpu_gradient(ctx, case, nslow, nsub, w_tip, w_f, r):
+    gb = M.body_from_case(ctx, case, M.FP64)
+    steps = _steps(case, gb, nslow, nsub)
+    ckpts, counts = [], []
+    for p in steps:
+        ckpts.append(gb.save_state())
+        counts.append(gb.advance_slow_step(**p).substeps)
+    u_end = gb.read(M.F_U)
+    gb.adjoint_enable(max(counts))
+    gb.adjoint_seed(u_bar=r, tip_bar=w_tip, force_bar=w_f)
+    th = np.zeros(7)
+    for p, ck, k in zip(reversed(steps), reversed(ckpts), reversed(counts)):
+        gb.load_state(ck)
+        th += gb.adjoint_slow_step(k, **p)
+    return gb, th, steps, u_end
+
+
+def _oracle_gradient(case, gb, steps, nsub, w_tip, w_f, r):
+    ob = O.body_from_case(case, damp_layout=gb.damping_layout())
+    tb = A.TorchBody(case, ob)
+    th = tb.theta0().clone().requires_grad_(True)
+    st0 = list(tb.initial_state())
+    u0 = st0[0].clone().requires_grad_(True)
+    st = (u0, *st0[1:])
+    ef = tip = None
+    for p in steps:
+        st, ef, tip, _ = tb.slow_step(st, th, p["ramp"], nsub, dt_slow=p["dt_slow"])
+    L = (torch.from_numpy(w_tip) * tip).sum() + (torch.from_numpy(w_f) * ef).sum() + (
+        torch.from_numpy(r) * tb.to_original(st[0])).sum()
+    g_th, g_u0 = torch.autograd.grad(L, (th, u0))
+    return g_th.numpy(), tb.to_original(g_u0).numpy(), tb.to_original(st[0]).detach().numpy()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_matches_reverse_mode_oracle(ctx, name):
+    make, nslow, nsub = CASES[name]
+    case = make()
+    w_tip, w_f, r = _weights(case)
+    gb, th_g, steps, u_end = _gpu_gradient(ctx, case, nslow, nsub, w_tip, w_f, r)
+    th_o, u0_o, u_o = _oracle_gradient(case, gb, steps, nsub, w_tip, w_f, r)
+    assert np.max(np.abs(u_end - u_o)) <= 1e-11 * np.max(np.abs(u_o))   # same forward run
+    used = [0] if case.material.model == "svk" else [0, 1, 2, 3, 4]
+    if case.diffusion is not None:
+        used += [5, 6]
+    for k in used:
+        assert abs(th_g[k] - th_o[k]) <= 1e-8 * max(abs(th_o[k]), 1e-300), (
+            A.THETA_NAMES[k], th_g[k], th_o[k])
+        assert th_o[k] != 0.0, A.THETA_NAMES[k]
+    u0_g = gb.read_adjoint(M.F_U)
+    assert np.max(np.abs(u0_g - u0_o)) <= 1e-8 * np.max(np.abs(u0_o))
+
+
+def test_adjoint_dot_product_one_substep(ctx):
+    """<J dtheta, lambda> from the oracle's forward-mode derivative equals
+    <dtheta, J^T lambda> from the GPU reverse mode, for one substep of the
+    J2 cylinder (lambda on the final displacement)."""
+    case = small_cylinder()
+    rng = np.random.default_rng(5)
+    lam = rng.normal(size=(case.n, case.dim))
+    gb = M.body_from_case(ctx, case, M.FP64)
+    p = _steps(case, gb, 1, 1)[0]
+    ck = gb.save_state()
+    gb.advance_slow_step(**p)
+    gb.adjoint_enable(1)
+    gb.adjoint_seed(u_bar=lam)
+    gb.load_state(ck)
+    th_g = gb.adjoint_slow_step(1, **p)
+    ob = O.body_from_case(case, damp_layout=gb.damping_layout())
+    tb = A.TorchBody(case, ob)
+    th0 = tb.theta0()
+    dth = torch.from_numpy(rng.normal(size=7)) * th0.abs()
+    dth[5] = dth[6] = 0.0
+
+    def f(th):
+        st, _, _, _ = tb.slow_step(tb.initial_state(), th, p["ramp"], 1)
+        return tb.to_original(st[0])
+
+    _, jv = torch.func.jvp(f, (th0,), (dth,))
+    lhs = float((jv.numpy() * lam).sum())
+    rhs = float((dth.numpy() * th_g).sum())
+    assert abs(lhs - rhs) <= 1e-9 * max(abs(lhs), abs(rhs)), (lhs, rhs)
+
+
+def test_adjoint_central_differences_on_gpu(ctx):
+    """The GPU's own forward runs, differenced in E and sigma_inf with fixed
+    substep size, against the GPU reverse mode."""
+    case = small_cylinder()
+    w_tip, w_f, r = _weights(case, seed=3)
+    gb0 = M.body_from_case(ctx, case, M.FP64)
+    dt_sub = 0.5 * 0.6 * case.h_over_dx * case.dx / np.sqrt(
+        case.material.E / (3 * (1 - 2 * case.material.nu)) / case.material.rho0)
+    steps = [dict(ramp=l / case.plan.n_ramp, ke_tol=-1.0, max_substeps=6, dt_sub=dt_sub)
+             for l in (1, 2)]
+
+    def objective(theta):
+        gb = M.body_from_case(ctx, case, M.FP64)
+        gb.set_parameters(theta)
+        rep = None
+        for p in steps:
+            rep = gb.advance_slow_step(**p)
+        d = case.dim
+        return (w_tip @ np.array(rep.tip_deflection[:d]) + w_f @ np.array(rep.end_force[:d]) +
+                float((r * gb.read(M.F_U)).sum()))
+
+    ckpts = []
+    for p in steps:
+        ckpts.append(gb0.save_state())
+        gb0.advance_slow_step(**p)
+    gb0.adjoint_enable(6)
+    gb0.adjoint_seed(u_bar=r, tip_bar=w_tip, force_bar=w_f)
+    th = np.zeros(7)
+    for p, ck in zip(reversed(steps), reversed(ckpts)):
+        gb0.load_state(ck)
+        th += gb0.adjoint_slow_step(6, **p)
+    theta0 = gb0.parameters()
+    for k in (0, 2):
+        h = 1e-6 * abs(theta0[k])
+        tp, tm = theta0.copy(), theta0.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (objective(tp) - objective(tm)) / (2 * h)
+        assert abs(th[k] - fd) <= 2e-6 * max(abs(fd), abs(th[k])), (A.THETA_NAMES[k], th[k], fd)
+
+
+def test_autograd_function_wraps_the_reverse_mode(ctx):
+    case = small_bar()
+    gb = M.body_from_case(ctx, case, M.FP64)
+    steps = _steps(case, gb, 2, 10)
+    theta = torch.tensor(gb.parameters(), dtype=torch.float64, requires_grad=True)
+    ck = gb.save_state()
+    out = M.slow_steps(gb, theta, steps)
+    w = torch.tensor([0.3, -0.2, 1.1, 0.4], dtype=torch.float64)
+    (g,) = torch.autograd.grad((out * w).sum(), theta)
+    # the same through the explicit calls
+    gb2 = M.body_from_case(ctx, case, M.FP64)
+    ckpts, counts = [], []
+    for p in steps:
+        ckpts.append(gb2.save_state())
+        counts.append(gb2.advance_slow_step(**p).substeps)
+    gb2.adjoint_enable(max(counts))
+    gb2.adjoint_seed(tip_bar=w[:2].numpy(), force_bar=w[2:].numpy())
+    th = np.zeros(7)
+    for p, c, k in zip(reversed(steps), reversed(ckpts), reversed(counts)):
+        gb2.load_state(c)
+        th += gb2.adjoint_slow_step(k, **p)
+    assert np.array_equal(g.numpy(), th)
+    assert g[0] != 0
+    gb.load_state(ck)
+
+
+def test_adjoint_errors(ctx):
+    case = small_bar()
+    gm = M.body_from_case(ctx, case, M.MIXED)
+    with pytest.raises(M.MtsError) as e:
+        gm.adjoint_enable(4)
+    assert e.value.status == M.ERR_STATE
+    gb = M.body_from_case(ctx, case, M.FP64)
+    with pytest.raises(M.MtsError) as e:
+        gb.adjoint_slow_step(2, ramp=0.1)
+    assert e.value.status == M.ERR_STATE
+    gb.adjoint_enable(3)
+    with pytest.raises(M.MtsError) as e:
+        gb.adjoint_slow_step(5, ramp=0.1)
+    assert e.value.status == M.ERR_INVALID_ARG
