@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--cpu-substeps", type=int, default=2,
                     help="substeps in the oracle CPU-baseline sample (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--batch-count", type=int, default=64,
+                    help="instances of the batched workload (0 = skip)")
+    ap.add_argument("--adjoint-steps", type=int, default=3,
+                    help="slow steps reversed in the FP64 reverse-mode measurement (0 = skip)")
     ap.add_argument("--ref-substeps", type=int, default=1,
                     help="oracle substeps per reference-arm step")
     return ap.parse_args()
@@ -201,6 +205,128 @@ def run_reference(args, rank):
     }), flush=True)
 
 
+def reduce_over_ranks(dist, ms: float, updates: float, device: str):
+    """Whole-job timing of replicated ranks: the slowest rank's time (max) and
+    the particle updates of all ranks (sum); dist = None for one process."""
+    if dist is None:
+        return ms, updates
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([updates], device=device, dtype=torch.float64)
+    dist.all_reduce(u)
+    dist.barrier()
+    return float(t.item()), float(u.item())
+
+
+def shard_instances(sizes, world: int):
+    """Instances of a batch dealt to ranks by estimated work (particles),
+    largest first onto the least-loaded rank; returns one index list per
+    rank, each ascending.  Instances are independent: no collective is needed
+    on the data path."""
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in sorted(range(len(sizes)), key=lambda k: (-sizes[k], k)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(p) for p in parts]
+
+
+def _batch_params(c, body, l):
+    """Slow step l of a batched-workload instance (strips: one diffusion step
+    of the stable size; bars: load increment), at most 2,000 substeps."""
+    p = dict(ramp=l / max(c.plan.n_ramp, 1), ke_tol=c.plan.ke_tol, ke_ref=c.plan.ke_ref,
+             ke_mode=c.plan.ke_mode, max_substeps=2000)
+    if c.diffusion is not None:
+        p["dt_slow"] = body.diffusion_dt()[1]
+    return p
+
+
+def measure_batch(ctx, args, M, rank=0, world=1, dist=None):
+    """The batched mode on the 64-instance workload (uneven 2D strips and J2
+    bars, mixed precision): slow steps of all bodies through one batch graph
+    launch each, against the same bodies advanced one after another.  With
+    several ranks each takes a shard of the instances (no collective on the
+    data path; max time and summed updates over ranks)."""
+    import torch
+    from synth import bodies as B
+    cases_all = B.batch_instances(count=args.batch_count)
+    mine = shard_instances([c.n for c in cases_all], world)[rank]
+    cases = [cases_all[i] for i in mine]
+    bodies = [M.body_from_case(ctx, c, M.MIXED) for c in cases]
+    bt = M.Batch(ctx, bodies)
+    bt.advance([_batch_params(c, b, 1) for c, b in zip(cases, bodies)])      # warm-up
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    reps = bt.advance([_batch_params(c, b, 2) for c, b in zip(cases, bodies)])
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    upd_b = sum(c.n * r.substeps for c, r in zip(cases, reps))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    upd_s = 0
+    for c, b in zip(cases, bodies):
+        r = b.advance_slow_step(**_batch_params(c, b, 3))
+        upd_s += c.n * r.substeps
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    bt.close()
+    for b in bodies:
+        b.close()
+    tb, upd_b = reduce_over_ranks(dist, tb, float(upd_b), "cuda")
+    ts, upd_s = reduce_over_ranks(dist, ts, float(upd_s), "cuda")
+    return {"workload": f"batch_instances-{len(cases_all)}",
+            "particles": int(sum(c.n for c in cases_all)), "n_gpus": world,
+            "batched_value": upd_b / tb, "sequential_value": upd_s / ts,
+            "speedup": (upd_b / tb) / (upd_s / ts), "unit": UNIT,
+            "substeps_range": [int(min(r.substeps for r in reps)), int(max(r.substeps for r in reps))],
+            "timing": "host wall clock around one slow step of every instance (slow step 2 "
+                      "batched, slow step 3 one body after another), stream synchronised, "
+                      "max over ranks"}
+
+
+def measure_adjoint(ctx, args, M, case):
+    """Reverse mode (FP64) on the cylinder: one forward slow step, then its
+    reversal (recompute with tape + transposed substeps)."""
+    import numpy as np
+    import torch
+    gb = M.body_from_case(ctx, case, M.FP64)
+    plan = case.plan
+    steps = [dict(ramp=l / plan.n_ramp, ke_tol=plan.ke_tol, ke_ref=plan.ke_ref,
+                  ke_mode=plan.ke_mode, max_substeps=plan.max_substeps)
+             for l in range(1, args.adjoint_steps + 1)]
+    ckpts, counts = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for p in steps:
+        ckpts.append(gb.save_state())
+        counts.append(gb.advance_slow_step(**p).substeps)
+    torch.cuda.synchronize()
+    tf = time.perf_counter() - t0
+    gb.adjoint_enable(max(counts))
+    gb.adjoint_seed(tip_bar=[1.0, 0.0, 0.0], force_bar=[1.0, 0.0, 0.0])
+    th = np.zeros(7)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for p, ck, k in zip(reversed(steps), reversed(ckpts), reversed(counts)):
+        gb.load_state(ck)
+        th += gb.adjoint_slow_step(k, **p)
+    torch.cuda.synchronize()
+    ta = time.perf_counter() - t0
+    gb.close()
+    sub = sum(counts)
+    return {"workload": f"cylinder3d-j2-{case.n}", "precision": "f64", "slow_steps": len(steps),
+            "substeps": sub, "forward_s": tf, "reverse_s": ta,
+            "reverse_value": case.n * sub / ta, "unit": UNIT, "reverse_over_forward": ta / tf,
+            "dtheta_nonzero": [bool(x != 0) for x in th],
+            "timing": "host wall clock, stream synchronised; the reverse time includes the "
+                      "taped recomputation of the step"}
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -271,16 +397,7 @@ def run_ours(args, rank, world, local):
     stage_avg = {k: stage_ms[k] / stage_n[k] for k in stage_ms if stage_n[k]}
     dom = max(stage_avg, key=stage_avg.get) if stage_avg else 2
     prof_ms, prof_n = stage_ms.get(dom, 0.0), stage_n.get(dom, 0)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        tot = torch.tensor([float(substeps)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tot)
-        total_updates = float(tot.item()) * case.n
-        dist.barrier()
-    else:
-        total_updates = float(substeps) * case.n
+    ms, total_updates = reduce_over_ranks(dist, ms, float(substeps) * case.n, "cuda")
     value = total_updates / (ms * 1e-3)
 
     # e2e through the C ABI with host-resident state: upload (u, v) from pinned
@@ -328,6 +445,9 @@ def run_ours(args, rank, world, local):
         g64.close()
         g32.close()
 
+    batch = measure_batch(ctx, args, M, rank, world, dist) if args.batch_count > 0 else None
+    adjoint = measure_adjoint(ctx, args, M, case) if args.adjoint_steps > 0 and rank == 0 else None
+
     if rank != 0:
         return
     hbm, peak_kind = peaks()
@@ -369,6 +489,8 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d},
         "fp64_comparison": fp64,
+        "batch": batch,
+        "adjoint": adjoint,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -382,15 +382,16 @@ static int build_b0(ob_body *b) {
 /* ------------------------------------------------------------------ */
 /* Canonical order of the pairwise damping sweep (Sec. 4.3 leaves the   */
 /* order to the cited splitting scheme; this is the order chosen):      */
-/*   block = cell >> blk_shift per axis (B = 2^blk_shift cells, B*dx    */
-/*   > 2h); pair (a<b) is owned by the componentwise-min block of its   */
-/*   two particles; block colour = parity bits of the owner block;      */
-/*   inside an owner block its pairs, visited by offset class (the      */
-/*   sign-folded cell offset) and then ascending (a,b), take the        */
-/*   smallest sub-colour unused at a and at b that holds fewer than 32  */
-/*   pairs so far (greedy, capped level size).  Sequential              */
-/*   order: colour, owner block Morton key, sub-colour, a, b.  Pairs of */
-/*   one (colour, sub-colour) touch disjoint particles.                 */
+/*   block = cell >> ax_shift[k] on axis k (2^shift cells, 2^shift * dx */
+/*   > 2h; OB_WHOLE_AXIS = the axis is not blocked); pair (a<b) is owned */
+/*   by the componentwise-min block of its two particles; block colour  */
+/*   = parity bits of the owner block; inside an owner block its pairs, */
+/*   visited by offset class (the sign-folded cell offset) and then     */
+/*   ascending (a,b), take the smallest sub-colour unused at a and at b */
+/*   that holds fewer than level_cap pairs so far (greedy; level_cap 0  */
+/*   = no cap).  Sequential order: colour, owner block Morton key,      */
+/*   sub-colour, a, b.  Pairs of one (colour, sub-colour) touch         */
+/*   disjoint particles.                                                */
 /* ------------------------------------------------------------------ */
 typedef struct { int32_t col; int32_t sub; uint64_t key; int32_t cls; int32_t a, b; } pair_rec;
 

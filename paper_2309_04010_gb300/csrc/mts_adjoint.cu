@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(128) k_adj_diffuse(Args<double> A, const doubl
     for (int k = threadIdx.x; k < nh; k += blockDim.x) {
         const long long g = __ldg(A.halo_idx + h0 + k);
         double x[P];
-        ldg_vec<double, P>(x, A.X + g * P);
+        ldg_vec<double, P>(x, A.halo_x + (h0 + k) * P);
         st_vec<double, P>(sX + k * P, x);
         sY[k] = y[g];
         sC[k] = cpre[g];

@@ -88,7 +88,7 @@ void body_free(mts_body *b) {
                      (void **)&b->c_tmp, (void **)&b->c_held, (void **)&b->u, (void **)&b->u_unit,
                      (void **)&b->flags, (void **)&b->ctrl, (void **)&b->part_force,
                      (void **)&b->part_drift, (void **)&b->scratch, (void **)&b->halo_off,
-                     (void **)&b->halo_idx, (void **)&b->lself, (void **)&b->lell,
+                     (void **)&b->halo_idx, (void **)&b->halo_x, (void **)&b->lself, (void **)&b->lell,
                      (void **)&b->lell_off, (void **)&b->tile_w, (void **)&b->pair_slot,
                      (void **)&b->kpad_ab, (void **)&b->kpad_g, (void **)&b->bperm,
                      (void **)&b->bflags, (void **)&b->tape_u, (void **)&b->tape_cp,

@@ -122,6 +122,7 @@ struct Args {
     int max_halo;                // largest halo (tile + neighbours)
     const long long *halo_off;   // tile -> first halo entry, ntiles + 1
     const int32_t *halo_idx;     // halo particle indices, ascending per tile
+    const R *halo_x;             // per halo entry: X relative to the tile's first particle
     const uint16_t *lself;       // particle -> its slot in its tile's halo
     const uint16_t *lell;        // local neighbour slots, neighbour-major per tile
     const long long *lell_off;   // tile -> first local ELL entry
@@ -199,6 +200,7 @@ struct mts_body {
     int max_halo;
     long long *halo_off;
     int32_t *halo_idx;
+    void *halo_x;             // per halo entry, storage precision: X - X(first particle of tile)
     uint16_t *lself;
     uint16_t *lell;
     long long *lell_off;

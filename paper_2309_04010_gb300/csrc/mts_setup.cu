@@ -590,6 +590,24 @@ __global__ void k_halo_off(const long long *seg, const long long *scan, long lon
     }
 }
 
+// per halo entry of tile t: X(particle) - X(first particle of the tile), in
+// FP64, stored in the storage precision
+template <class R, int P>
+__global__ void k_halo_x(const long long *hoff, const int32_t *halo, long long ntiles, int T,
+                         long long total, const double *X64, R *hx) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    long long lo = 0, hi = ntiles;   // tile of entry e: hoff[t] <= e < hoff[t + 1]
+    while (hi - lo > 1) {
+        const long long mid = (lo + hi) >> 1;
+        if (hoff[mid] <= e) lo = mid;
+        else hi = mid;
+    }
+    const double *o = X64 + lo * T * P, *x = X64 + (long long)halo[e] * P;
+#pragma unroll
+    for (int k = 0; k < P; ++k) hx[e * P + k] = (R)(x[k] - o[k]);
+}
+
 __global__ void k_tile_w(const long long *off, long long n, int T, long long ntiles, long long *w) {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
@@ -759,6 +777,21 @@ mts_status build_tiles(mts_body *b, Tmp &tmp, cudaStream_t st, int T) {
         return MTS_ERR_INVALID_ARG;
     }
     b->max_halo = (int)hm;
+    {
+        const int P = b->dim == 2 ? 2 : 4;
+        MTS_TRY(dalloc_into(ctx, &b->halo_x, (size_t)total * P * b->rsize + 16));
+        if (b->rsize == 8) {
+            if (P == 2)
+                k_halo_x<double, 2><<<grid_for(total), TPB, 0, st>>>(b->halo_off, b->halo_idx, ntiles, T, total, b->X64, (double *)b->halo_x);
+            else
+                k_halo_x<double, 4><<<grid_for(total), TPB, 0, st>>>(b->halo_off, b->halo_idx, ntiles, T, total, b->X64, (double *)b->halo_x);
+        } else {
+            if (P == 2)
+                k_halo_x<float, 2><<<grid_for(total), TPB, 0, st>>>(b->halo_off, b->halo_idx, ntiles, T, total, b->X64, (float *)b->halo_x);
+            else
+                k_halo_x<float, 4><<<grid_for(total), TPB, 0, st>>>(b->halo_off, b->halo_idx, ntiles, T, total, b->X64, (float *)b->halo_x);
+        }
+    }
     long long *w = tmp.get<long long>(ntiles + 1);
     NEED(w);
     MTS_TRY(dalloc_t(ctx, &b->lell_off, ntiles + 1));

@@ -128,9 +128,11 @@ __global__ void __launch_bounds__(256) k_stress(Args<R> A) {
             PB[r][c] = acc;
         }
     if constexpr (D == 3) {
-        // force record: X then P B0 row-major, 12 reals (three 16-byte rows)
+        // force record: X then P B0 row-major, 12 reals (three 16-byte rows);
+        // X relative to the body's corner (one origin for every particle: the
+        // force gathers records of particles from many tiles)
         R rec[12];
-        ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(rec), sX + A.lself[i] * P);
+        ldg_vec<R, 4>(*reinterpret_cast<R(*)[4]>(rec), A.X + i * P);
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -788,7 +790,7 @@ __global__ void __launch_bounds__(256) k_diffuse(Args<R> A, R dt) {
     for (int k = threadIdx.x; k < nh; k += blockDim.x) {
         const long long g = __ldg(A.halo_idx + h0 + k);
         R x[P];
-        ldg_vec<R, P>(x, A.X + g * P);
+        ldg_vec<R, P>(x, A.halo_x + (h0 + k) * P);
         st_vec<R, P>(sX + k * P, x);
         sC[k] = A.c[g];
     }
@@ -954,12 +956,21 @@ __global__ void k_tip(const double *u, const uint8_t *flags, long long n, double
         }
 }
 
-__global__ void k_tip_final(const double *part, int nblk, double *out) {
-    if (threadIdx.x != 0) return;
+// all partials summed by one block: strided per thread, then a fixed tree
+__global__ void __launch_bounds__(kBlock) k_tip_final(const double *part, int nblk, double *out) {
+    __shared__ double red[4][kBlock];
     double s[4] = {0, 0, 0, 0};
-    for (int b = 0; b < nblk; ++b)
+    for (int b = threadIdx.x; b < nblk; b += kBlock)
         for (int k = 0; k < 4; ++k) s[k] += part[b * 4 + k];
-    for (int k = 0; k < 3; ++k) out[k] = s[3] > 0 ? s[k] / s[3] : 0.0;
+    for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = kBlock / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) out[k] = red[3][0] > 0 ? red[k][0] / red[3][0] : 0.0;
 }
 
 // --------------------------------------------------------------------- args
@@ -975,6 +986,7 @@ Args<R> make_args(mts_body *b) {
     A.max_halo = b->max_halo;
     A.halo_off = b->halo_off;
     A.halo_idx = b->halo_idx;
+    A.halo_x = (const R *)b->halo_x;
     A.lself = b->lself;
     A.lell = b->lell;
     A.lell_off = b->lell_off;
@@ -1296,7 +1308,7 @@ mts_status launch_tip(mts_body *b, double *out3) {
         k_tip<2><<<g, kBlock, 0, b->ctx->stream>>>(b->u, b->flags, b->n, part);
     else
         k_tip<3><<<g, kBlock, 0, b->ctx->stream>>>(b->u, b->flags, b->n, part);
-    k_tip_final<<<1, 32, 0, b->ctx->stream>>>(part, (int)g, part + (size_t)g * 4);
+    k_tip_final<<<1, kBlock, 0, b->ctx->stream>>>(part, (int)g, part + (size_t)g * 4);
     MTS_CUDA(cudaGetLastError());
     MTS_CUDA(cudaMemcpyAsync(out3, part + (size_t)g * 4, 3 * sizeof(double), cudaMemcpyDeviceToHost,
                              b->ctx->stream));

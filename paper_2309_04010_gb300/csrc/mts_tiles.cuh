@@ -21,7 +21,10 @@ __host__ __device__ __forceinline__ size_t second_off(int max_halo) {
 // A CTA owns one Morton tile of T = blockDim.x consecutive particles.  It
 // stages the reference positions and one more per-particle array of the tile's
 // halo (the tile and all its neighbours) in shared memory, then every
-// neighbour access reads shared memory through a 16-bit local slot.
+// neighbour access reads shared memory through a 16-bit local slot.  The
+// positions come from the per-tile table halo_x (computed once in FP64
+// relative to the tile's first particle), so in FP32 the separations keep
+// their relative precision however far the tile is from the body's corner.
 template <class R, int P, int NY>
 __device__ __forceinline__ int stage_halo(const Args<R> &A, R *sX, R *sY, const R *Y) {
     const long long t = blockIdx.x;
@@ -40,7 +43,7 @@ __device__ __forceinline__ int stage_halo(const Args<R> &A, R *sX, R *sY, const 
         for (int u = 0; u < U; ++u) {
             const int k = k0 + u * blockDim.x;
             if (g[u] < 0) continue;
-            if (sX) cp_async_reals<R, P>(sX + (size_t)k * P, A.X + (size_t)g[u] * P);
+            if (sX) cp_async_reals<R, P>(sX + (size_t)k * P, A.halo_x + (size_t)(h0 + k) * P);
             if (sY) cp_async_reals<R, NY>(sY + (size_t)k * NY, Y + (size_t)g[u] * NY);
         }
     }

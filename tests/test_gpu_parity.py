@@ -331,3 +331,53 @@ def test_save_load_state_resumes_bit_exact(ctx, precision):
     assert e.value.status == M.ERR_INVALID_ARG
     with pytest.raises(M.MtsError):
         gb.load_state(state[:-8])
+
+
+# ---------------------------------------------------------------- other workloads at full size
+def test_full_size_strip_diffusion_swelling():
+    """The 2D swelling strip at its full size (2,000 x 20 = 40,000 particles):
+    setup bit-exact, then two slow steps (diffusion step + 40 substeps each)
+    against the oracle, FP64 and mixed precision."""
+    ctx = M.Context(0)
+    case = B.strip2d()
+    assert case.n == 40000
+    ob = O.body_from_case(case)
+    dts = ob.diffusion_dt()[1]
+    for l in (1, 2):
+        ob.advance(dt_slow=dts, ke_tol=-1.0, max_substeps=40, ke_mode=1)
+    for prec, tol_u, tol_c in ((M.FP64, 1e-9, 1e-12), (M.MIXED, 1e-4, 1e-5)):
+        gb = M.body_from_case(ctx, case, prec)
+        if prec == M.FP64:
+            for g, o in zip(gb.colouring(), ob.colouring()):
+                assert np.array_equal(g, o)
+        for l in (1, 2):
+            r = gb.advance_slow_step(dt_slow=dts, ke_tol=-1.0, max_substeps=40, ke_mode=1)
+            assert r.substeps == 40
+        assert rel(gb.read(M.F_C), ob.read(O.F_C)) < tol_c
+        assert rel(gb.read(M.F_U), ob.read(O.F_U)) < tol_u
+        gb.close()
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(M.FP64, 1e-12), (M.MIXED, 2e-5)])
+def test_full_size_plate_properties(precision, tol):
+    """The 3D plate at its full size (1,000 x 250 x 10 = 2.5 M particles), too
+    large for the oracle's setup: properties that hold at any size.  The
+    neighbour lists are symmetric with the lattice count in the interior, the
+    damping order lists every pair once, and an affine displacement field
+    gives F = I + G exactly at every particle, surfaces included."""
+    ctx = M.Context(0)
+    case = B.plate3d()
+    assert case.n == 2_500_000
+    gb = M.Body(ctx, case.X, case.dx, case.h_over_dx, precision)
+    off, idx = gb.neighbors()
+    deg = np.diff(off)
+    assert off[-1] % 2 == 0 and deg.max() <= 80 and np.median(deg) == 80
+    pa, pb = gb.colouring()[:2]
+    assert pa.size == off[-1] // 2 and np.all(pa < pb)
+    G = np.random.default_rng(4).uniform(-0.02, 0.02, (3, 3))
+    gb.write(M.F_U, case.X @ G.T)
+    F = gb.read(M.F_DEFGRAD).reshape(-1, 3, 3)
+    assert np.max(np.abs(F - (np.eye(3) + G))) < tol
+    gb.close()
+    ctx.close()
