@@ -162,6 +162,20 @@ mts_status mts_set_bc_displacement(mts_body *body, int64_t count, const int64_t 
 /* Hold c = c_value on `count` particles (Dirichlet layers of the slow step). */
 mts_status mts_set_bc_concentration(mts_body *body, int64_t count, const int64_t *ids,
                                     double c_value);
+/* Discretisation of the diffusion step: 0 (default) = the one-pass pairwise
+ * Laplacian in the reference configuration; 1 = the two-stage form of
+ * Sec. 3.2 in the deformed configuration (flux, then its divergence, kernel
+ * gradients mapped by F), written through the Piola transform of the flux:
+ * Q_a = -D J_a C_a^-1 B0_a^T sum_b V (c_b - c_a) grad0_a W_ab with C = F^T F,
+ * then c_a -= dt sum_b V (Q_a + Q_b) . grad0_a W_ab (conservative pair form).
+ * mts_diffusion_dt then reports as the stable step 1.8 / a Gershgorin bound
+ * of that operator at the current deformation.  The reverse mode covers
+ * mode 0 only. */
+mts_status mts_set_diffusion_mode(mts_body *body, int32_t mode);
+/* Stop holding c on `count` particles (the end of a time-limited contact,
+ * Sec. 5.3-5.4 droplet schedule): their c keeps its value and evolves by
+ * diffusion from the next slow step on. */
+mts_status mts_release_bc_concentration(mts_body *body, int64_t count, const int64_t *ids);
 /* Particles whose mean displacement is reported as the tip deflection. */
 mts_status mts_set_tip(mts_body *body, int64_t count, const int64_t *ids);
 /* Diffusion step limits: dt_paper = 0.5 h^2 / D (Sec. 4.1) and the stable
@@ -313,6 +327,22 @@ mts_status mts_adjoint_seed(mts_body *body, const double *u_bar, const double *t
 mts_status mts_adjoint_slow_step(mts_body *body, const mts_step_params *params, int64_t substeps,
                                  double *theta_bar);
 mts_status mts_read_adjoint(mts_body *body, int32_t field, double *host_out, int64_t len);
+
+/* Equilibrium (implicit-function) adjoint of the state the body holds, for a
+ * slow step relaxed to equilibrium: with x* = G(x*, theta) the substep map's
+ * fixed point, lambda = s + A^T lambda (A = dG/dx at x*, s the seeds) is
+ * summed as a Neumann series by repeated transposed substeps linearised about
+ * x* (substep size: the one the next substep would take), and theta_bar
+ * receives sum_k B^T (A^T)^k s (B = dG/dtheta).  Only the mechanical
+ * relaxation is reversed: u-bar and v-bar decay, while c-bar and the plastic
+ * state's adjoint accumulate their sensitivities; the diffusion step before
+ * the relaxation is not included (D gets no contribution).  Stops when
+ * |(u-bar, v-bar)| <= tol |(u-bar, v-bar)| at the start (checked every 8
+ * iterations); *iters (may be NULL) = transposed substeps run.  Errors:
+ * MTS_ERR_TIMEOUT after max_iters without reaching tol, MTS_ERR_STATE (no
+ * material / reverse mode not enabled; enable with max_substeps >= 1). */
+mts_status mts_adjoint_equilibrium(mts_body *body, int64_t max_iters, double tol,
+                                   double *theta_bar, int64_t *iters);
 
 /* ------------------------------------------------------------------ */
 /* Allocation-free reduction                                            */

@@ -102,6 +102,8 @@ def lib():
         L.ob_set_bc_displacement.argtypes = [vp, i64, vp, C.c_uint, vp, C.c_int]
         L.ob_set_bc_concentration.argtypes = [vp, i64, vp, d]
         L.ob_set_tip.argtypes = [vp, i64, vp]
+        L.ob_release_bc_concentration.argtypes = [vp, i64, vp]
+        L.ob_set_diffusion_mode.argtypes = [vp, C.c_int]
         L.ob_stress_point.argtypes = [C.c_int, d, d, d, d, d, d, d, vp, vp, vp, vp, vp]
         L.ob_substep.argtypes = [vp, d, d, vp, vp, vp]
         L.ob_substep_partial.argtypes = [vp, d, d, C.c_int, vp]
@@ -232,6 +234,16 @@ class OracleBody:
         ids = np.ascontiguousarray(ids, dtype=np.int64)
         _check(lib().ob_set_bc_concentration(self._h, ids.size, _ptr(ids), value),
                "set_bc_concentration")
+
+    def set_diffusion_mode(self, mode: int):
+        """0: one-pass pairwise Laplacian; 1: two-stage flux in the deformed
+        configuration (Sec. 3.2)."""
+        _check(lib().ob_set_diffusion_mode(self._h, int(mode)), "set_diffusion_mode")
+
+    def release_bc_concentration(self, ids):
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        _check(lib().ob_release_bc_concentration(self._h, ids.size, _ptr(ids)),
+               "release_bc_concentration")
 
     def set_tip(self, ids):
         ids = np.ascontiguousarray(ids, dtype=np.int64)

@@ -118,6 +118,7 @@ typedef struct {
     double rho0, E, nu, K, mu, lambda, s0, sinf, delta, Hlin, eta;
     int has_diff;
     double D, beta, c0;
+    int diff_mode;           /* 0: one-pass pairwise Laplacian, 1: two-stage flux */
     /* state, sorted order */
     double *u, *v, *acc, *PB, *cpinv, *alpha, *c, *u_unit, *cheld_val;
     unsigned char *fix, *fgrp, *tgrp, *cheld;
@@ -699,6 +700,16 @@ int ob_set_bc_concentration(ob_body *b, int64_t count, const int64_t *ids, doubl
     return OB_OK;
 }
 
+/* end of a time-limited contact (Sec. 5.3-5.4): the particles keep their c
+ * and take part in the diffusion step again */
+int ob_release_bc_concentration(ob_body *b, int64_t count, const int64_t *ids) {
+    for (int64_t t = 0; t < count; t++) {
+        if (ids[t] < 0 || ids[t] >= b->n) return OB_ERR_ARG;
+        b->cheld[b->rank[ids[t]]] = 0;
+    }
+    return OB_OK;
+}
+
 int ob_set_tip(ob_body *b, int64_t count, const int64_t *ids) {
     memset(b->tgrp, 0, (size_t)b->n);
     for (int64_t t = 0; t < count; t++) {
@@ -972,9 +983,20 @@ int ob_substep_partial(ob_body *b, double dt, double ramp, int upto, double out[
 /* Slow process: diffusion (Sec. 2.2 Fick's law, Sec. 3.2, reduced to a */
 /* scalar concentration; explicit Jacobi update).                       */
 /* ------------------------------------------------------------------ */
+static void defgrad(const ob_body *b, int64_t a, double F[9]);
+static double two_stage_bound(const ob_body *b);
+
 int ob_diffusion_dt(const ob_body *b, double *dt_paper, double *dt_stable) {
     /* Sec. 4.1: dt_d = 0.5 h^2 / D.  Max-principle bound: 1/max_i sum_j a_ij
-     * with a_ij = 2 D V |W'_ij|/r_ij; the stable step is 0.9 of it. */
+     * with a_ij = 2 D V |W'_ij|/r_ij; the stable step is 0.9 of it.  For the
+     * two-stage form: 0.9 * 2 / (a Gershgorin bound of its operator at the
+     * current deformation). */
+    *dt_paper = b->D > 0 ? 0.5 * b->h * b->h / b->D : INFINITY;
+    if (b->diff_mode == 1) {
+        double lam = two_stage_bound(b);
+        *dt_stable = lam > 0 ? 1.8 / lam : INFINITY;
+        return OB_OK;
+    }
     double amax = 0.0;
     for (int64_t i = 0; i < b->n; i++) {
         double s = 0.0;
@@ -990,12 +1012,120 @@ int ob_diffusion_dt(const ob_body *b, double *dt_paper, double *dt_stable) {
         }
         if (s > amax) amax = s;
     }
-    *dt_paper = b->D > 0 ? 0.5 * b->h * b->h / b->D : INFINITY;
     *dt_stable = amax > 0 ? 0.9 / amax : INFINITY;
     return OB_OK;
 }
 
+/* Gershgorin bound of the two-stage operator c -> dc/dt: with s1_x =
+ * sum_b V |grad0 W_xb|_1 and R_x = 2 D J_x |C_x^-1 B0_x^T|_inf s1_x (a bound
+ * of the coefficient sum of each component of Q_x), every row of the
+ * operator has absolute sum <= sum_b V |grad0 W_ab|_1 (R_a + R_b). */
+static double two_stage_bound(const ob_body *b) {
+    int d = b->dim;
+    double *R = malloc((size_t)b->n * sizeof(double));
+    if (!R) return INFINITY;
+    for (int64_t a = 0; a < b->n; a++) {
+        double s1 = 0.0;
+        for (int64_t p = b->off[a]; p < b->off[a + 1]; p++) {
+            double w[3];
+            grad_w(b, a, b->nbr[p], w);
+            for (int k = 0; k < d; k++) s1 += b->V * fabs(w[k]);
+        }
+        double F[9], Ft[9], Cm[9], Ci[9];
+        defgrad(b, a, F);
+        m3_transpose(F, Ft);
+        m3_mul(Ft, F, Cm);
+        m3_inv(Cm, Ci);
+        double J = m3_det(F);
+        double nrm = 0.0;   /* |C^-1 B0^T|_inf over the d x d block */
+        for (int r = 0; r < d; r++) {
+            double row = 0.0;
+            for (int k = 0; k < d; k++) {
+                double m = 0.0;
+                for (int q = 0; q < d; q++) m += Ci[3 * r + q] * b->B0[9 * a + 3 * k + q];
+                row += fabs(m);
+            }
+            if (row > nrm) nrm = row;
+        }
+        R[a] = 2.0 * b->D * fabs(J) * nrm * s1;
+    }
+    double lam = 0.0;
+    for (int64_t a = 0; a < b->n; a++) {
+        double row = 0.0;
+        for (int64_t p = b->off[a]; p < b->off[a + 1]; p++) {
+            int64_t j = b->nbr[p];
+            double w[3], w1 = 0.0;
+            grad_w(b, a, j, w);
+            for (int k = 0; k < d; k++) w1 += fabs(w[k]);
+            row += b->V * w1 * (R[a] + R[j]);
+        }
+        if (row > lam) lam = row;
+    }
+    free(R);
+    return lam;
+}
+
+/* Two-stage diffusion in the deformed configuration (Sec. 3.2, flux then its
+ * divergence, kernel gradients mapped by F).  Written in the reference
+ * configuration through the Piola transform of the flux:
+ *   stage 1: g_a = B0_a^T sum_b V (c_b - c_a) grad0_a W_ab   (corrected reference gradient)
+ *            Q_a = -D J_a C_a^-1 g_a,  C = F^T F,  J = det F
+ *   stage 2: c_a <- c_a - dt sum_b V (Q_a + Q_b) . grad0_a W_ab   (free-c particles)
+ * The pair form of stage 2 is antisymmetric in a, b, so sum c is conserved
+ * when nothing is held. */
+static int diffusion_step_two_stage(ob_body *b, double dt) {
+    int d = b->dim;
+    double *Q = calloc((size_t)b->n * 3, sizeof(double));
+    double *cn = malloc((size_t)b->n * sizeof(double));
+    if (!Q || !cn) { free(Q); free(cn); return OB_ERR_OOM; }
+    for (int64_t a = 0; a < b->n; a++) {
+        double g[3] = {0, 0, 0};
+        for (int64_t p = b->off[a]; p < b->off[a + 1]; p++) {
+            int64_t j = b->nbr[p];
+            double w[3];
+            grad_w(b, a, j, w);
+            for (int k = 0; k < d; k++) g[k] += b->V * (b->c[j] - b->c[a]) * w[k];
+        }
+        double g0[3] = {0, 0, 0};            /* B0^T g */
+        for (int r = 0; r < d; r++)
+            for (int k = 0; k < d; k++) g0[r] += b->B0[9 * a + 3 * k + r] * g[k];
+        double F[9], Ft[9], Cm[9], Ci[9];
+        defgrad(b, a, F);
+        m3_transpose(F, Ft);
+        m3_mul(Ft, F, Cm);
+        m3_inv(Cm, Ci);
+        double J = m3_det(F);
+        for (int r = 0; r < d; r++) {
+            double s = 0.0;
+            for (int k = 0; k < d; k++) s += Ci[3 * r + k] * g0[k];
+            Q[3 * a + r] = -b->D * J * s;
+        }
+    }
+    for (int64_t a = 0; a < b->n; a++) {
+        if (b->cheld[a]) { cn[a] = b->cheld_val[a]; continue; }
+        double s = 0.0;
+        for (int64_t p = b->off[a]; p < b->off[a + 1]; p++) {
+            int64_t j = b->nbr[p];
+            double w[3];
+            grad_w(b, a, j, w);
+            for (int k = 0; k < d; k++) s += b->V * (Q[3 * a + k] + Q[3 * j + k]) * w[k];
+        }
+        cn[a] = b->c[a] - dt * s;
+    }
+    memcpy(b->c, cn, (size_t)b->n * sizeof(double));
+    free(Q);
+    free(cn);
+    return OB_OK;
+}
+
+int ob_set_diffusion_mode(ob_body *b, int mode) {
+    if (mode != 0 && mode != 1) return OB_ERR_ARG;
+    b->diff_mode = mode;
+    return OB_OK;
+}
+
 int ob_diffusion_step(ob_body *b, double dt) {
+    if (b->diff_mode == 1) return diffusion_step_two_stage(b, dt);
     double *cn = malloc((size_t)b->n * sizeof(double));
     if (!cn) return OB_ERR_OOM;
     for (int64_t i = 0; i < b->n; i++) {

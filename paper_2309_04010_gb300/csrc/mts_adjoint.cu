@@ -492,6 +492,40 @@ __global__ void k_adj_out(long long n, const long long *perm, int field, const d
     }
 }
 
+// sum of squares of the (u, v) adjoint: block partials, then one block in
+// block order
+template <int D>
+__global__ void k_adj_norm_part(const double *au, const double *av, long long n, double *part) {
+    constexpr int P = Pad<D>::v;
+    const long long i = blockIdx.x * (long long)kBlock + threadIdx.x;
+    double s = 0.0;
+    if (i < n)
+#pragma unroll
+        for (int q = 0; q < D; ++q) s += au[i * P + q] * au[i * P + q] + av[i * P + q] * av[i * P + q];
+    __shared__ double sh[kBlock / 32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < kBlock / 32; ++q) t += sh[q];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_adj_norm_final(const double *part, long long nb, double *out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long long q = threadIdx.x; q < nb; q += blockDim.x) s += part[q];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
 template <int D>
 size_t smem_adj_stress(const mts_body *b) {
     return 3 * second_off<double, Pad<D>::v>(b->max_halo);
@@ -616,6 +650,18 @@ mts_status adjoint_seed(mts_body *b, const double *ubar_orig_dev, const double t
     else
         k_adj_seed<3><<<grid_n(b->n), kBlock, 0, b->ctx->stream>>>(b->flags, b->perm, b->n,
                                                                    ubar_orig_dev, t0, t1, t2, b->adj_u);
+    MTS_CUDA(cudaGetLastError());
+    return MTS_OK;
+}
+
+// |(u-bar, v-bar)|^2 into out_dev[0]; part_dev holds one double per block of kBlock
+mts_status adjoint_norm2(mts_body *b, double *part_dev, double *out_dev) {
+    const unsigned g = grid_n(b->n);
+    if (b->dim == 2)
+        k_adj_norm_part<2><<<g, kBlock, 0, b->ctx->stream>>>(b->adj_u, b->adj_v, b->n, part_dev);
+    else
+        k_adj_norm_part<3><<<g, kBlock, 0, b->ctx->stream>>>(b->adj_u, b->adj_v, b->n, part_dev);
+    k_adj_norm_final<<<1, 256, 0, b->ctx->stream>>>(part_dev, g, out_dev);
     MTS_CUDA(cudaGetLastError());
     return MTS_OK;
 }

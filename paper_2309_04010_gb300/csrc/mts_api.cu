@@ -91,7 +91,7 @@ void body_free(mts_body *b) {
                      (void **)&b->halo_idx, (void **)&b->halo_x, (void **)&b->lself, (void **)&b->lell,
                      (void **)&b->lell_off, (void **)&b->tile_w, (void **)&b->pair_slot,
                      (void **)&b->kpad_ab, (void **)&b->kpad_g, (void **)&b->bperm,
-                     (void **)&b->bflags, (void **)&b->tape_u, (void **)&b->tape_cp,
+                     (void **)&b->bflags, (void **)&b->qflux, (void **)&b->tape_u, (void **)&b->tape_cp,
                      (void **)&b->tape_dt, (void **)&b->tape_c, (void **)&b->adj_u,
                      (void **)&b->adj_v, (void **)&b->adj_cp, (void **)&b->adj_c,
                      (void **)&b->adj_a, (void **)&b->adj_G, (void **)&b->adj_theta,
@@ -715,6 +715,24 @@ mts_status mts_set_bc_displacement(mts_body *b, int64_t count, const int64_t *id
     return upload_bc(b, uu);
 }
 
+mts_status mts_release_bc_concentration(mts_body *b, int64_t count, const int64_t *ids) {
+    if (!b || count < 0 || (count > 0 && !ids)) {
+        set_error("mts_release_bc_concentration: invalid arguments");
+        return MTS_ERR_INVALID_ARG;
+    }
+    std::vector<long long> rank;
+    MTS_TRY(get_rank_host(b, rank));
+    for (int64_t t = 0; t < count; ++t) {
+        if (ids[t] < 0 || ids[t] >= b->n) {
+            set_error("mts_release_bc_concentration: id %lld out of range", (long long)ids[t]);
+            return MTS_ERR_INVALID_ARG;
+        }
+        b->h_flags[rank[ids[t]]] &= (uint8_t)~kCHeldBit;
+    }
+    MTS_TRY(upload_bc(b, {}));
+    return MTS_OK;
+}
+
 mts_status mts_set_bc_concentration(mts_body *b, int64_t count, const int64_t *ids, double value) {
     if (!b || count < 0 || (count > 0 && !ids) || !std::isfinite(value)) {
         set_error("mts_set_bc_concentration: invalid arguments");
@@ -775,10 +793,30 @@ mts_status mts_diffusion_dt(mts_body *b, double *dt_paper, double *dt_stable) {
         set_error("mts_diffusion_dt: no diffusion set");
         return MTS_ERR_STATE;
     }
+    *dt_paper = b->D > 0 ? 0.5 * b->h * b->h / b->D : INFINITY;
+    if (b->diff_mode == 1) {
+        double lam = 0;
+        MTS_TRY(diffusion_bound_two_stage(b, &lam));
+        *dt_stable = lam > 0 ? 1.8 / lam : INFINITY;
+        return MTS_OK;
+    }
     double amax = 0;
     MTS_TRY(diffusion_bound(b, &amax));
-    *dt_paper = b->D > 0 ? 0.5 * b->h * b->h / b->D : INFINITY;
     *dt_stable = amax > 0 ? 0.9 / amax : INFINITY;
+    return MTS_OK;
+}
+
+mts_status mts_set_diffusion_mode(mts_body *b, int32_t mode) {
+    if (!b || (mode != 0 && mode != 1)) {
+        set_error("mts_set_diffusion_mode: mode must be 0 or 1");
+        return MTS_ERR_INVALID_ARG;
+    }
+    if (mode == 1 && !b->qflux) {
+        const size_t pad = b->dim == 2 ? 2 : 4;
+        MTS_TRY(dalloc_into(b->ctx, &b->qflux, (size_t)b->n * pad * b->rsize + 16));
+        MTS_CUDA(cudaMemsetAsync(b->qflux, 0, (size_t)b->n * pad * b->rsize, b->ctx->stream));
+    }
+    b->diff_mode = mode;
     return MTS_OK;
 }
 
@@ -1173,6 +1211,10 @@ mts_status mts_adjoint_slow_step(mts_body *b, const mts_step_params *p, int64_t 
                   (long long)substeps, (long long)b->adj_cap);
         return MTS_ERR_INVALID_ARG;
     }
+    if (p->dt_slow > 0 && b->diff_mode != 0) {
+        set_error("mts_adjoint_slow_step: the reverse mode covers the one-pass diffusion step only");
+        return MTS_ERR_STATE;
+    }
     cudaStream_t st = b->ctx->stream;
     // recompute the slow step from its start, taping every substep's input
     mts_step_params q = *p;
@@ -1229,3 +1271,58 @@ mts_status mts_read_adjoint(mts_body *b, int32_t field, double *out, int64_t len
 }
 
 }  // extern "C"
+
+extern "C" mts_status mts_adjoint_equilibrium(mts_body *b, int64_t max_iters, double tol,
+                                             double *theta_bar, int64_t *iters) {
+    MTS_TRY(adjoint_ready(b, "mts_adjoint_equilibrium"));
+    if (!theta_bar || max_iters < 1 || !(tol > 0.0) || !std::isfinite(tol)) {
+        set_error("mts_adjoint_equilibrium: NULL theta_bar, max_iters < 1 or tol not > 0");
+        return MTS_ERR_INVALID_ARG;
+    }
+    if (!b->has_material) {
+        set_error("mts_adjoint_equilibrium: no material set");
+        return MTS_ERR_STATE;
+    }
+    cudaStream_t st = b->ctx->stream;
+    // the held state, with the size the next substep would take, is the one
+    // taped entry every transposed substep linearises about
+    MTS_TRY(adjoint_tape(b, 0));
+    // norm scratch: one double per block of the drift grid (part_drift holds two)
+    double *part = b->part_drift, *nrm = b->scratch;
+    double h[2];
+    MTS_TRY(adjoint_norm2(b, part, nrm));
+    MTS_CUDA(cudaMemcpyAsync(h, nrm, 8, cudaMemcpyDeviceToHost, st));
+    MTS_CUDA(cudaStreamSynchronize(st));
+    const double n0 = h[0];
+    int64_t it = 0;
+    bool done = n0 == 0.0 && b->adj_force_seed[0] == 0.0 && b->adj_force_seed[1] == 0.0 &&
+                b->adj_force_seed[2] == 0.0;
+    while (!done && it < max_iters) {
+        MTS_TRY(adjoint_substep(b, 0, it == 0));
+        ++it;
+        if (it % 8 == 0 || it == max_iters) {
+            MTS_TRY(adjoint_norm2(b, part, nrm));
+            MTS_CUDA(cudaMemcpyAsync(h, nrm, 8, cudaMemcpyDeviceToHost, st));
+            MTS_CUDA(cudaStreamSynchronize(st));
+            if (!std::isfinite(h[0])) {
+                set_error("mts_adjoint_equilibrium: non-finite adjoint after %lld iterations",
+                          (long long)it);
+                return MTS_ERR_NONFINITE;
+            }
+            done = h[0] <= tol * tol * (n0 > 0.0 ? n0 : h[0]);
+        }
+    }
+    double th[8];
+    MTS_CUDA(cudaMemcpyAsync(th, b->adj_theta, sizeof(th), cudaMemcpyDeviceToHost, st));
+    MTS_CUDA(cudaMemsetAsync(b->adj_theta, 0, sizeof(th), st));
+    MTS_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < 7; ++k) theta_bar[k] += th[k];
+    for (int k = 0; k < 3; ++k) b->adj_force_seed[k] = 0.0;
+    if (iters) *iters = it;
+    if (!done) {
+        set_error("mts_adjoint_equilibrium: adjoint not below tol after %lld iterations",
+                  (long long)it);
+        return MTS_ERR_TIMEOUT;
+    }
+    return MTS_OK;
+}

@@ -98,6 +98,8 @@ struct Args {
     R swell;       // 3 K beta
     R c0;
     R dcoef;       // 2 D * kcoef (diffusion, includes V)
+    R diffD;       // D (two-stage diffusion)
+    R *qflux;      // two-stage diffusion: Piola-mapped flux per particle (PAD)
     int swelling;
     double mass, h, cs;
     // damping
@@ -218,6 +220,8 @@ struct mts_body {
     double rho0, E, nu, K, mu, lambda, s0, sinf, delta, Hlin, eta;
     bool has_diff;
     double D, beta, c0;
+    int diff_mode;            // 0: one-pass Laplacian, 1: two-stage flux (deformed configuration)
+    void *qflux;              // n x PAD, allocated with diff_mode 1
 
     // loop machinery
     mts::Control *ctrl;
@@ -285,6 +289,7 @@ mts_status adjoint_diffusion(mts_body *b, double dt);
 mts_status adjoint_load(mts_body *b);
 mts_status adjoint_seed(mts_body *b, const double *ubar_orig_dev, const double tip[3]);
 mts_status adjoint_out(mts_body *b, int field, double *out_dev);
+mts_status adjoint_norm2(mts_body *b, double *part_dev, double *out_dev);
 mts_status launch_drift(mts_body *b);
 mts_status prepare_kernels(mts_body *b);
 // shared memory of the CTA-per-group damping kernel for this body's layout
@@ -293,6 +298,8 @@ mts_status update_pair_fixbits(mts_body *b);
 mts_status launch_slow_begin(mts_body *b);
 mts_status launch_diffusion(mts_body *b, double dt);
 mts_status diffusion_bound(mts_body *b, double *amax_sum);
+// Gershgorin bound of the two-stage diffusion operator at the current deformation
+mts_status diffusion_bound_two_stage(mts_body *b, double *lambda);
 mts_status launch_defgrad(mts_body *b, double *out_sorted);
 mts_status launch_tip(mts_body *b, double *out3);
 mts_status launch_reset_ctrl(mts_body *b, double dt, double dt_fixed, double ramp,

@@ -824,6 +824,233 @@ __global__ void __launch_bounds__(256) k_diffuse(Args<R> A, R dt) {
     A.c_tmp[i] = ca + dt * A.dcoef * s;
 }
 
+// Two-stage diffusion in the deformed configuration (Sec. 3.2: flux, then its
+// divergence, kernel gradients mapped by F), written in the reference
+// configuration through the Piola transform of the flux:
+//   stage 1  Q_a = -D J_a C_a^-1 B0_a^T sum_b V (c_b - c_a) grad0_a W_ab,  C = F^T F
+//   stage 2  c_a <- c_a - dt sum_b V (Q_a + Q_b) . grad0_a W_ab   (free-c particles)
+// Stage 1 stages X, u and c of the tile's halo (F as in the stress kernel).
+template <class R, int D>
+__device__ __forceinline__ void inv_cauchy_green(const R (&F)[3][3], R (&Ci)[3][3], R &J) {
+    R Cm[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Cm[i][j] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
+    R cof[3][3];
+    m3_cof(Cm, cof);                       // symmetric: cof = det(C) C^-1
+    const R idet = R(1) / m3_det(Cm);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Ci[i][j] = cof[i][j] * idet;
+    J = m3_det(F);
+}
+
+template <class R, int D>
+__global__ void __launch_bounds__(256) k_diff_flux(Args<R> A) {
+    constexpr int P = Pad<D>::v;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const size_t o1 = second_off<R, P>(A.max_halo);
+    R *sX = reinterpret_cast<R *>(smem);
+    R *sU = reinterpret_cast<R *>(smem + o1);
+    R *sC = reinterpret_cast<R *>(smem + 2 * o1);
+    stage_halo<R, P, P>(A, sX, sU, A.uf);
+    const long long t = blockIdx.x;
+    const long long h0 = A.halo_off[t];
+    const int nh = (int)(A.halo_off[t + 1] - h0);
+    for (int k = threadIdx.x; k < nh; k += blockDim.x) sC[k] = A.c[__ldg(A.halo_idx + h0 + k)];
+    __syncthreads();
+    const long long i = t * A.T + threadIdx.x;
+    if (i >= A.n) return;
+    R F[3][3];
+    compute_F<R, D>(A, sX, sU, i, F);
+    const int li = A.lself[i];
+    R xa[P];
+    ld_vec<R, P>(xa, sX + li * P);
+    const R ca = sC[li];
+    R g[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) g[k] = R(0);
+    const uint16_t *row = A.lell + A.lell_off[t] + threadIdx.x;
+    for_each_neighbour(row, A.T, A.tile_w[t], [&](int l) {
+        R xb[P];
+        ld_vec<R, P>(xb, sX + l * P);
+        R d[D], r2 = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            d[k] = xa[k] - xb[k];
+            r2 += d[k] * d[k];
+        }
+        const R tt = R(1) - R(0.5) * nsqrt(r2) * A.inv_h;
+        const R f = A.kcoef * tt * tt * tt * (sC[l] - ca);   // V W'/r (c_b - c_a)
+#pragma unroll
+        for (int k = 0; k < D; ++k) g[k] += f * d[k];
+    });
+    R B[D][D];
+    ldg_mat<R, D>(B, A.B0 + i * MatS<D>::v);
+    R g0[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        R s = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) s += B[k][r] * g[k];
+        g0[r] = s;
+    }
+    R Ci[3][3], J;
+    inv_cauchy_green<R, D>(F, Ci, J);
+    R q[P];
+#pragma unroll
+    for (int r = 0; r < P; ++r) {
+        R s = R(0);
+        if (r < D)
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += Ci[r][k] * g0[k];
+        q[r] = r < D ? -A.diffD * J * s : R(0);
+    }
+    st_vec<R, P>(A.qflux + i * P, q);
+}
+
+template <class R, int D>
+__global__ void __launch_bounds__(256) k_diff_div(Args<R> A, R dt) {
+    constexpr int P = Pad<D>::v;
+    extern __shared__ __align__(16) unsigned char smem[];
+    R *sX = reinterpret_cast<R *>(smem);
+    R *sQ = reinterpret_cast<R *>(smem + second_off<R, P>(A.max_halo));
+    stage_halo<R, P, P>(A, sX, sQ, A.qflux);
+    const long long t = blockIdx.x;
+    const long long i = t * A.T + threadIdx.x;
+    if (i >= A.n) return;
+    if (A.flags[i] & kCHeldBit) {
+        A.c_tmp[i] = A.c_held[i];
+        return;
+    }
+    const int li = A.lself[i];
+    R xa[P], qa[P];
+    ld_vec<R, P>(xa, sX + li * P);
+    ld_vec<R, P>(qa, sQ + li * P);
+    R s = R(0);
+    const uint16_t *row = A.lell + A.lell_off[t] + threadIdx.x;
+    for_each_neighbour(row, A.T, A.tile_w[t], [&](int l) {
+        R xb[P], qb[P];
+        ld_vec<R, P>(xb, sX + l * P);
+        ld_vec<R, P>(qb, sQ + l * P);
+        R d[D], r2 = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            d[k] = xa[k] - xb[k];
+            r2 += d[k] * d[k];
+        }
+        const R tt = R(1) - R(0.5) * nsqrt(r2) * A.inv_h;
+        const R f = A.kcoef * tt * tt * tt;
+        R dot = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) dot += (qa[k] + qb[k]) * d[k];
+        s += f * dot;
+    });
+    A.c_tmp[i] = A.c[i] - dt * s;
+}
+
+// Gershgorin bound of the two-stage operator (see the oracle): R_x =
+// 2 D |J_x| |C_x^-1 B0_x^T|_inf s1_x with s1_x = sum_b V |grad0 W_xb|_1, then
+// max over rows of sum_b V |grad0 W_ab|_1 (R_a + R_b)
+template <class R, int D>
+__global__ void __launch_bounds__(256) k_ts_rowcoef(Args<R> A, double *Rx) {
+    constexpr int P = Pad<D>::v;
+    extern __shared__ __align__(16) unsigned char smem[];
+    R *sX = reinterpret_cast<R *>(smem);
+    R *sU = reinterpret_cast<R *>(smem + second_off<R, P>(A.max_halo));
+    stage_halo<R, P, P>(A, sX, sU, A.uf);
+    const long long t = blockIdx.x;
+    const long long i = t * A.T + threadIdx.x;
+    if (i >= A.n) return;
+    R F[3][3];
+    compute_F<R, D>(A, sX, sU, i, F);
+    const int li = A.lself[i];
+    R xa[P];
+    ld_vec<R, P>(xa, sX + li * P);
+    double s1 = 0.0;
+    const uint16_t *row = A.lell + A.lell_off[t] + threadIdx.x;
+    for_each_neighbour(row, A.T, A.tile_w[t], [&](int l) {
+        R xb[P];
+        ld_vec<R, P>(xb, sX + l * P);
+        R d[D], r2 = R(0), n1 = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            d[k] = xa[k] - xb[k];
+            r2 += d[k] * d[k];
+            n1 += d[k] < R(0) ? -d[k] : d[k];
+        }
+        const R tt = R(1) - R(0.5) * nsqrt(r2) * A.inv_h;
+        const R f = A.kcoef * tt * tt * tt;
+        s1 += (double)(f < R(0) ? -f : f) * (double)n1;
+    });
+    R B[D][D];
+    ldg_mat<R, D>(B, A.B0 + i * MatS<D>::v);
+    R Ci[3][3], J;
+    inv_cauchy_green<R, D>(F, Ci, J);
+    double nrm = 0.0;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        double rs = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            double m = 0.0;
+#pragma unroll
+            for (int q = 0; q < D; ++q) m += (double)Ci[r][q] * (double)B[k][q];
+            rs += fabs(m);
+        }
+        nrm = fmax(nrm, rs);
+    }
+    Rx[i] = 2.0 * (double)A.diffD * fabs((double)J) * nrm * s1;
+}
+
+template <class R, int D>
+__global__ void __launch_bounds__(256) k_ts_bound(Args<R> A, const double *Rx, double *part) {
+    constexpr int P = Pad<D>::v;
+    extern __shared__ __align__(16) unsigned char smem[];
+    R *sX = reinterpret_cast<R *>(smem);
+    double *sR = reinterpret_cast<double *>(smem + second_off<R, P>(A.max_halo));
+    stage_halo<R, P, P>(A, sX, nullptr, (const R *)nullptr);
+    const long long t = blockIdx.x;
+    const long long h0 = A.halo_off[t];
+    const int nh = (int)(A.halo_off[t + 1] - h0);
+    for (int k = threadIdx.x; k < nh; k += blockDim.x) sR[k] = Rx[__ldg(A.halo_idx + h0 + k)];
+    __syncthreads();
+    const long long i = t * A.T + threadIdx.x;
+    double rowsum = 0.0;
+    if (i < A.n) {
+        const int li = A.lself[i];
+        R xa[P];
+        ld_vec<R, P>(xa, sX + li * P);
+        const double ra = sR[li];
+        const uint16_t *row = A.lell + A.lell_off[t] + threadIdx.x;
+        for_each_neighbour(row, A.T, A.tile_w[t], [&](int l) {
+            R xb[P];
+            ld_vec<R, P>(xb, sX + l * P);
+            R d[D], r2 = R(0), n1 = R(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                d[k] = xa[k] - xb[k];
+                r2 += d[k] * d[k];
+                n1 += d[k] < R(0) ? -d[k] : d[k];
+            }
+            const R tt = R(1) - R(0.5) * nsqrt(r2) * A.inv_h;
+            const R f = A.kcoef * tt * tt * tt;
+            rowsum += (double)(f < R(0) ? -f : f) * (double)n1 * (ra + sR[l]);
+        });
+    }
+    rowsum = warp_max(rowsum);
+    __shared__ double sh[8];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = rowsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m = fmax(m, sh[q]);
+        part[blockIdx.x] = m;
+    }
+}
+
 template <class R>
 __global__ void k_copy(const R *src, R *dst, long long n) {
     const long long i = blockIdx.x * (long long)kBlock + threadIdx.x;
@@ -1016,6 +1243,8 @@ Args<R> make_args(mts_body *b) {
     A.swell = (R)(3.0 * b->K * b->beta);
     A.c0 = (R)b->c0;
     A.dcoef = (R)(2.0 * b->D * b->V * (-5.0 * alpha / (b->h * b->h)));
+    A.diffD = (R)b->D;
+    A.qflux = (R *)b->qflux;
     A.mass = b->rho0 * b->V;
     A.h = b->h;
     A.cs = std::sqrt(b->K / b->rho0);
@@ -1167,6 +1396,12 @@ mts_status prepare_t(mts_body *b) {
     MTS_TRY(attr((const void *)k_defgrad<R, D>, sa, "deformation gradient"));
     MTS_TRY(attr((const void *)k_force<R, D>, smem_force<R, D>(b), "force"));
     MTS_TRY(attr((const void *)k_diffuse<R, D>, smem_diffuse<R, D>(b), "diffusion"));
+    const size_t sh2 = 2 * second_off<R, Pad<D>::v>(b->max_halo);
+    MTS_TRY(attr((const void *)k_diff_flux<R, D>, 3 * second_off<R, Pad<D>::v>(b->max_halo), "diffusion flux"));
+    MTS_TRY(attr((const void *)k_diff_div<R, D>, sh2, "diffusion divergence"));
+    MTS_TRY(attr((const void *)k_ts_rowcoef<R, D>, sh2, "diffusion bound"));
+    MTS_TRY(attr((const void *)k_ts_bound<R, D>,
+                 second_off<R, Pad<D>::v>(b->max_halo) + (size_t)b->max_halo * 8, "diffusion bound"));
     return MTS_OK;
 }
 
@@ -1191,9 +1426,36 @@ template <class R, int D>
 mts_status diffuse_t(mts_body *b, double dt) {
     Args<R> A = make_args<R>(b);
     MTS_TRY((prepare_t<R, D>(b)));
-    k_diffuse<R, D><<<(unsigned)b->ntiles, b->T, smem_diffuse<R, D>(b), b->ctx->stream>>>(A, (R)dt);
+    if (b->diff_mode == 1) {
+        const size_t s1 = 3 * second_off<R, Pad<D>::v>(b->max_halo);
+        const size_t s2 = 2 * second_off<R, Pad<D>::v>(b->max_halo);
+        k_diff_flux<R, D><<<(unsigned)b->ntiles, b->T, s1, b->ctx->stream>>>(A);
+        k_diff_div<R, D><<<(unsigned)b->ntiles, b->T, s2, b->ctx->stream>>>(A, (R)dt);
+    } else {
+        k_diffuse<R, D><<<(unsigned)b->ntiles, b->T, smem_diffuse<R, D>(b), b->ctx->stream>>>(A, (R)dt);
+    }
     k_copy<R><<<grid_of(b->n), kBlock, 0, b->ctx->stream>>>((const R *)b->c_tmp, (R *)b->c, b->n);
     MTS_CUDA(cudaGetLastError());
+    return MTS_OK;
+}
+
+template <class R, int D>
+mts_status ts_bound_t(mts_body *b, double *lambda) {
+    MTS_TRY((prepare_t<R, D>(b)));
+    Args<R> A = make_args<R>(b);
+    double *Rx = b->scratch, *part = b->scratch + b->n;
+    const size_t s2 = 2 * second_off<R, Pad<D>::v>(b->max_halo);
+    const size_t s3 = second_off<R, Pad<D>::v>(b->max_halo) + (size_t)b->max_halo * 8;
+    k_ts_rowcoef<R, D><<<(unsigned)b->ntiles, b->T, s2, b->ctx->stream>>>(A, Rx);
+    k_ts_bound<R, D><<<(unsigned)b->ntiles, b->T, s3, b->ctx->stream>>>(A, Rx, part);
+    MTS_CUDA(cudaGetLastError());
+    std::vector<double> h(b->ntiles);
+    MTS_CUDA(cudaMemcpyAsync(h.data(), part, b->ntiles * sizeof(double), cudaMemcpyDeviceToHost,
+                             b->ctx->stream));
+    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    double m = 0;
+    for (double x : h) m = std::max(m, x);
+    *lambda = m;
     return MTS_OK;
 }
 
@@ -1270,6 +1532,7 @@ mts_status update_pair_fixbits(mts_body *b) {
 }
 mts_status launch_slow_begin(mts_body *b) { return DISPATCH(load_t, b); }
 mts_status launch_diffusion(mts_body *b, double dt) { return DISPATCH(diffuse_t, b, dt); }
+mts_status diffusion_bound_two_stage(mts_body *b, double *lambda) { return DISPATCH(ts_bound_t, b, lambda); }
 mts_status launch_defgrad(mts_body *b, double *out_sorted) { return DISPATCH(defgrad_t, b, out_sorted); }
 mts_status field_to_scratch(mts_body *b, int field) { return DISPATCH(field_out_t, b, field); }
 mts_status scratch_to_field(mts_body *b, int field) { return DISPATCH(field_in_t, b, field); }

@@ -107,12 +107,15 @@ def lib():
         "mts_body_permutation": [vp, vp],
         "mts_body_damping_layout": [vp, vp, C.POINTER(i32)],
         "mts_save_state": [vp, vp, C.POINTER(C.c_size_t)],
+        "mts_release_bc_concentration": [vp, i64, vp],
+        "mts_set_diffusion_mode": [vp, i32],
         "mts_batch_create": [vp, i32, vp, C.POINTER(vp)],
         "mts_adjoint_enable": [vp, i64],
         "mts_adjoint_reset": [vp],
         "mts_adjoint_seed": [vp, vp, vp, vp],
         "mts_adjoint_slow_step": [vp, C.POINTER(StepParams), i64, vp],
         "mts_read_adjoint": [vp, i32, vp, i64],
+        "mts_adjoint_equilibrium": [vp, i64, d, vp, C.POINTER(i64)],
         "mts_batch_advance": [vp, vp, vp],
         "mts_batch_destroy": [vp],
         "mts_load_state": [vp, vp, C.c_size_t],
@@ -340,6 +343,15 @@ class Body:
                "mts_adjoint_slow_step")
         return th
 
+    def adjoint_equilibrium(self, max_iters: int = 100000, tol: float = 1e-10):
+        """Equilibrium adjoint of the held (converged) state; returns
+        (d objective / d theta, transposed substeps run)."""
+        th = np.zeros(7)
+        it = C.c_int64()
+        _check(lib().mts_adjoint_equilibrium(self._h, int(max_iters), float(tol), _ptr(th),
+                                             C.byref(it)), "mts_adjoint_equilibrium")
+        return th, int(it.value)
+
     def read_adjoint(self, field: int) -> np.ndarray:
         w = self._width(field)
         out = np.zeros(self.n * w)
@@ -357,6 +369,16 @@ class Body:
         ids = np.ascontiguousarray(ids, dtype=np.int64)
         _check(lib().mts_set_bc_concentration(self._h, ids.size, _ptr(ids), value),
                "mts_set_bc_concentration")
+
+    def set_diffusion_mode(self, mode: int):
+        """0: one-pass pairwise Laplacian; 1: two-stage flux in the deformed
+        configuration (Sec. 3.2)."""
+        _check(lib().mts_set_diffusion_mode(self._h, int(mode)), "mts_set_diffusion_mode")
+
+    def release_bc_concentration(self, ids):
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        _check(lib().mts_release_bc_concentration(self._h, ids.size, _ptr(ids)),
+               "mts_release_bc_concentration")
 
     def set_tip(self, ids):
         ids = np.ascontiguousarray(ids, dtype=np.int64)

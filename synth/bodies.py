@@ -103,6 +103,8 @@ class Case:
     lattice_index: Optional[np.ndarray] = None               # (n, dim) int64
     counts: Optional[Tuple[int, ...]] = None
     h_over_dx: float = H_OVER_DX
+    # time-limited contact: (time after which the set is released, its ids)
+    release: Optional[Tuple[float, np.ndarray]] = None
 
     @property
     def n(self) -> int:
@@ -297,6 +299,65 @@ def batch_instances(count: int = 64, n_min: int = 5_000, n_max: int = 200_000,
         cases.append(c)
     return cases
 
+
+
+# --------------------------------------------------------------------------
+# Droplet-contact schedules (Sec. 5.3 2D beam, Sec. 5.4 3D membrane): a porous
+# body clamped at its ends / sides; the centre part of its upper half is held
+# at the saturation of the droplet contact (0.4 = the porosity) for a limited
+# time, then released; elsewhere c starts at 0; no flux leaves the body.
+# --------------------------------------------------------------------------
+def _droplet_case(name, counts, dx, seed, E, nu, rho0, eta, D, beta, c_held, t_contact,
+                  t_end, ke_tol, jitter, clamp_axes) -> Case:
+    dim = len(counts)
+    X, idx, _ = box_body(counts, dx, seed, jitter)
+    clamp = np.unique(np.concatenate(
+        [layer_ids(idx, a, 0, 3) for a in clamp_axes] +
+        [layer_ids(idx, a, counts[a] - 3, 3) for a in clamp_axes]))
+    bcs = [DispBC(clamp, (1 << dim) - 1, np.zeros((clamp.size, dim)))]
+    thick = dim - 1
+    sel = idx[:, thick] >= counts[thick] // 2                  # upper half
+    for a in range(dim - 1):                                   # centre 0.3 of each long side
+        lo = int(round(0.35 * counts[a]))
+        hi = int(round(0.65 * counts[a]))
+        sel &= (idx[:, a] >= lo) & (idx[:, a] < hi)
+    contact = np.nonzero(sel)[0].astype(np.int64)
+    K = E / (3.0 * (1.0 - 2.0 * nu))
+    plan = StepPlan(n_slow=0, n_ramp=0, dt_slow=None, ke_tol=ke_tol, ke_ref=3.0 * K * beta,
+                    ke_mode=1, max_substeps=1_000_000, t_end=t_end)
+    mid = [counts[a] // 2 for a in range(dim - 1)]
+    centre = np.nonzero(np.all(idx[:, :dim - 1] == mid, axis=1))[0].astype(np.int64)
+    return Case(name, dim, X, dx, Material("svk", rho0, E, nu), eta, bcs,
+                [ConcBC(contact, c_held)], centre, plan, (D, beta, 0.0), idx, tuple(counts),
+                release=(t_contact, contact))
+
+
+def beam_droplet2d(L: float = 10e-3, W: float = 0.125e-3, ny: int = 8,
+                   seed: int = SEED_BASE + 6, E: float = 200e6, nu: float = 0.4,
+                   rho0: float = 2000.0, eta: float = 1e4, D: float = 1e-10, beta: float = 0.1,
+                   c_held: float = 0.4, t_contact: float = 10.0, t_end: float = 100.0,
+                   ke_tol: float = 5e-4, jitter: float = JITTER) -> Case:
+    """Sec. 5.3: a 10 x 0.125 mm beam, both ends clamped, contact on the centre
+    0.3 L of the upper half for 10 s of 100 s (isotropic spacing W/ny)."""
+    dx = W / ny
+    nx = int(round(L / dx))
+    return _droplet_case("beam_droplet2d", (nx, ny), dx, seed, E, nu, rho0, eta, D, beta,
+                         c_held, t_contact, t_end, ke_tol, jitter, clamp_axes=(0,))
+
+
+def membrane_droplet3d(Lx: float = 10e-3, Ly: float = 10e-3, Lz: float = 0.125e-3, nz: int = 8,
+                       seed: int = SEED_BASE + 7, E: float = 200e6, nu: float = 0.4,
+                       rho0: float = 2000.0, eta: float = 1e4, D: float = 1e-10,
+                       beta: float = 0.1, c_held: float = 0.4, t_contact: float = 450.0,
+                       t_end: float = 2500.0, ke_tol: float = 1e-3,
+                       jitter: float = JITTER) -> Case:
+    """Sec. 5.4: a 10 x 10 x 0.125 mm membrane, four sides clamped, contact on
+    the centre 0.3 Lx x 0.3 Ly of the upper half for 450 s of 2500 s
+    (isotropic spacing Lz/nz)."""
+    dx = Lz / nz
+    nx, ny = int(round(Lx / dx)), int(round(Ly / dx))
+    return _droplet_case("membrane_droplet3d", (nx, ny, nz), dx, seed, E, nu, rho0, eta, D,
+                         beta, c_held, t_contact, t_end, ke_tol, jitter, clamp_axes=(0, 1))
 
 def workload(number: int, **kw) -> Case:
     """The five benchmark workloads by number (1..4; 5 is batch_instances)."""

@@ -217,3 +217,34 @@ def test_adjoint_errors(ctx):
     with pytest.raises(M.MtsError) as e:
         gb.adjoint_slow_step(5, ramp=0.1)
     assert e.value.status == M.ERR_INVALID_ARG
+
+
+def test_equilibrium_adjoint_matches_differences_of_equilibria(ctx):
+    """Implicit-function adjoint at a relaxed equilibrium (SVK bar) against
+    central differences of equilibria relaxed to machine precision."""
+    case = B.bar2d(nx=24, ny=6, n_slow=4, eta=1e3)   # relaxes in ~1e4 substeps (1e4: overdamped)
+    w_tip, w_f, r = _weights(case, seed=8)
+    p = dict(ramp=1.0 / case.plan.n_ramp, ke_tol=1e-26, ke_ref=case.plan.ke_ref,
+             max_substeps=60000)
+
+    def objective(theta):
+        gb = M.body_from_case(ctx, case, M.FP64)
+        gb.set_parameters(theta)
+        rep = gb.advance_slow_step(**p)
+        d = case.dim
+        val = (w_tip @ np.array(rep.tip_deflection[:d]) + w_f @ np.array(rep.end_force[:d]) +
+               float((r * gb.read(M.F_U)).sum()))
+        return val, gb
+
+    J0, gb = objective(M.body_from_case(ctx, case, M.FP64).parameters())
+    gb.adjoint_enable(1)
+    gb.adjoint_seed(u_bar=r, tip_bar=w_tip, force_bar=w_f)
+    th, iters = gb.adjoint_equilibrium(max_iters=100000, tol=1e-10)
+    assert iters > 10
+    theta0 = gb.parameters()
+    h = 1e-5 * theta0[0]
+    tp, tm = theta0.copy(), theta0.copy()
+    tp[0] += h
+    tm[0] -= h
+    fd = (objective(tp)[0] - objective(tm)[0]) / (2 * h)
+    assert abs(th[0] - fd) <= 1e-5 * abs(fd), (th[0], fd)

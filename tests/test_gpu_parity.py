@@ -381,3 +381,48 @@ def test_full_size_plate_properties(precision, tol):
     assert np.max(np.abs(F - (np.eye(3) + G))) < tol
     gb.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("which", ["beam", "membrane"])
+@pytest.mark.parametrize("precision,tol_u,tol_c", [(M.FP64, 1e-9, 1e-12), (M.MIXED, 1e-4, 1e-5)])
+def test_droplet_contact_schedule(ctx, which, precision, tol_u, tol_c):
+    """Sec. 5.3 / 5.4 schedules (small bodies): held contact for two slow
+    steps, released, two more; GPU against the oracle."""
+    case = (B.beam_droplet2d(L=2e-3) if which == "beam"
+            else B.membrane_droplet3d(Lx=0.6e-3, Ly=0.6e-3))
+    ob, gb = pair(ctx, case, precision)
+    dts = ob.diffusion_dt()[1]
+    for step in range(4):
+        if step == 2:
+            ob.release_bc_concentration(case.release[1])
+            gb.release_bc_concentration(case.release[1])
+        kw = dict(dt_slow=dts, ke_tol=-1.0, ke_ref=case.plan.ke_ref, ke_mode=1, max_substeps=30)
+        rg = gb.advance_slow_step(**kw)
+        ro = ob.advance(**kw)
+        assert rg.substeps == ro.substeps == 30
+    assert rel(gb.read(M.F_C), ob.read(O.F_C)) < tol_c
+    assert rel(gb.read(M.F_U), ob.read(O.F_U)) < tol_u
+    assert np.max(np.abs(ob.read(O.F_U))) > 0
+
+
+@pytest.mark.parametrize("which", ["strip", "plate"])
+@pytest.mark.parametrize("precision,tol_u,tol_c", [(M.FP64, 1e-9, 1e-12), (M.MIXED, 1e-4, 1e-5)])
+def test_two_stage_diffusion(ctx, which, precision, tol_u, tol_c):
+    """Diffusion mode 1 (two-stage flux in the deformed configuration):
+    stable-step bound and three slow steps (diffusion + 20 substeps) against
+    the oracle; the body bends, so F enters the flux."""
+    case = small_strip() if which == "strip" else B.plate3d(nx=24, ny=10, nz=8)
+    ob, gb = pair(ctx, case, precision)
+    ob.set_diffusion_mode(1)
+    gb.set_diffusion_mode(1)
+    for step in range(3):
+        dto = ob.diffusion_dt()
+        dtg = gb.diffusion_dt()
+        assert abs(dtg[1] - dto[1]) <= (1e-12 if precision == M.FP64 else 1e-5) * dto[1]
+        kw = dict(dt_slow=dto[1], ke_tol=-1.0, ke_ref=case.plan.ke_ref, ke_mode=1, max_substeps=20,
+                  force_dt=True)
+        gb.advance_slow_step(**kw)
+        ob.advance(**kw)
+    assert rel(gb.read(M.F_C), ob.read(O.F_C)) < tol_c
+    assert rel(gb.read(M.F_U), ob.read(O.F_U)) < tol_u
+    assert np.max(np.abs(ob.read(O.F_U))) > 0

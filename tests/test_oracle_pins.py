@@ -752,3 +752,108 @@ def test_end_force_equals_stress_times_area():
     area = counts[1] * dx
     assert abs(r.end_force[0] - Ep * eps * area) < 0.03 * Ep * eps * area
     assert abs(r.end_force[1]) < 0.03 * Ep * eps * area
+
+
+# ----------------------------------------------------------------------------
+# P17: time-limited contact (Sec. 5.3-5.4 droplet schedule): released particles
+# rejoin the diffusion, and with nothing held the step conserves sum V c
+# ----------------------------------------------------------------------------
+def test_released_contact_rejoins_diffusion_and_conserves_mass():
+    c = B.beam_droplet2d(L=1e-3, W=0.125e-3, ny=8)
+    ob = O.body_from_case(c)
+    dts = ob.diffusion_dt()[1]
+    for _ in range(3):
+        ob.diffusion_step(dts)
+    cc = ob.read(O.F_C)
+    held = c.release[1]
+    assert np.all(cc[held] == 0.4) and cc.sum() > 0.4 * held.size
+    ob.release_bc_concentration(held)
+    m0 = cc.sum()
+    for _ in range(5):
+        ob.diffusion_step(dts)
+    c2 = ob.read(O.F_C)
+    assert abs(c2.sum() - m0) <= 1e-12 * m0            # no held particles left: conservative
+    assert np.max(c2[held]) < 0.4                     # the released set drains
+    assert c2.min() >= 0.0 and c2.max() <= 0.4        # max principle
+
+
+# ----------------------------------------------------------------------------
+# P18: two-stage diffusion in the deformed configuration (Sec. 3.2 form, mode 1)
+# ----------------------------------------------------------------------------
+def _two_stage_body(nx=36, ny=36, D=1e-10, dx=1e-5):
+    X, idx, _ = B.box_body((nx, ny), dx, seed=5, jitter=0.0)
+    ob = O.OracleBody(X, dx)
+    ob.set_material(O.SVK, 2000.0, 200e6, 0.4)
+    ob.set_diffusion(D, 0.0, 0.0)
+    ob.set_diffusion_mode(1)
+    deep = np.all((idx >= 6) & (idx < np.array([nx, ny]) - 6), axis=1)
+    return ob, X, idx, deep
+
+
+def test_two_stage_linear_profile_is_steady_in_the_interior():
+    ob, X, idx, deep = _two_stage_body()
+    c0 = 0.3 + 0.7 * X[:, 0] / X[:, 0].max()
+    ob.write(O.F_C, c0)
+    ob.diffusion_step(1e-3)
+    c1 = ob.read(O.F_C)
+    assert np.max(np.abs(c1 - c0)[deep]) < 1e-13
+
+
+@pytest.mark.parametrize("stretch", [1.0, 1.2, 0.9])
+def test_two_stage_quadratic_rate_matches_closed_form(stretch):
+    """c = (X/L)^2 under u = (lambda - 1) X e_x: the Piola-mapped flux is
+    Q = -(2 D / lambda L^2) X e_x, so dc/dt = 2 D m / (lambda L^2) on particles
+    whose whole two-stage stencil is interior (m: the lattice's second-moment
+    factor, computed independently)."""
+    D, dx = 1e-10, 1e-5
+    ob, X, idx, deep = _two_stage_body(D=D, dx=dx)
+    L = X[:, 0].max()
+    u = np.zeros_like(X)
+    u[:, 0] = (stretch - 1.0) * X[:, 0]
+    ob.write(O.F_U, u)
+    c0 = (X[:, 0] / L) ** 2
+    ob.write(O.F_C, c0)
+    dt = 1e-3
+    ob.diffusion_step(dt)
+    rate = (ob.read(O.F_C) - c0) / dt
+    want = 2 * D * _lattice_second_moment(1.3) / (stretch * L * L)
+    assert np.max(np.abs(rate[deep] - want)) < 1e-9 * want
+
+
+def test_two_stage_rigid_rotation_changes_nothing_and_conserves_mass():
+    ob, X, idx, deep = _two_stage_body(nx=20, ny=16)
+    rng = np.random.default_rng(2)
+    c0 = rng.uniform(0, 1, X.shape[0])
+    ob.write(O.F_C, c0)
+    ob.diffusion_step(2e-3)
+    ref = ob.read(O.F_C)
+    ob2, *_ = _two_stage_body(nx=20, ny=16)
+    th = 0.4
+    R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    ob2.write(O.F_U, X @ R.T - X)
+    ob2.write(O.F_C, c0)
+    ob2.diffusion_step(2e-3)
+    rot = ob2.read(O.F_C)
+    assert np.max(np.abs(rot - ref)) < 1e-12
+    assert abs(ref.sum() - c0.sum()) < 1e-12 * c0.sum()      # no held particles
+
+
+def test_two_stage_stable_step_bound_holds():
+    """At the reported stable step a rough field on a jittered, sheared body
+    stays bounded over many steps."""
+    X, idx, _ = B.box_body((16, 12), 1e-5, seed=9, jitter=0.2)
+    ob = O.OracleBody(X, 1e-5)
+    ob.set_material(O.SVK, 2000.0, 200e6, 0.4)
+    ob.set_diffusion(1e-10, 0.0, 0.0)
+    ob.set_diffusion_mode(1)
+    u = np.zeros_like(X)
+    u[:, 0] = 0.2 * X[:, 1]
+    ob.write(O.F_U, u)
+    c0 = np.random.default_rng(4).uniform(0, 1, X.shape[0])
+    ob.write(O.F_C, c0)
+    dt_p, dt_s = ob.diffusion_dt()
+    assert 0 < dt_s < dt_p
+    for _ in range(300):
+        ob.diffusion_step(dt_s)
+    c = ob.read(O.F_C)
+    assert np.all(np.isfinite(c)) and np.max(np.abs(c - c0.mean())) <= 1.0
