@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--batch-count", type=int, default=64,
                     help="instances of the batched workload (0 = skip)")
+    ap.add_argument("--next-rows", type=int, default=1,
+                    help="measure the droplet schedule, two-stage diffusion and equilibrium "
+                         "adjoint (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=3,
                     help="slow steps reversed in the FP64 reverse-mode measurement (0 = skip)")
     ap.add_argument("--ref-substeps", type=int, default=1,
@@ -327,6 +330,63 @@ def measure_adjoint(ctx, args, M, case):
                       "taped recomputation of the step"}
 
 
+def measure_next_rows(ctx, M):
+    """The rows built after the hot path: the droplet-contact membrane
+    (Sec. 5.4 schedule, 819,200 particles, mixed) with the one-pass and the
+    two-stage diffusion step, and the equilibrium adjoint of a relaxed beam
+    (FP64) against the unrolled reverse of the same slow step."""
+    import numpy as np
+    import torch
+    from synth import bodies as B
+    out = {}
+    case = B.membrane_droplet3d(Lx=5e-3, Ly=5e-3)
+    for mode in (0, 1):
+        gb = M.body_from_case(ctx, case, M.MIXED)
+        if mode:
+            gb.set_diffusion_mode(1)
+        dts = gb.diffusion_dt()[1]
+        kw = dict(dt_slow=dts, ke_tol=case.plan.ke_tol, ke_ref=case.plan.ke_ref, ke_mode=1,
+                  max_substeps=2000)
+        gb.advance_slow_step(**kw)                        # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sub = 0
+        for _ in range(2):
+            sub += gb.advance_slow_step(**kw).substeps
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out["membrane_two_stage" if mode else "membrane_one_pass"] = {
+            "particles": case.n, "slow_steps": 2, "substeps": sub, "seconds": dt,
+            "value": case.n * sub / dt, "unit": UNIT, "dt_slow": dts}
+        gb.close()
+    beam = B.bar2d(nx=24, ny=6, n_slow=4, eta=1e3)
+    gb = M.body_from_case(ctx, beam, M.FP64)
+    ck = gb.save_state()
+    p = dict(ramp=0.25, ke_tol=1e-26, ke_ref=beam.plan.ke_ref, max_substeps=60000)
+    k = gb.advance_slow_step(**p).substeps
+    gb.adjoint_enable(k)
+    gb.adjoint_seed(tip_bar=[1.0, 0.0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    th_eq, iters = gb.adjoint_equilibrium(max_iters=200000, tol=1e-10)
+    torch.cuda.synchronize()
+    t_eq = time.perf_counter() - t0
+    gb.adjoint_reset()
+    gb.adjoint_seed(tip_bar=[1.0, 0.0])
+    gb.load_state(ck)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    th_un = gb.adjoint_slow_step(k, **p)
+    torch.cuda.synchronize()
+    t_un = time.perf_counter() - t0
+    gb.close()
+    out["equilibrium_adjoint"] = {
+        "workload": f"bar2d-{beam.n}-svk-relaxed", "forward_substeps": k,
+        "equilibrium_iterations": iters, "equilibrium_s": t_eq, "unrolled_s": t_un,
+        "dE_rel_difference": float(abs(th_eq[0] - th_un[0]) / abs(th_un[0]))}
+    return out
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -447,6 +507,7 @@ def run_ours(args, rank, world, local):
 
     batch = measure_batch(ctx, args, M, rank, world, dist) if args.batch_count > 0 else None
     adjoint = measure_adjoint(ctx, args, M, case) if args.adjoint_steps > 0 and rank == 0 else None
+    nxt = measure_next_rows(ctx, M) if args.next_rows > 0 and rank == 0 else None
 
     if rank != 0:
         return
@@ -491,6 +552,7 @@ def run_ours(args, rank, world, local):
         "fp64_comparison": fp64,
         "batch": batch,
         "adjoint": adjoint,
+        "next_rows": nxt,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
