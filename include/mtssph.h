@@ -97,6 +97,10 @@ typedef struct {
     double h_over_dx;        /* smoothing length h = h_over_dx * dx, support 2h       */
     int32_t damp_layout;     /* mts_damp_layout of the pairwise damping order         */
     int32_t reserved;
+    double dx_axis[3];       /* lattice spacing per axis (the anisotropic kernel of   */
+                             /* thin bodies); all 0 = dx on every axis.  Otherwise dx */
+                             /* is ignored, h = h_over_dx * min spacing and the       */
+                             /* kernel is detS W(|s (.) x|), s_k = min spacing / dx_k */
 } mts_body_desc;
 
 /* Builds, on the GPU: the Morton order of the particles (cell = floor((X -

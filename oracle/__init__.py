@@ -84,6 +84,8 @@ def lib():
         L.ob_create.argtypes = [C.c_int, i64, vp, d, d, C.c_int, C.POINTER(vp)]
         L.ob_create_layout.argtypes = [C.c_int, i64, vp, d, d, C.c_int, vp, C.c_int32,
                                        C.POINTER(vp)]
+        L.ob_create_aniso.argtypes = [C.c_int, i64, vp, vp, d, C.c_int, vp, C.c_int32,
+                                      C.POINTER(vp)]
         L.ob_destroy.argtypes = [vp]
         L.ob_destroy.restype = None
         for name in ("ob_nnz", "ob_npairs", "ob_n"):
@@ -161,10 +163,12 @@ class OracleBody:
     """A particle body advanced by the FP64 oracle (same calls as the library)."""
 
     def __init__(self, X: np.ndarray, dx: float, h_over_dx: float = 1.3, brute: bool = False,
-                 damp_layout=None):
+                 damp_layout=None, dx_axis=None):
         """damp_layout = (shifts per axis, level cap) of the damping order; shifts
         are log2 of the block width in cells, WHOLE_AXIS for an unblocked axis,
-        -1 for the smallest admissible width.  Default: smallest blocks, cap 32."""
+        -1 for the smallest admissible width.  Default: smallest blocks, cap 32.
+        dx_axis: lattice spacing per axis (the anisotropic kernel); None = dx on
+        every axis."""
         X = np.ascontiguousarray(X, dtype=np.float64)
         self.n, self.dim = X.shape
         h = C.c_void_p()
@@ -172,8 +176,15 @@ class OracleBody:
             damp_layout = ((-1, -1, -1), 32)
         shifts = np.ascontiguousarray(list(damp_layout[0]) + [-1] * (3 - len(damp_layout[0])),
                                       dtype=np.int32)
-        _check(lib().ob_create_layout(self.dim, self.n, _ptr(X), dx, h_over_dx, int(brute),
-                                      _ptr(shifts), int(damp_layout[1]), C.byref(h)), "create")
+        if dx_axis is None:
+            _check(lib().ob_create_layout(self.dim, self.n, _ptr(X), dx, h_over_dx, int(brute),
+                                          _ptr(shifts), int(damp_layout[1]), C.byref(h)), "create")
+        else:
+            dk = np.ascontiguousarray(list(dx_axis) + [dx_axis[0]] * (3 - len(dx_axis)),
+                                      dtype=np.float64)
+            _check(lib().ob_create_aniso(self.dim, self.n, _ptr(X), _ptr(dk), h_over_dx,
+                                         int(brute), _ptr(shifts), int(damp_layout[1]),
+                                         C.byref(h)), "create")
         self._h = h
 
     def __del__(self):
@@ -303,7 +314,8 @@ class OracleBody:
 
 def body_from_case(case, brute: bool = False, damp_layout=None) -> OracleBody:
     """Oracle body with the material, damping, diffusion and BCs of a synth Case."""
-    b = OracleBody(case.X, case.dx, case.h_over_dx, brute=brute, damp_layout=damp_layout)
+    b = OracleBody(case.X, case.dx, case.h_over_dx, brute=brute, damp_layout=damp_layout,
+                   dx_axis=getattr(case, "dx_axis", None))
     m = case.material
     b.set_material(SVK if m.model == "svk" else J2, m.rho0, m.E, m.nu, m.sigma0, m.sigma_inf,
                    m.delta, m.H)

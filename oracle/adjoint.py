@@ -243,7 +243,7 @@ class TorchBody:
         d = self.dim
         F = self.defgrad(u)
         P, cp2, al2 = self._stress(F, cp, al, c, th)
-        PB = P[:, :d, :d] @ self.B0
+        PB = P[:, :d, :d] @ self.B0.transpose(1, 2)      # P B0^T (the C oracle's form)
         acc = self.force(PB)
         free = ~self.fix
         v = v + dt * acc * free

@@ -96,6 +96,11 @@ typedef struct {
     int dim;
     int64_t n;
     double dx, h, V, cut2;
+    /* anisotropic kernel (N4, the paper's thin-body kernel): spacing dxk per
+     * axis, h = h_over_dx * min dxk, s_k = h / (h_over_dx dxk) <= 1; the kernel
+     * is W(x) = detS W_iso(|s (.) x|) with W_iso of smoothing length h */
+    int aniso;
+    double dxk[3], sk[3], detS;
     int blk_shift;           /* smallest damping block width (2^blk_shift cells) */
     int ax_shift[3];         /* damping block width per axis: 2^ax_shift cells;  */
                              /* OB_WHOLE_AXIS = one block spans the whole axis   */
@@ -153,6 +158,18 @@ double ob_kernel_dwdr(int dim, double h, double r) {
 /* gradient with respect to X_a of W(|X_a - X_b|) (Sec. 3.1, kernel gradient) */
 static void grad_w(const ob_body *b, int64_t a, int64_t j, double g[3]) {
     double d[3], r2 = 0.0;
+    if (b->aniso) {
+        /* grad of detS W_iso(|s (.) d|): detS W_iso'(r~) s_k^2 d_k / r~ */
+        for (int k = 0; k < 3; k++) {
+            d[k] = b->X[3 * a + k] - b->X[3 * j + k];
+            double e = d[k] * b->sk[k];
+            r2 += e * e;
+        }
+        double r = sqrt(r2);
+        double dw = ob_kernel_dwdr(b->dim, b->h, r);
+        for (int k = 0; k < 3; k++) g[k] = b->detS * (dw / r) * b->sk[k] * b->sk[k] * d[k];
+        return;
+    }
     for (int k = 0; k < 3; k++) {
         d[k] = b->X[3 * a + k] - b->X[3 * j + k];
         r2 += d[k] * d[k];
@@ -242,9 +259,11 @@ static int cmp_key_idx(const void *pa, const void *pb) {
 /* 3.1, total Lagrangian formulation).                                  */
 /* ------------------------------------------------------------------ */
 static int is_neighbour(const ob_body *b, int64_t i, int64_t j) {
+    /* |s (.) (X_i - X_j)|^2 < (2h)^2: the kernel's support (an ellipsoid for
+     * an anisotropic kernel, s = 1 otherwise) */
     double r2 = 0.0;
     for (int k = 0; k < 3; k++) {
-        double d = b->X[3 * i + k] - b->X[3 * j + k];
+        double d = (b->X[3 * i + k] - b->X[3 * j + k]) * b->sk[k];
         r2 += d * d;
     }
     return r2 < b->cut2;
@@ -287,7 +306,9 @@ static int build_neighbours_cells(ob_body *b) {
             double e = b->X[3 * i + k] - b->Xmin[k];
             if (e > ext[k]) ext[k] = e;
         }
-    for (int k = 0; k < b->dim; k++) nb[k] = (int64_t)floor(ext[k] / w) + 1;
+    double wk[3];
+    for (int k = 0; k < 3; k++) wk[k] = w / b->sk[k];   /* support extent per axis */
+    for (int k = 0; k < b->dim; k++) nb[k] = (int64_t)floor(ext[k] / wk[k]) + 1;
     int64_t nbins = nb[0] * nb[1] * nb[2];
     int64_t *bin_of = malloc((size_t)n * sizeof(int64_t));
     int64_t *head = calloc((size_t)nbins + 1, sizeof(int64_t));
@@ -297,7 +318,7 @@ static int build_neighbours_cells(ob_body *b) {
     if (!bin_of || !head || !items || !fill || !b->off) return OB_ERR_OOM;
     for (int64_t i = 0; i < n; i++) {
         int64_t c[3] = {0, 0, 0};
-        for (int k = 0; k < b->dim; k++) c[k] = (int64_t)floor((b->X[3 * i + k] - b->Xmin[k]) / w);
+        for (int k = 0; k < b->dim; k++) c[k] = (int64_t)floor((b->X[3 * i + k] - b->Xmin[k]) / wk[k]);
         bin_of[i] = (c[2] * nb[1] + c[1]) * nb[0] + c[0];
         head[bin_of[i] + 1]++;
     }
@@ -531,19 +552,46 @@ int ob_create(int dim, int64_t n, const double *Xorig, double dx, double h_over_
     return ob_create_layout(dim, n, Xorig, dx, h_over_dx, brute, def, 32, out);
 }
 
+int ob_create_aniso(int dim, int64_t n, const double *Xorig, const double dxk[3],
+                    double h_over_dx, int brute, const int32_t ax_shift[3], int32_t level_cap,
+                    ob_body **out);
+
 int ob_create_layout(int dim, int64_t n, const double *Xorig, double dx, double h_over_dx,
                      int brute, const int32_t ax_shift[3], int32_t level_cap, ob_body **out) {
+    const double dxk[3] = {dx, dx, dx};
+    return ob_create_aniso(dim, n, Xorig, dxk, h_over_dx, brute, ax_shift, level_cap, out);
+}
+
+/* spacing dxk per axis; equal spacings give the isotropic kernel exactly */
+int ob_create_aniso(int dim, int64_t n, const double *Xorig, const double dxk[3],
+                    double h_over_dx, int brute, const int32_t ax_shift[3], int32_t level_cap,
+                    ob_body **out) {
     *out = NULL;
     if (level_cap < 0) return OB_ERR_ARG;
-    if ((dim != 2 && dim != 3) || n < 2 || !(dx > 0.0) || !(h_over_dx > 0.0) || n > 2000000000LL)
+    if ((dim != 2 && dim != 3) || n < 2 || !(h_over_dx > 0.0) || n > 2000000000LL)
         return OB_ERR_ARG;
+    double dx = dxk[0];
+    for (int k = 0; k < dim; k++) {
+        if (!(dxk[k] > 0.0)) return OB_ERR_ARG;
+        if (dxk[k] < dx) dx = dxk[k];
+    }
     ob_body *b = calloc(1, sizeof(ob_body));
     if (!b) return OB_ERR_OOM;
     b->dim = dim; b->n = n; b->dx = dx;
     b->h = h_over_dx * dx;
     double w = 2.0 * b->h;
     b->cut2 = w * w;
-    b->V = dim == 2 ? dx * dx : dx * dx * dx;
+    b->detS = 1.0;
+    b->V = 1.0;
+    for (int k = 0; k < 3; k++) {
+        b->dxk[k] = k < dim ? dxk[k] : dx;
+        b->sk[k] = dx / b->dxk[k];
+        if (k < dim) {
+            b->V *= b->dxk[k];
+            b->detS *= b->sk[k];
+            if (b->dxk[k] != dx) b->aniso = 1;
+        }
+    }
     /* block width: smallest power of two >= floor(2h/dx) + 1 cells */
     int64_t need = (int64_t)floor(w / dx) + 1;
     b->blk_shift = 0;
@@ -571,7 +619,7 @@ int ob_create_layout(int dim, int64_t n, const double *Xorig, double dx, double 
     if (!ki || !b->perm || !b->rank || !b->cell || !b->X) { free(ki); ob_destroy(b); return OB_ERR_OOM; }
     for (int64_t i = 0; i < n; i++) {
         int64_t c[3] = {0, 0, 0};
-        for (int k = 0; k < dim; k++) c[k] = (int64_t)floor((Xorig[(size_t)i * dim + k] - b->Xmin[k]) / dx);
+        for (int k = 0; k < dim; k++) c[k] = (int64_t)floor((Xorig[(size_t)i * dim + k] - b->Xmin[k]) / b->dxk[k]);
         ki[i].key = morton_key(dim, c);
         ki[i].orig = i;
     }
@@ -582,7 +630,7 @@ int ob_create_layout(int dim, int64_t n, const double *Xorig, double dx, double 
         b->rank[i] = s;
         for (int k = 0; k < dim; k++) {
             b->X[3 * s + k] = Xorig[(size_t)i * dim + k];
-            b->cell[3 * s + k] = (int64_t)floor((b->X[3 * s + k] - b->Xmin[k]) / dx);
+            b->cell[3 * s + k] = (int64_t)floor((b->X[3 * s + k] - b->Xmin[k]) / b->dxk[k]);
         }
     }
     free(ki);
@@ -848,9 +896,12 @@ static int stage_stress(ob_body *b) {
         double F[9], P[9];
         defgrad(b, a, F);
         stress_point(b, F, b->cpinv + 6 * a, b->alpha + a, b->c[a], P, NULL);
-        /* store PB_a = P_a B0_a (d x d block) */
-        double PBf[9];
-        m3_mul(P, b->B0 + 9 * a, PBf);
+        /* store PB_a = P_a B0_a^T (d x d block): the force that is the
+         * variation of sum V psi(F) for F = I + sum_b (u_b - u_a) (x) B0_a^T V grad W
+         * (B0 is symmetric for an isotropic kernel) */
+        double PBf[9], B0t[9];
+        m3_transpose(b->B0 + 9 * a, B0t);
+        m3_mul(P, B0t, PBf);
         for (int r = 0; r < d; r++)
             for (int s = 0; s < d; s++) b->PB[9 * a + 3 * r + s] = PBf[3 * r + s];
         for (int k = 0; k < 9; k++)
@@ -904,9 +955,12 @@ static void damp_pair(ob_body *b, int64_t a, int64_t j, double dt, double coef) 
 
 /* B_ab = -2 eta V_a V_b W'(r0_ab)/r0_ab  (Sec. 4.3, viscous damping) */
 static double damp_coef(const ob_body *b, int64_t a, int64_t j) {
+    /* anisotropic kernel: the same formula on the scaled distance |s (.) d|
+     * (the damping is a relaxation device; its form does not move the
+     * equilibrium) */
     double r2 = 0.0;
     for (int k = 0; k < 3; k++) {
-        double dd = b->X[3 * a + k] - b->X[3 * j + k];
+        double dd = (b->X[3 * a + k] - b->X[3 * j + k]) * b->sk[k];
         r2 += dd * dd;
     }
     double r = sqrt(r2);
@@ -1126,6 +1180,9 @@ int ob_set_diffusion_mode(ob_body *b, int mode) {
 
 int ob_diffusion_step(ob_body *b, double dt) {
     if (b->diff_mode == 1) return diffusion_step_two_stage(b, dt);
+    /* the one-pass pairwise Laplacian is not consistent for an anisotropic
+     * kernel (its second moment is not isotropic): two-stage form only */
+    if (b->aniso) return OB_ERR_STATE;
     double *cn = malloc((size_t)b->n * sizeof(double));
     if (!cn) return OB_ERR_OOM;
     for (int64_t i = 0; i < b->n; i++) {

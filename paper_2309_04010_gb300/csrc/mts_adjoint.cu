@@ -12,8 +12,8 @@
 //   drift    v-bar += dt u-bar on free axes; u-bar = v-bar = 0 on prescribed axes
 //   damping  the same sequence of pair updates, each 2x2 update transposed
 //   kick     a-bar = dt v-bar on free axes, plus the end-force adjoint
-//   force    (P B0)-bar_c = -(1/rho0) sum_b (a-bar_b - a-bar_c) (x) g_cb
-//   P B0     P-bar = (P B0)-bar B0^T
+//   force    (P B0^T)-bar_c = -(1/rho0) sum_b (a-bar_b - a-bar_c) (x) g_cb
+//   P B0^T   P-bar = (P B0^T)-bar B0
 //   stress   Jacobian columns from forward-mode duals, contracted with the
 //            output adjoints (P, C-bar_p^-1', alpha')
 //   F        G-bar = F-bar B0^T;  u-bar_c -= sum_b (G-bar_c + G-bar_b) g_cb
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(128) k_adj_stress(Args<double> A, const double
                 for (int k = 0; k < D; ++k) s += Gu[r][k] * B[k][q];
                 F[r][q] += s;
             }
-        // P-bar = (P B0)-bar B0^T with (P B0)-bar = -(1/rho0) G[a-bar]
+        // P-bar = (P B0^T)-bar B0 with (P B0^T)-bar = -(1/rho0) G[a-bar]
         double yb[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) yb[k] = 0.0;
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(128) k_adj_stress(Args<double> A, const double
             for (int q = 0; q < D; ++q) {
                 double s = 0.0;
 #pragma unroll
-                for (int k = 0; k < D; ++k) s += Ga[r][k] * B[q][k];
+                for (int k = 0; k < D; ++k) s += Ga[r][k] * B[k][q];
                 yb[r * 3 + q] = irho * s;
             }
         double cp7[7];

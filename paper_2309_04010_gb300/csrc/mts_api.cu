@@ -305,6 +305,11 @@ mts_status slow_step_begin(mts_body *b, const mts_step_params *p, long long *lau
             set_error("mts_advance_slow_step: dt_slow > 0 without diffusion");
             return MTS_ERR_STATE;
         }
+        if (b->aniso && b->diff_mode == 0) {
+            set_error("mts_advance_slow_step: an anisotropic kernel needs the two-stage diffusion "
+                      "(mts_set_diffusion_mode 1)");
+            return MTS_ERR_STATE;
+        }
         double dtp, dts;
         MTS_TRY(mts_diffusion_dt(b, &dtp, &dts));
         if (p->dt_slow > dts * (1.0 + 1e-12) && !p->force_dt) {
@@ -486,6 +491,20 @@ mts_status mts_body_create(mts_ctx *ctx, const mts_body_desc *desc, mts_body **o
                   desc->precision, desc->damp_layout);
         return MTS_ERR_INVALID_ARG;
     }
+    // per-axis spacing (anisotropic kernel): all zero = isotropic
+    double dxk[3] = {desc->dx, desc->dx, desc->dx};
+    bool any_axis = false;
+    for (int k = 0; k < desc->dim; ++k) any_axis |= desc->dx_axis[k] != 0.0;
+    if (any_axis)
+        for (int k = 0; k < desc->dim; ++k) {
+            if (!(desc->dx_axis[k] > 0) || !std::isfinite(desc->dx_axis[k])) {
+                set_error("mts_body_create: dx_axis[%d] = %g", k, desc->dx_axis[k]);
+                return MTS_ERR_INVALID_ARG;
+            }
+            dxk[k] = desc->dx_axis[k];
+        }
+    double dref = dxk[0];
+    for (int k = 1; k < desc->dim; ++k) dref = std::min(dref, dxk[k]);
     MTS_CUDA(cudaSetDevice(ctx->device));
     mts_body *b = new (std::nothrow) mts_body();
     if (!b) return MTS_ERR_OOM;
@@ -493,11 +512,20 @@ mts_status mts_body_create(mts_ctx *ctx, const mts_body_desc *desc, mts_body **o
     b->dim = desc->dim;
     b->precision = desc->precision;
     b->n = desc->n;
-    b->dx = desc->dx;
-    b->h = desc->h_over_dx * desc->dx;
+    b->dx = dref;
+    b->h = desc->h_over_dx * dref;
     const double w = 2.0 * b->h;
     b->cut2 = w * w;
-    b->V = b->dim == 2 ? b->dx * b->dx : b->dx * b->dx * b->dx;
+    b->V = 1.0;
+    b->detS = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        b->sk[k] = k < b->dim ? dref / dxk[k] : 1.0;
+        if (k < b->dim) {
+            b->V *= dxk[k];
+            b->detS *= b->sk[k];
+            b->aniso |= dxk[k] != dref;
+        }
+    }
     long long need = (long long)std::floor(w / b->dx) + 1;
     b->blk_shift = 0;
     while ((1LL << b->blk_shift) < need) ++b->blk_shift;
@@ -553,7 +581,15 @@ mts_status mts_body_create(mts_ctx *ctx, const mts_body_desc *desc, mts_body **o
         body_free(b);
         return cuda_fail(e, "k_init_state");
     }
-    s = build_body(b, desc->X);
+    if (b->aniso) {
+        // the whole set-up runs on positions scaled to the isotropic kernel
+        std::vector<double> Xs((size_t)n * b->dim);
+        for (long long i = 0; i < n; ++i)
+            for (int k = 0; k < b->dim; ++k) Xs[i * b->dim + k] = desc->X[i * b->dim + k] * b->sk[k];
+        s = build_body(b, Xs.data());
+    } else {
+        s = build_body(b, desc->X);
+    }
     if (s != MTS_OK) {
         cudaStreamSynchronize(st);
         body_free(b);
@@ -1148,6 +1184,10 @@ mts_status mts_adjoint_enable(mts_body *b, int64_t max_substeps) {
     }
     if (b->precision != MTS_FP64) {
         set_error("mts_adjoint_enable: the reverse mode runs on FP64 bodies only");
+        return MTS_ERR_STATE;
+    }
+    if (b->aniso) {
+        set_error("mts_adjoint_enable: the reverse mode has no anisotropic-kernel form");
         return MTS_ERR_STATE;
     }
     MTS_CUDA(cudaSetDevice(b->ctx->device));

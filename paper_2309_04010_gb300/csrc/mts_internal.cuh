@@ -99,6 +99,9 @@ struct Args {
     R c0;
     R dcoef;       // 2 D * kcoef (diffusion, includes V)
     R diffD;       // D (two-stage diffusion)
+    int aniso;     // anisotropic kernel: positions scaled by sk
+    R sk[3];       // per-axis scale of the positions (1 = isotropic)
+    R detS;        // product of sk over the axes
     R *qflux;      // two-stage diffusion: Piola-mapped flux per particle (PAD)
     int swelling;
     double mass, h, cs;
@@ -221,6 +224,10 @@ struct mts_body {
     bool has_diff;
     double D, beta, c0;
     int diff_mode;            // 0: one-pass Laplacian, 1: two-stage flux (deformed configuration)
+    // anisotropic kernel: positions are stored scaled by sk (X~ = s (.) X, the
+    // kernel isotropic with h in those coordinates); V is the real volume
+    int aniso;
+    double sk[3], detS;
     void *qflux;              // n x PAD, allocated with diff_mode 1
 
     // loop machinery

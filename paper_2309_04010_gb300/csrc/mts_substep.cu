@@ -85,6 +85,18 @@ __device__ __forceinline__ void compute_F(const Args<R> &A, const R *sX, const R
         }
 }
 
+// Anisotropic kernel: the gathers run on scaled positions X~ = s (.) X, where
+// the kernel is isotropic; the real deformation gradient is
+// F = I + (F~ - I) diag(s) (the corrected gradient maps back column by column).
+template <class R, int D>
+__device__ __forceinline__ void unscale_F(const Args<R> &A, R (&F)[3][3]) {
+    if (!A.aniso) return;
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) F[r][c] = (r == c ? R(1) : R(0)) + (F[r][c] - (r == c ? R(1) : R(0))) * A.sk[c];
+}
+
 // --------------------------------------------------------------------- K_A
 template <class R, int D, int MAT>
 __global__ void __launch_bounds__(256) k_stress(Args<R> A) {
@@ -98,6 +110,7 @@ __global__ void __launch_bounds__(256) k_stress(Args<R> A) {
     if (i >= A.n) return;
     R F[3][3];
     compute_F<R, D>(A, sX, sU, i, F);
+    unscale_F<R, D>(A, F);
     R P3[3][3];
     if constexpr (MAT == MTS_ELASTIC_SVK) {
         stress_svk<R>(F, A.lambda, A.mu, P3);
@@ -117,6 +130,8 @@ __global__ void __launch_bounds__(256) k_stress(Args<R> A) {
     if (A.swelling) add_swelling<R>(F, A.swell * (A.c[i] - A.c0), P3);
     R B[D][D];
     ldg_mat<R, D>(B, A.B0 + i * MatS<D>::v);
+    // P B0^T (the variational force of F = I + sum (u_b - u_a) (x) B0^T grad W;
+    // B0 is symmetric for an isotropic kernel); anisotropic: P diag(s) B0~^T
     R PB[D][D];
 #pragma unroll
     for (int r = 0; r < D; ++r)
@@ -124,7 +139,7 @@ __global__ void __launch_bounds__(256) k_stress(Args<R> A) {
         for (int c = 0; c < D; ++c) {
             R acc = R(0);
 #pragma unroll
-            for (int k = 0; k < D; ++k) acc += P3[r][k] * B[k][c];
+            for (int k = 0; k < D; ++k) acc += P3[r][k] * (A.aniso ? A.sk[k] : R(1)) * B[c][k];
             PB[r][c] = acc;
         }
     if constexpr (D == 3) {
@@ -865,6 +880,7 @@ __global__ void __launch_bounds__(256) k_diff_flux(Args<R> A) {
     if (i >= A.n) return;
     R F[3][3];
     compute_F<R, D>(A, sX, sU, i, F);
+    unscale_F<R, D>(A, F);
     const int li = A.lself[i];
     R xa[P];
     ld_vec<R, P>(xa, sX + li * P);
@@ -889,13 +905,13 @@ __global__ void __launch_bounds__(256) k_diff_flux(Args<R> A) {
     });
     R B[D][D];
     ldg_mat<R, D>(B, A.B0 + i * MatS<D>::v);
-    R g0[D];
+    R g0[D];   // reference gradient of c: B0^T g (anisotropic: s (.) B0~^T g~)
 #pragma unroll
     for (int r = 0; r < D; ++r) {
         R s = R(0);
 #pragma unroll
         for (int k = 0; k < D; ++k) s += B[k][r] * g[k];
-        g0[r] = s;
+        g0[r] = A.aniso ? s * A.sk[r] : s;
     }
     R Ci[3][3], J;
     inv_cauchy_green<R, D>(F, Ci, J);
@@ -906,7 +922,8 @@ __global__ void __launch_bounds__(256) k_diff_flux(Args<R> A) {
         if (r < D)
 #pragma unroll
             for (int k = 0; k < D; ++k) s += Ci[r][k] * g0[k];
-        q[r] = r < D ? -A.diffD * J * s : R(0);
+        // stored for the divergence gather on scaled positions: detS s (.) Q
+        q[r] = r < D ? -A.diffD * J * s * (A.aniso ? A.detS * A.sk[r] : R(1)) : R(0);
     }
     st_vec<R, P>(A.qflux + i * P, q);
 }
@@ -979,16 +996,18 @@ __global__ void __launch_bounds__(256) k_ts_rowcoef(Args<R> A, double *Rx) {
         for (int k = 0; k < D; ++k) {
             d[k] = xa[k] - xb[k];
             r2 += d[k] * d[k];
-            n1 += d[k] < R(0) ? -d[k] : d[k];
+            n1 += (d[k] < R(0) ? -d[k] : d[k]) * (A.aniso ? A.detS * A.sk[k] : R(1));
         }
         const R tt = R(1) - R(0.5) * nsqrt(r2) * A.inv_h;
         const R f = A.kcoef * tt * tt * tt;
         s1 += (double)(f < R(0) ? -f : f) * (double)n1;
     });
+    unscale_F<R, D>(A, F);
     R B[D][D];
     ldg_mat<R, D>(B, A.B0 + i * MatS<D>::v);
     R Ci[3][3], J;
     inv_cauchy_green<R, D>(F, Ci, J);
+    // real B0^T = diag(s) B0~^T diag(1/s) / detS; real |grad W|_1 = detS sum s_k |grad~_k|
     double nrm = 0.0;
 #pragma unroll
     for (int r = 0; r < D; ++r) {
@@ -997,7 +1016,9 @@ __global__ void __launch_bounds__(256) k_ts_rowcoef(Args<R> A, double *Rx) {
         for (int k = 0; k < D; ++k) {
             double m = 0.0;
 #pragma unroll
-            for (int q = 0; q < D; ++q) m += (double)Ci[r][q] * (double)B[k][q];
+            for (int q = 0; q < D; ++q)
+                m += (double)Ci[r][q] * (double)B[k][q] *
+                     (A.aniso ? (double)A.sk[q] / ((double)A.sk[k] * (double)A.detS) : 1.0);
             rs += fabs(m);
         }
         nrm = fmax(nrm, rs);
@@ -1033,7 +1054,7 @@ __global__ void __launch_bounds__(256) k_ts_bound(Args<R> A, const double *Rx, d
             for (int k = 0; k < D; ++k) {
                 d[k] = xa[k] - xb[k];
                 r2 += d[k] * d[k];
-                n1 += d[k] < R(0) ? -d[k] : d[k];
+                n1 += (d[k] < R(0) ? -d[k] : d[k]) * (A.aniso ? A.detS * A.sk[k] : R(1));
             }
             const R tt = R(1) - R(0.5) * nsqrt(r2) * A.inv_h;
             const R f = A.kcoef * tt * tt * tt;
@@ -1099,6 +1120,7 @@ __global__ void __launch_bounds__(256) k_defgrad(Args<R> A, double *out) {
     if (i >= A.n) return;
     R F[3][3];
     compute_F<R, D>(A, sX, sU, i, F);
+    unscale_F<R, D>(A, F);
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) out[i * 9 + r * 3 + c] = (double)F[r][c];
 }
@@ -1113,14 +1135,17 @@ __global__ void k_field_out(Args<R> A, int field, const long long *perm, const d
     const long long i = perm[s];
     switch (field) {
     case MTS_F_U: for (int k = 0; k < D; ++k) out[i * D + k] = A.u[s * P + k]; break;
-    case MTS_F_X: for (int k = 0; k < D; ++k) out[i * D + k] = X64[s * P + k]; break;
+    case MTS_F_X:
+        for (int k = 0; k < D; ++k) out[i * D + k] = X64[s * P + k] / (A.aniso ? (double)A.sk[k] : 1.0);
+        break;
     case MTS_F_V: for (int k = 0; k < D; ++k) out[i * D + k] = (double)A.v[s * P + k]; break;
     case MTS_F_ACC: for (int k = 0; k < D; ++k) out[i * D + k] = (double)A.acc[s * P + k]; break;
     case MTS_F_PB:
         for (int r = 0; r < D; ++r)
             for (int c = 0; c < D; ++c)
                 out[i * D * D + r * D + c] =
-                    (double)A.PB[s * MatS<D>::v + (D == 3 ? 3 + 3 * r + c : r * P + c)];
+                    (double)A.PB[s * MatS<D>::v + (D == 3 ? 3 + 3 * r + c : r * P + c)] /
+                    (A.aniso ? (double)A.detS * (double)A.sk[c] : 1.0);
         break;
     case MTS_F_C: out[i] = (double)A.c[s]; break;
     case MTS_F_ALPHA: out[i] = (double)A.cp[s * 8 + 6]; break;
@@ -1245,6 +1270,9 @@ Args<R> make_args(mts_body *b) {
     A.dcoef = (R)(2.0 * b->D * b->V * (-5.0 * alpha / (b->h * b->h)));
     A.diffD = (R)b->D;
     A.qflux = (R *)b->qflux;
+    A.aniso = b->aniso;
+    for (int k = 0; k < 3; ++k) A.sk[k] = (R)b->sk[k];
+    A.detS = (R)b->detS;
     A.mass = b->rho0 * b->V;
     A.h = b->h;
     A.cs = std::sqrt(b->K / b->rho0);

@@ -63,7 +63,8 @@ class Allocator(C.Structure):
 class BodyDesc(C.Structure):
     _fields_ = [("dim", C.c_int32), ("precision", C.c_int32), ("n", C.c_int64),
                 ("X", C.c_void_p), ("dx", C.c_double), ("h_over_dx", C.c_double),
-                ("damp_layout", C.c_int32), ("reserved", C.c_int32)]
+                ("damp_layout", C.c_int32), ("reserved", C.c_int32),
+                ("dx_axis", C.c_double * 3)]
 
 
 class StepParams(C.Structure):
@@ -218,12 +219,16 @@ class Body:
     """mts_body: a particle body with its fixed neighbourhood on the GPU."""
 
     def __init__(self, ctx: Context, X: np.ndarray, dx: float, h_over_dx: float = 1.3,
-                 precision: int = FP64, damp_layout: int = DAMP_AUTO):
+                 precision: int = FP64, damp_layout: int = DAMP_AUTO, dx_axis=None):
+        """dx_axis: lattice spacing per axis (anisotropic kernel); None = dx."""
         X = np.ascontiguousarray(X, dtype=np.float64)
         self.n, self.dim = X.shape
         self.ctx = ctx
         self.precision = precision
-        desc = BodyDesc(self.dim, precision, self.n, X.ctypes.data, dx, h_over_dx, damp_layout, 0)
+        da = (C.c_double * 3)(*([0.0] * 3 if dx_axis is None else
+                                list(dx_axis) + [0.0] * (3 - len(dx_axis))))
+        desc = BodyDesc(self.dim, precision, self.n, X.ctypes.data, dx, h_over_dx, damp_layout, 0,
+                        da)
         h = C.c_void_p()
         _check(lib().mts_body_create(ctx.handle, C.byref(desc), C.byref(h)), "mts_body_create")
         self._h = h
@@ -525,7 +530,8 @@ def slow_steps(body: Body, theta, steps):
 
 def body_from_case(ctx: Context, case, precision: int = FP64, damp_layout: int = DAMP_AUTO) -> Body:
     """Body with the material, damping, diffusion and BCs of a synth Case."""
-    b = Body(ctx, case.X, case.dx, case.h_over_dx, precision, damp_layout)
+    b = Body(ctx, case.X, case.dx, case.h_over_dx, precision, damp_layout,
+             getattr(case, "dx_axis", None))
     m = case.material
     b.set_material(ELASTIC_SVK if m.model == "svk" else NEOHOOKE_J2, m.rho0, m.E, m.nu,
                    m.sigma0, m.sigma_inf, m.delta, m.H)

@@ -105,6 +105,8 @@ class Case:
     h_over_dx: float = H_OVER_DX
     # time-limited contact: (time after which the set is released, its ids)
     release: Optional[Tuple[float, np.ndarray]] = None
+    # lattice spacing per axis (anisotropic kernel); None = dx on every axis
+    dx_axis: Optional[Tuple[float, ...]] = None
 
     @property
     def n(self) -> int:
@@ -115,18 +117,20 @@ def rng_for(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(seed))
 
 
-def lattice_box(counts, dx: float) -> Tuple[np.ndarray, np.ndarray]:
-    """Cell-centred lattice; returns (positions, integer lattice indices)."""
+def lattice_box(counts, dx) -> Tuple[np.ndarray, np.ndarray]:
+    """Cell-centred lattice (dx: one spacing, or one per axis); returns
+    (positions, integer lattice indices)."""
     axes = [np.arange(c, dtype=np.int64) for c in counts]
     grids = np.meshgrid(*axes, indexing="ij")
     idx = np.stack([g.reshape(-1) for g in grids], axis=1)
-    X = (idx.astype(np.float64) + 0.5) * dx
+    X = (idx.astype(np.float64) + 0.5) * np.asarray(dx, dtype=np.float64)
     return X, idx
 
 
-def add_jitter(X: np.ndarray, dx: float, rng: np.random.Generator,
+def add_jitter(X: np.ndarray, dx, rng: np.random.Generator,
                frac: float = JITTER) -> np.ndarray:
-    return X + rng.uniform(-frac * dx, frac * dx, size=X.shape)
+    a = frac * np.asarray(dx, dtype=np.float64)
+    return X + rng.uniform(-a, a, size=X.shape)
 
 
 def box_body(counts, dx: float, seed: int, jitter: float = JITTER):
@@ -308,9 +312,9 @@ def batch_instances(count: int = 64, n_min: int = 5_000, n_max: int = 200_000,
 # time, then released; elsewhere c starts at 0; no flux leaves the body.
 # --------------------------------------------------------------------------
 def _droplet_case(name, counts, dx, seed, E, nu, rho0, eta, D, beta, c_held, t_contact,
-                  t_end, ke_tol, jitter, clamp_axes) -> Case:
+                  t_end, ke_tol, jitter, clamp_axes, dx_axis=None) -> Case:
     dim = len(counts)
-    X, idx, _ = box_body(counts, dx, seed, jitter)
+    X, idx, _ = box_body(counts, dx if dx_axis is None else dx_axis, seed, jitter)
     clamp = np.unique(np.concatenate(
         [layer_ids(idx, a, 0, 3) for a in clamp_axes] +
         [layer_ids(idx, a, counts[a] - 3, 3) for a in clamp_axes]))
@@ -329,20 +333,23 @@ def _droplet_case(name, counts, dx, seed, E, nu, rho0, eta, D, beta, c_held, t_c
     centre = np.nonzero(np.all(idx[:, :dim - 1] == mid, axis=1))[0].astype(np.int64)
     return Case(name, dim, X, dx, Material("svk", rho0, E, nu), eta, bcs,
                 [ConcBC(contact, c_held)], centre, plan, (D, beta, 0.0), idx, tuple(counts),
-                release=(t_contact, contact))
+                release=(t_contact, contact), dx_axis=dx_axis)
 
 
 def beam_droplet2d(L: float = 10e-3, W: float = 0.125e-3, ny: int = 8,
                    seed: int = SEED_BASE + 6, E: float = 200e6, nu: float = 0.4,
                    rho0: float = 2000.0, eta: float = 1e4, D: float = 1e-10, beta: float = 0.1,
                    c_held: float = 0.4, t_contact: float = 10.0, t_end: float = 100.0,
-                   ke_tol: float = 5e-4, jitter: float = JITTER) -> Case:
+                   ke_tol: float = 5e-4, jitter: float = JITTER, aniso: float = 1.0) -> Case:
     """Sec. 5.3: a 10 x 0.125 mm beam, both ends clamped, contact on the centre
-    0.3 L of the upper half for 10 s of 100 s (isotropic spacing W/ny)."""
-    dx = W / ny
-    nx = int(round(L / dx))
-    return _droplet_case("beam_droplet2d", (nx, ny), dx, seed, E, nu, rho0, eta, D, beta,
-                         c_held, t_contact, t_end, ke_tol, jitter, clamp_axes=(0,))
+    0.3 L of the upper half for 10 s of 100 s.  Spacing W/ny across the beam,
+    aniso times that along it (the paper uses 4 with its anisotropic kernel)."""
+    dy = W / ny
+    dxa = aniso * dy
+    nx = int(round(L / dxa))
+    return _droplet_case("beam_droplet2d", (nx, ny), dy, seed, E, nu, rho0, eta, D, beta,
+                         c_held, t_contact, t_end, ke_tol, jitter, clamp_axes=(0,),
+                         dx_axis=None if aniso == 1.0 else (dxa, dy))
 
 
 def membrane_droplet3d(Lx: float = 10e-3, Ly: float = 10e-3, Lz: float = 0.125e-3, nz: int = 8,
@@ -350,14 +357,16 @@ def membrane_droplet3d(Lx: float = 10e-3, Ly: float = 10e-3, Lz: float = 0.125e-
                        rho0: float = 2000.0, eta: float = 1e4, D: float = 1e-10,
                        beta: float = 0.1, c_held: float = 0.4, t_contact: float = 450.0,
                        t_end: float = 2500.0, ke_tol: float = 1e-3,
-                       jitter: float = JITTER) -> Case:
+                       jitter: float = JITTER, aniso: float = 1.0) -> Case:
     """Sec. 5.4: a 10 x 10 x 0.125 mm membrane, four sides clamped, contact on
-    the centre 0.3 Lx x 0.3 Ly of the upper half for 450 s of 2500 s
-    (isotropic spacing Lz/nz)."""
-    dx = Lz / nz
-    nx, ny = int(round(Lx / dx)), int(round(Ly / dx))
-    return _droplet_case("membrane_droplet3d", (nx, ny, nz), dx, seed, E, nu, rho0, eta, D,
-                         beta, c_held, t_contact, t_end, ke_tol, jitter, clamp_axes=(0, 1))
+    the centre 0.3 Lx x 0.3 Ly of the upper half for 450 s of 2500 s.  Spacing
+    Lz/nz through the thickness, aniso times that in plane (the paper uses 8)."""
+    dz = Lz / nz
+    dxy = aniso * dz
+    nx, ny = int(round(Lx / dxy)), int(round(Ly / dxy))
+    return _droplet_case("membrane_droplet3d", (nx, ny, nz), dz, seed, E, nu, rho0, eta, D,
+                         beta, c_held, t_contact, t_end, ke_tol, jitter, clamp_axes=(0, 1),
+                         dx_axis=None if aniso == 1.0 else (dxy, dxy, dz))
 
 def workload(number: int, **kw) -> Case:
     """The five benchmark workloads by number (1..4; 5 is batch_instances)."""

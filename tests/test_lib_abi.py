@@ -45,4 +45,4 @@ def test_allocator_hook_is_validated():
 def test_struct_layouts_match_header():
     assert C.sizeof(M.StepParams) == 5 * 8 + 8 + 4 * 4
     assert C.sizeof(M.StepReport) == 8 + 4 + 4 + 4 * 8 + 6 * 8 + 8 + 8 + 8
-    assert C.sizeof(M.BodyDesc) == 4 + 4 + 8 + 8 + 8 + 8 + 4 + 4
+    assert C.sizeof(M.BodyDesc) == 4 + 4 + 8 + 8 + 8 + 8 + 4 + 4 + 3 * 8

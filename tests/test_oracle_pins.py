@@ -419,7 +419,7 @@ def test_uniaxial_closed_form_is_discrete_equilibrium(dim):
     # traction-free lateral surfaces included: no force anywhere away from the ends
     assert np.max(np.abs(acc[body])) < 1e-4 * scale
     PB = ob.read(O.F_PB).reshape(-1, dim, dim)
-    P = np.einsum("nij,njk->nik", PB, np.linalg.inv(ob.b0()))
+    P = np.einsum("nij,njk->nik", PB, np.linalg.inv(np.transpose(ob.b0(), (0, 2, 1))))
     assert np.max(np.abs(P[:, 0, 0] - Ep * eps)) < 1e-4 * Ep * eps
     for k in range(1, dim):
         assert np.max(np.abs(P[:, k, k])) < 1e-4 * Ep * eps
@@ -659,7 +659,7 @@ def test_j2_body_matches_material_point_under_affine_F():
     ob.write(O.F_U, X @ G.T)
     ob.substep_partial(1e-15, 1)
     PB = ob.read(O.F_PB).reshape(-1, 3, 3)
-    P = np.einsum("nij,njk->nik", PB, np.linalg.inv(ob.b0()))
+    P = np.einsum("nij,njk->nik", PB, np.linalg.inv(np.transpose(ob.b0(), (0, 2, 1))))
     Pw, cpw, alw, plw, _ = O.stress_point(O.J2, p["rho0"], p["E"], p["nu"], np.eye(3) + G, None,
                                           0.0, p["sigma0"], p["sigma_inf"], p["delta"], p["H"])
     assert plw
@@ -857,3 +857,105 @@ def test_two_stage_stable_step_bound_holds():
         ob.diffusion_step(dt_s)
     c = ob.read(O.F_C)
     assert np.all(np.isfinite(c)) and np.max(np.abs(c - c0.mean())) <= 1.0
+
+
+# ----------------------------------------------------------------------------
+# P19: anisotropic kernel for thin bodies (spacing per axis; Sec. 5.3-5.4)
+# ----------------------------------------------------------------------------
+def _aniso_body(dim, counts, ratio, jitter=0.01, seed=31):
+    d0 = 1e-5
+    dxk = [ratio * d0] * (dim - 1) + [d0]                 # coarse in plane, fine across
+    X, idx, _ = B.box_body(counts, dxk, seed, jitter)
+    return X, idx, dxk
+
+
+@pytest.mark.parametrize("dim,counts,ratio", [(2, (12, 16), 4.0), (3, (7, 6, 12), 8.0)])
+def test_aniso_neighbours_are_the_ellipsoid_and_F_is_exact(dim, counts, ratio):
+    X, idx, dxk = _aniso_body(dim, counts, ratio)
+    ob = O.OracleBody(X, min(dxk), dx_axis=dxk)
+    off, nb = ob.neighbors()
+    perm = ob.perm()
+    Xs = X[perm]
+    h = 1.3 * min(dxk)
+    s = min(dxk) / np.asarray(dxk)
+    d = (Xs[:, None, :] - Xs[None, :, :]) * s          # NumPy brute force, scaled
+    r2 = (d * d).sum(-1)
+    np.fill_diagonal(r2, np.inf)
+    for i in range(len(Xs)):
+        assert np.array_equal(nb[off[i]:off[i + 1]], np.nonzero(r2[i] < (2 * h) ** 2)[0])
+    G = np.random.default_rng(3).uniform(-0.05, 0.05, (dim, dim))
+    ob.write(O.F_U, X @ G.T)
+    F = ob.read(O.F_DEFGRAD).reshape(-1, 3, 3)
+    want = np.eye(3)
+    want[:dim, :dim] += G
+    assert np.max(np.abs(F - want)) < 1e-12
+
+
+def test_aniso_force_balance_and_momentum():
+    X, idx, dxk = _aniso_body(2, (14, 20), 4.0, jitter=0.0)
+    ob = O.OracleBody(X, min(dxk), dx_axis=dxk)
+    ob.set_material(O.SVK, 2000.0, 200e6, 0.4)
+    G = np.array([[1e-3, 3e-4], [-2e-4, 5e-4]])
+    ob.write(O.F_U, X @ G.T)
+    ob.substep_partial(1e-12, 2)
+    acc = ob.read(O.F_ACC)
+    scale = 200e6 * 1e-3 / (2000 * min(dxk))
+    deep = np.all((idx >= 4) & (idx < np.array([14, 20]) - 4), axis=1)
+    assert np.max(np.abs(acc[deep])) < 1e-9 * scale          # uniform stress: no interior force
+    X2, _, dxk2 = _aniso_body(2, (10, 12), 4.0, jitter=0.05)
+    ob2 = O.OracleBody(X2, min(dxk2), dx_axis=dxk2)
+    ob2.set_material(O.SVK, 2000.0, 200e6, 0.4)
+    ob2.write(O.F_U, B.random_field(X2.shape[0], 2, 1e-2 * min(dxk2), 6))
+    ob2.substep_partial(1e-12, 2)
+    a2 = ob2.read(O.F_ACC)
+    assert np.max(np.abs(a2.sum(0))) < 1e-10 * np.abs(a2).sum()   # pair-antisymmetric force
+
+
+def test_aniso_two_stage_quadratic_rate_and_one_pass_refused():
+    D, ratio = 1e-10, 4.0
+    X, idx, dxk = _aniso_body(2, (20, 40), ratio, jitter=0.0)
+    ob = O.OracleBody(X, min(dxk), dx_axis=dxk)
+    ob.set_material(O.SVK, 2000.0, 200e6, 0.4)
+    ob.set_diffusion(D, 0.0, 0.0)
+    with pytest.raises(O.OracleError):
+        ob.diffusion_step(1e-3)                               # one-pass form: not for this kernel
+    ob.set_diffusion_mode(1)
+    Ly = X[:, 1].max()
+    c0 = (X[:, 1] / Ly) ** 2
+    ob.write(O.F_C, c0)
+    ob.diffusion_step(1e-3)
+    rate = (ob.read(O.F_C) - c0) / 1e-3
+    # second moment of the normalised anisotropic kernel on this lattice,
+    # summed here independently: -sum_b V dy_b (d W / d y)_b
+    h = 1.3 * min(dxk)
+    sx = min(dxk) / dxk[0]
+    ad = 7 / (4 * math.pi * h * h)
+    m = 0.0
+    for i in range(-4, 5):
+        for j in range(-4, 5):
+            if i == 0 and j == 0:
+                continue
+            dxv, dyv = i * dxk[0], j * dxk[1]
+            rt = math.hypot(dxv * sx, dyv)
+            if rt >= 2 * h:
+                continue
+            q = rt / h
+            dw = -5 * ad * q * (1 - q / 2) ** 3 / h
+            gy = sx * dw / rt * dyv                           # detS * W'/r~ * s_y^2 * dy
+            m += -(dxk[0] * dxk[1]) * dyv * gy
+    deep = np.all((idx >= np.array([6, 6])) & (idx < np.array([20, 40]) - 6), axis=1)
+    want = 2 * D * m / Ly ** 2
+    assert abs(m - 1) < 0.05
+    assert np.max(np.abs(rate[deep] - want)) < 1e-9 * want
+
+
+def test_aniso_with_equal_spacings_is_the_isotropic_body():
+    X, _, _ = B.box_body((9, 7), 1e-5, seed=4, jitter=0.05)
+    a = O.OracleBody(X, 1e-5)
+    b = O.OracleBody(X, 1e-5, dx_axis=[1e-5, 1e-5])
+    for o in (a, b):
+        o.set_material(O.SVK, 2000.0, 200e6, 0.4)
+        o.set_damping(1e3)
+        o.write(O.F_U, B.random_field(X.shape[0], 2, 1e-7, 2))
+        o.advance(ramp=0.0, ke_tol=-1.0, max_substeps=5)
+    assert np.array_equal(a.read(O.F_U), b.read(O.F_U))
