@@ -1333,13 +1333,22 @@ extern "C" mts_status mts_adjoint_equilibrium(mts_body *b, int64_t max_iters, do
     MTS_TRY(adjoint_norm2(b, part, nrm));
     MTS_CUDA(cudaMemcpyAsync(h, nrm, 8, cudaMemcpyDeviceToHost, st));
     MTS_CUDA(cudaStreamSynchronize(st));
-    const double n0 = h[0];
+    double n0 = h[0];
     int64_t it = 0;
-    bool done = n0 == 0.0 && b->adj_force_seed[0] == 0.0 && b->adj_force_seed[1] == 0.0 &&
-                b->adj_force_seed[2] == 0.0;
+    const bool force_seed = b->adj_force_seed[0] != 0.0 || b->adj_force_seed[1] != 0.0 ||
+                            b->adj_force_seed[2] != 0.0;
+    bool done = n0 == 0.0 && !force_seed;
     while (!done && it < max_iters) {
         MTS_TRY(adjoint_substep(b, 0, it == 0));
         ++it;
+        if (it == 1 && force_seed) {
+            // an end-force seed enters through the first transposed kick: the
+            // reference norm includes what it put into (u-bar, v-bar)
+            MTS_TRY(adjoint_norm2(b, part, nrm));
+            MTS_CUDA(cudaMemcpyAsync(h, nrm, 8, cudaMemcpyDeviceToHost, st));
+            MTS_CUDA(cudaStreamSynchronize(st));
+            n0 = std::max(n0, h[0]);
+        }
         if (it % 8 == 0 || it == max_iters) {
             MTS_TRY(adjoint_norm2(b, part, nrm));
             MTS_CUDA(cudaMemcpyAsync(h, nrm, 8, cudaMemcpyDeviceToHost, st));
@@ -1349,7 +1358,7 @@ extern "C" mts_status mts_adjoint_equilibrium(mts_body *b, int64_t max_iters, do
                           (long long)it);
                 return MTS_ERR_NONFINITE;
             }
-            done = h[0] <= tol * tol * (n0 > 0.0 ? n0 : h[0]);
+            done = h[0] <= tol * tol * n0;
         }
     }
     double th[8];

@@ -248,3 +248,23 @@ def test_equilibrium_adjoint_matches_differences_of_equilibria(ctx):
     tm[0] -= h
     fd = (objective(tp)[0] - objective(tm)[0]) / (2 * h)
     assert abs(th[0] - fd) <= 1e-5 * abs(fd), (th[0], fd)
+
+
+def test_equilibrium_adjoint_with_end_force_seed_only(ctx):
+    """A seed on the end force alone (nothing in u-bar, v-bar at the start)
+    converges and agrees with the unrolled reverse of the same relaxed step."""
+    case = B.bar2d(nx=24, ny=6, n_slow=4, eta=1e3)
+    gb = M.body_from_case(ctx, case, M.FP64)
+    ck = gb.save_state()
+    p = dict(ramp=0.25, ke_tol=1e-22, ke_ref=case.plan.ke_ref, max_substeps=60000)
+    k = gb.advance_slow_step(**p).substeps
+    gb.adjoint_enable(k)
+    gb.adjoint_seed(force_bar=[1.0, 0.0])
+    th_eq, iters = gb.adjoint_equilibrium(max_iters=200000, tol=1e-10)
+    assert iters > 8
+    gb.adjoint_reset()
+    gb.adjoint_seed(force_bar=[1.0, 0.0])
+    gb.load_state(ck)
+    th_un = gb.adjoint_slow_step(k, **p)
+    assert th_un[0] != 0
+    assert abs(th_eq[0] - th_un[0]) <= 1e-5 * abs(th_un[0]), (th_eq[0], th_un[0])
