@@ -91,7 +91,7 @@ void body_free(mts_body *b) {
                      (void **)&b->halo_idx, (void **)&b->halo_x, (void **)&b->lself, (void **)&b->lell,
                      (void **)&b->lell_off, (void **)&b->tile_w, (void **)&b->pair_slot,
                      (void **)&b->kpad_ab, (void **)&b->kpad_g, (void **)&b->bperm,
-                     (void **)&b->bflags, (void **)&b->qflux, (void **)&b->tape_u, (void **)&b->tape_cp,
+                     (void **)&b->bflags, (void **)&b->grp_cons, (void **)&b->qflux, (void **)&b->tape_u, (void **)&b->tape_cp,
                      (void **)&b->tape_dt, (void **)&b->tape_c, (void **)&b->adj_u,
                      (void **)&b->adj_v, (void **)&b->adj_cp, (void **)&b->adj_c,
                      (void **)&b->adj_a, (void **)&b->adj_G, (void **)&b->adj_theta,

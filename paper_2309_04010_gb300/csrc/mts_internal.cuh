@@ -113,6 +113,7 @@ struct Args {
     const int32_t *grp_lvl;      // group -> first level, n_groups + 1
     const int32_t *touch_start;  // group x NB: first block-sorted position of a touched block
     const int32_t *touch_cnt;
+    const uint8_t *grp_cons;     // group -> 1 if a touched particle has a constrained axis
     const int32_t *bperm;        // block-sorted position -> particle
     const uint8_t *bflags;       // flags in block-sorted order (wide layout)
     int transpose;               // damping: apply the transposed pair updates (adjoint)
@@ -192,6 +193,7 @@ struct mts_body {
     long long *lvl_pair;
     int32_t *grp_lvl;
     int32_t *touch_start, *touch_cnt;
+    uint8_t *grp_cons;           // blocks layout: group touches a constrained particle
     int32_t *bperm;           // block-sorted position -> particle (identity for BLOCKS)
     uint8_t *bflags;          // flags in block-sorted order (WIDE only)
     long long n_groups, n_levels;

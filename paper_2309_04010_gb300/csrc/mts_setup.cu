@@ -818,7 +818,7 @@ void free_damping(mts_body *b) {
                      (void **)&b->pair_g, (void **)&b->lvl_pair, (void **)&b->grp_lvl,
                      (void **)&b->touch_start, (void **)&b->touch_cnt, (void **)&b->pair_slot,
                      (void **)&b->kpad_ab, (void **)&b->kpad_g, (void **)&b->bperm,
-                     (void **)&b->bflags};
+                     (void **)&b->bflags, (void **)&b->grp_cons};
     for (void **pp : ptrs) {
         dfree(b->ctx, *pp);
         *pp = nullptr;
@@ -1063,6 +1063,8 @@ mts_status build_damping(mts_body *b, Tmp &tmp, cudaStream_t st, const int *cell
                                                   b->pair_slot, b->kpad_ab, bps);
         k_fill_slot_g<R><<<grid_for(m), TPB, 0, st>>>((const R *)b->pair_g, b->pair_slot, m,
                                                        (R *)b->kpad_g);
+        MTS_TRY(dalloc_t(ctx, &b->grp_cons, ngg));
+        MTS_CUDA(cudaMemsetAsync(b->grp_cons, 0, ngg, st));   // flags start at zero
     }
     int *dcol = tmp.get<int>(16);
     NEED(dcol);

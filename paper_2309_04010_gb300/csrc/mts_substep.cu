@@ -281,18 +281,17 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
 
 // --------------------------------------------------------------------- K_C
 // shared-memory layout of one damping warp: velocities of the 2^d touched
-// blocks, the owner group's pair coefficients and packed local indices, its
-// level table, the touched particles' flags
+// blocks, the owner group's pair coefficients and pair words (the words carry
+// the constrained axes, so no flags are staged)
 template <class R, int D>
 struct DampSmem {
     // velocities (+1 dummy slot, padded to 16 bytes), 32 slots per level of
-    // coefficients and pair words (16-byte aligned for cp.async), flags (+1)
+    // coefficients and pair words (16-byte aligned for cp.async)
     __host__ __device__ static size_t vbytes(int mb) {
         return (((size_t)((1 << D) * mb + 1) * Pad<D>::v * sizeof(R)) + 15) & ~size_t(15);
     }
     __host__ __device__ static size_t bytes(int mb, int maxl) {
-        size_t b = vbytes(mb) + (size_t)32 * maxl * sizeof(R) + (size_t)32 * maxl * 4 +
-                   (size_t)(1 << D) * mb + 1;
+        size_t b = vbytes(mb) + (size_t)32 * maxl * sizeof(R) + (size_t)32 * maxl * 4;
         return (b + 15) & ~size_t(15);
     }
 };
@@ -351,31 +350,76 @@ __device__ __forceinline__ void damp_apply(R *pa, R *pb, R g, const uint8_t *sf,
     st_vec<R, P>(pb, vb);
 }
 
+// The free-free branch of damp_apply alone (no lane of the level holds a
+// constrained pair): the same arithmetic, nothing else on the level's chain.
 template <class R, int D>
-__device__ __forceinline__ void damp_pair(uint32_t w, R g, unsigned char *svb, const uint8_t *sf,
-                                          R hcim, bool transpose) {
-    constexpr int BPS = Pad<D>::v * (int)sizeof(R);
-    const uint32_t oa = w & 0xffffu, ob = w >> 16;
-    damp_apply<R, D>(reinterpret_cast<R *>(svb + oa), reinterpret_cast<R *>(svb + ob), g, sf,
-                     oa / BPS, ob / BPS, hcim, transpose);
+__device__ __forceinline__ void damp_pair_free(uint32_t w, R g, unsigned char *svb, R hcim) {
+    constexpr int P = Pad<D>::v;
+    R *pa = reinterpret_cast<R *>(svb + (w & 0xffffu));
+    R *pb = reinterpret_cast<R *>(svb + (w >> 16));
+    R va[P], vb[P];
+    ld_vec<R, P>(va, pa);
+    ld_vec<R, P>(vb, pb);
+    const R xm = hcim * g;
+    const R f2 = fast_div<R>(xm, R(1) + R(2) * xm);
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        const R d = va[q] - vb[q];
+        va[q] -= f2 * d;
+        vb[q] += f2 * d;
+    }
+    st_vec<R, P>(pa, va);
+    st_vec<R, P>(pb, vb);
+}
+
+// damp_apply for the warp-per-group kernel, where the pair word carries the
+// constrained axes of both particles in the low three bits of each byte
+// offset (velocity slots are at least 8 bytes, so those bits are free; they
+// are zero for a free pair).  Every lane of a level runs the same code: a
+// free pair takes ca = cb = f2 and the d form, exactly the free-free branch.
+template <class R, int D>
+__device__ __forceinline__ void damp_pair_coded(uint32_t w, R g, unsigned char *svb, R hcim,
+                                                bool transpose) {
+    constexpr int P = Pad<D>::v;
+    const uint32_t fa = w & 7u, fb = (w >> 16) & 7u;
+    R *pa = reinterpret_cast<R *>(svb + ((w & 0xffffu) & ~7u));
+    R *pb = reinterpret_cast<R *>(svb + ((w >> 16) & ~7u));
+    R va[P], vb[P];
+    ld_vec<R, P>(va, pa);
+    ld_vec<R, P>(vb, pb);
+    const bool cons = g < R(0);
+    const R xm = hcim * (cons ? -g : g);
+    const R f2 = fast_div<R>(xm, R(1) + R(2) * xm);
+    const R f1 = fast_div<R>(xm, R(1) + xm);
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+        const bool a_free = !((fa >> q) & 1u), b_free = !((fb >> q) & 1u);
+        const R ca = a_free ? (b_free ? f2 : f1) : R(0);
+        const R cb = b_free ? (a_free ? f2 : f1) : R(0);
+        if (transpose && cons) {    // the transposed 2x2 update (adjoint sweep)
+            const R t = ca * va[q] - cb * vb[q];
+            va[q] -= t;
+            vb[q] += t;
+        } else {
+            const R d = va[q] - vb[q];
+            va[q] -= ca * d;
+            vb[q] += cb * d;
+        }
+    }
+    st_vec<R, P>(pa, va);
+    st_vec<R, P>(pb, vb);
 }
 
 template <class R, int D>
 __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long long g_end,
                                              int mode) {
-    if (A.ctrl->done) return;
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int P = Pad<D>::v;
     constexpr int NB = 1 << D;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long g = g_begin + (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     if (g >= g_end) return;
-    const int mb = A.mb;
-    unsigned char *base = smem + (size_t)warp * DampSmem<R, D>::bytes(mb, A.max_group_levels);
-    R *sv = reinterpret_cast<R *>(base);                 // NB * mb slots + 1 dummy slot
-    R *sg = reinterpret_cast<R *>(base + DampSmem<R, D>::vbytes(mb));
-    uint32_t *sab = reinterpret_cast<uint32_t *>(sg + 32 * A.max_group_levels);
-    uint8_t *sf = reinterpret_cast<uint8_t *>(sab + 32 * A.max_group_levels);
+    // every scalar the group needs, issued together (one memory latency)
     int ts[NB], tc[NB];
 #pragma unroll
     for (int e = 0; e < NB; ++e) {
@@ -383,7 +427,16 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
         tc[e] = __ldg(A.touch_cnt + g * NB + e);
     }
     const int l0 = __ldg(A.grp_lvl + g), l1 = __ldg(A.grp_lvl + g + 1);
+    const bool cons = __ldg(A.grp_cons + g) != 0;
+    const int done = A.ctrl->done;
+    const double dt = A.ctrl->dt;
+    if (done) return;
     const int nl = l1 - l0;
+    const int mb = A.mb;
+    unsigned char *base = smem + (size_t)warp * DampSmem<R, D>::bytes(mb, A.max_group_levels);
+    R *sv = reinterpret_cast<R *>(base);                 // NB * mb slots + 1 dummy slot
+    R *sg = reinterpret_cast<R *>(base + DampSmem<R, D>::vbytes(mb));
+    uint32_t *sab = reinterpret_cast<uint32_t *>(sg + 32 * A.max_group_levels);
     // asynchronous staging: velocities of the touched blocks, and the group's
     // padded level slots (contiguous, 16-byte aligned: 32 slots per level)
 #pragma unroll
@@ -395,11 +448,7 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     for (int k = 4 * lane; k < 32 * nl; k += 128) cp_async(sab + k, gab + k, 16);
     constexpr int GPER = 16 / (int)sizeof(R);
     for (int k = GPER * lane; k < 32 * nl; k += 32 * GPER) cp_async(sg + k, gg + k, 16);
-#pragma unroll
-    for (int e = 0; e < NB; ++e)
-        for (int t = lane; t < tc[e]; t += 32) sf[e * mb + t] = A.flags[ts[e] + t];
     if (lane == 0) {
-        sf[NB * mb] = 0;
         R z[P];
 #pragma unroll
         for (int q = 0; q < P; ++q) z[q] = R(0);
@@ -408,9 +457,17 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     cp_async_wait_all();
     __syncwarp();
     const R im = (R)(1.0 / A.mass);
-    const R hcim = (R)(0.5 * A.ctrl->dt) * A.eta * im;   // (dt/2) eta / m
+    const R hcim = (R)(0.5 * dt) * A.eta * im;   // (dt/2) eta / m
     const bool tr = A.transpose != 0;
     unsigned char *svb = reinterpret_cast<unsigned char *>(sv);
+    // a group that touches no constrained particle has no negative coefficient;
+    // in one that does, a level without a constrained pair takes the free code
+    auto level = [&](uint32_t w, R gc) {
+        if (cons && __any_sync(0xffffffffu, gc < R(0)))
+            damp_pair_coded<R, D>(w, gc, svb, hcim, tr);
+        else
+            damp_pair_free<R, D>(w, gc, svb, hcim);
+    };
     if (nl > 0 && (mode & 1)) {
         uint32_t wn = sab[lane];
         R gn = sg[lane];
@@ -421,7 +478,7 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
                 wn = sab[32 * (l + 1) + lane];
                 gn = sg[32 * (l + 1) + lane];
             }
-            damp_pair<R, D>(w, gc, svb, sf, hcim, tr);
+            level(w, gc);
             __syncwarp();
         }
     }
@@ -435,7 +492,7 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
                 wn = sab[32 * (l - 1) + lane];
                 gn = sg[32 * (l - 1) + lane];
             }
-            damp_pair<R, D>(w, gc, svb, sf, hcim, tr);
+            level(w, gc);
             __syncwarp();
         }
     }
@@ -599,6 +656,31 @@ __global__ void k_gather_flags(const uint8_t *flags, const int32_t *bperm, long 
                                uint8_t *bflags) {
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s < n) bflags[s] = flags[bperm[s]];
+}
+
+// blocks layout: does an owner group touch a particle with a constrained axis
+// (its particles are the touched blocks' contiguous ranges)
+__global__ void k_group_cons(const int32_t *tstart, const int32_t *tcnt, long long ng, int nb,
+                             const uint8_t *flags, int fixmask, uint8_t *cons) {
+    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    uint8_t any = 0;
+    for (int e = 0; e < nb; ++e) {
+        const long long s0 = tstart[g * nb + e];
+        for (int t = 0; t < tcnt[g * nb + e]; ++t) any |= flags[s0 + t] & fixmask;
+    }
+    cons[g] = any != 0;
+}
+
+// blocks layout: the constrained axes of both particles in the low three bits
+// of each byte offset of the padded pair word (low half: pair_a)
+__global__ void k_pair_fixword(uint32_t *kab, const long long *slot, const int32_t *pa,
+                               const int32_t *pb, long long m, const uint8_t *flags, int fixmask) {
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    const uint32_t fa = flags[pa[p]] & fixmask, fb = flags[pb[p]] & fixmask;
+    uint32_t &w = kab[slot[p]];
+    w = (w & ~(7u | (7u << 16))) | fa | (fb << 16);
 }
 
 // pair coefficients: negative when either particle has a constrained axis
@@ -1281,6 +1363,7 @@ Args<R> make_args(mts_body *b) {
     A.pair_g = (const R *)b->kpad_g;
     A.lvl_pair = b->lvl_pair;
     A.grp_lvl = b->grp_lvl;
+    A.grp_cons = b->grp_cons;
     A.touch_start = b->touch_start;
     A.touch_cnt = b->touch_cnt;
     A.bperm = b->bperm;
@@ -1542,6 +1625,14 @@ size_t damp_wide_smem(const mts_body *b) {
 }
 
 mts_status update_pair_fixbits(mts_body *b) {
+    if (b->grp_cons && b->n_groups > 0)
+        k_group_cons<<<(unsigned)((b->n_groups + 255) / 256), 256, 0, b->ctx->stream>>>(
+            b->touch_start, b->touch_cnt, b->n_groups, 1 << b->dim, b->flags, (1 << b->dim) - 1,
+            b->grp_cons);
+    if (b->grp_cons && b->npairs > 0)
+        k_pair_fixword<<<(unsigned)((b->npairs + 255) / 256), 256, 0, b->ctx->stream>>>(
+            b->kpad_ab, b->pair_slot, b->pair_a, b->pair_b, b->npairs, b->flags,
+            (1 << b->dim) - 1);
     if (b->bflags)
         k_gather_flags<<<(unsigned)((b->n + 255) / 256), 256, 0, b->ctx->stream>>>(
             b->flags, b->bperm, b->n, b->bflags);
