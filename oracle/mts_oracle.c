@@ -408,21 +408,24 @@ static int build_b0(ob_body *b) {
 /*   > 2h; OB_WHOLE_AXIS = the axis is not blocked); pair (a<b) is owned */
 /*   by the componentwise-min block of its two particles; block colour  */
 /*   = parity bits of the owner block; inside an owner block its pairs, */
-/*   visited by offset class (the sign-folded cell offset) and then     */
-/*   ascending (a,b), take the smallest sub-colour unused at a and at b */
-/*   that holds fewer than level_cap pairs so far (greedy; level_cap 0  */
-/*   = no cap).  Sequential order: colour, owner block Morton key,      */
-/*   sub-colour, a, b.  Pairs of one (colour, sub-colour) touch         */
-/*   disjoint particles.                                                */
+/*   visited by descending offset class (the sign-folded cell offset),  */
+/*   then ascending (a,b), take the smallest sub-colour unused at a and */
+/*   at b that holds fewer than level_cap pairs so far (greedy;         */
+/*   level_cap 0 = no cap).  Sequential order: colour, owner block      */
+/*   Morton key, sub-colour, a, b.  Pairs of one (colour, sub-colour)   */
+/*   touch disjoint particles.  (Descending classes visit the longest   */
+/*   offsets first, which keeps the largest groups near the degree      */
+/*   bound on levels.)                                                  */
 /* ------------------------------------------------------------------ */
 typedef struct { int32_t col; int32_t sub; uint64_t key; int32_t cls; int32_t a, b; } pair_rec;
 
-/* owner block, then offset class, then (a, b): the order the greedy visits */
+/* owner block, then offset class (descending), then (a, b): the order the
+ * greedy visits */
 static int cmp_pair_owner(const void *x, const void *y) {
     const pair_rec *p = x, *q = y;
     if (p->col != q->col) return p->col < q->col ? -1 : 1;
     if (p->key != q->key) return p->key < q->key ? -1 : 1;
-    if (p->cls != q->cls) return p->cls < q->cls ? -1 : 1;
+    if (p->cls != q->cls) return p->cls > q->cls ? -1 : 1;
     if (p->a != q->a) return p->a < q->a ? -1 : 1;
     return (p->b > q->b) - (p->b < q->b);
 }

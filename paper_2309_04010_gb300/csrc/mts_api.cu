@@ -8,6 +8,7 @@
 // substeps after the stop inside a chunk are no-ops.  The host reads the
 // control block back once per chunk.
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
@@ -169,8 +170,7 @@ mts_status get_rank_host(mts_body *b, std::vector<long long> &rank) {
 // drift kernel's last block sets the condition to "not done".  No host round
 // trip and no work after the stop.  (Event-record nodes are not allowed in a
 // conditional body, so profiled runs use capture_chunk instead.)
-mts_status capture_loop(mts_body *b) {
-    if (b->graph && !b->graph_dirty && b->graph_is_loop) return MTS_OK;
+mts_status capture_loop_once(mts_body *b) {
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -204,12 +204,14 @@ mts_status capture_loop(mts_body *b) {
     }
     b->cond = h;
     b->use_cond = 1;
+    b->pdl_now = b->ctx->pdl;
     long long ndamp = 0;
     mts_status s = launch_stress(b);
     if (s == MTS_OK) s = launch_force(b);
     if (s == MTS_OK) s = launch_damping(b, &ndamp);
     if (s == MTS_OK) s = launch_drift(b);
     b->use_cond = 0;
+    b->pdl_now = false;
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(st, &captured);
     if (s != MTS_OK || e != cudaSuccess) {
@@ -226,10 +228,24 @@ mts_status capture_loop(mts_body *b) {
     return MTS_OK;
 }
 
-mts_status capture_chunk(mts_body *b, int chunk) {
-    if (b->graph && !b->graph_dirty && !b->graph_is_loop && b->graph_chunk == chunk &&
-        b->graph_prof_stage == b->prof_stage)
-        return MTS_OK;
+// A capture that fails with programmatic dependent launch enabled is retried
+// once without it (and the context keeps ordinary launches from then on).
+template <class F>
+mts_status with_chain_fallback(mts_ctx *ctx, F capture) {
+    mts_status s = capture();
+    if (s != MTS_OK && ctx->pdl) {
+        ctx->pdl = false;
+        s = capture();
+    }
+    return s;
+}
+
+mts_status capture_loop(mts_body *b) {
+    if (b->graph && !b->graph_dirty && b->graph_is_loop) return MTS_OK;
+    return with_chain_fallback(b->ctx, [&] { return capture_loop_once(b); });
+}
+
+mts_status capture_chunk_once(mts_body *b, int chunk) {
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -254,6 +270,7 @@ mts_status capture_chunk(mts_body *b, int chunk) {
             if (e != cudaSuccess) s = cuda_fail(e, "cudaEventRecordWithFlags");
         }
     };
+    b->pdl_now = b->ctx->pdl && ps == 0;
     for (int k = 0; k < chunk && s == MTS_OK; ++k) {
         mark(k, 1, 0);
         s = launch_stress(b);
@@ -268,6 +285,7 @@ mts_status capture_chunk(mts_body *b, int chunk) {
         if (s == MTS_OK) s = launch_drift(b);
         mark(k, 4, 1);
     }
+    b->pdl_now = false;
     b->launches_per_substep = 3 + ndamp;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &g);
@@ -284,6 +302,13 @@ mts_status capture_chunk(mts_body *b, int chunk) {
     b->graph_is_loop = false;
     b->graph_dirty = false;
     return MTS_OK;
+}
+
+mts_status capture_chunk(mts_body *b, int chunk) {
+    if (b->graph && !b->graph_dirty && !b->graph_is_loop && b->graph_chunk == chunk &&
+        b->graph_prof_stage == b->prof_stage)
+        return MTS_OK;
+    return with_chain_fallback(b->ctx, [&] { return capture_chunk_once(b, chunk); });
 }
 
 // Validation, load jump and diffusion step of one slow step (before its substeps).
@@ -363,11 +388,8 @@ mts_status slow_step_report(mts_body *b, mts_step_report *rep, long long launche
 // One graph for a batch: a conditional WHILE node per body, no edges between
 // them; each body graph is that body's substep, captured with the node's own
 // conditional handle (the body's drift kernel ends only its own loop).
-mts_status capture_batch(mts_batch *bt) {
+mts_status capture_batch_once(mts_batch *bt) {
     const int nb = (int)bt->bodies.size();
-    bool fresh = bt->graph != nullptr && (int)bt->gens.size() == nb;
-    for (int i = 0; fresh && i < nb; ++i) fresh = bt->gens[i] == bt->bodies[i]->graph_gen;
-    if (fresh) return MTS_OK;
     if (bt->graph) {
         cudaGraphExecDestroy(bt->graph);
         bt->graph = nullptr;
@@ -397,12 +419,14 @@ mts_status capture_batch(mts_batch *bt) {
         const cudaGraphConditionalHandle own = b->cond;
         b->cond = h;
         b->use_cond = 1;
+        b->pdl_now = b->ctx->pdl;
         long long ndamp = 0;
         s = launch_stress(b);
         if (s == MTS_OK) s = launch_force(b);
         if (s == MTS_OK) s = launch_damping(b, &ndamp);
         if (s == MTS_OK) s = launch_drift(b);
         b->use_cond = 0;
+        b->pdl_now = false;
         b->cond = own;
         cudaGraph_t captured = nullptr;
         e = cudaStreamEndCapture(st, &captured);
@@ -419,6 +443,14 @@ mts_status capture_batch(mts_batch *bt) {
     bt->gens.resize(nb);
     for (int i = 0; i < nb; ++i) bt->gens[i] = bt->bodies[i]->graph_gen;
     return MTS_OK;
+}
+
+mts_status capture_batch(mts_batch *bt) {
+    const int nb = (int)bt->bodies.size();
+    bool fresh = bt->graph != nullptr && (int)bt->gens.size() == nb;
+    for (int i = 0; fresh && i < nb; ++i) fresh = bt->gens[i] == bt->bodies[i]->graph_gen;
+    if (fresh) return MTS_OK;
+    return with_chain_fallback(bt->ctx, [&] { return capture_batch_once(bt); });
 }
 
 bool valid_field(int f) { return f >= MTS_F_U && f <= MTS_F_ACC; }
@@ -450,6 +482,7 @@ mts_status mts_ctx_create(int device, void *cuda_stream, const mts_allocator *al
     mts_ctx *c = new (std::nothrow) mts_ctx();
     if (!c) return MTS_ERR_OOM;
     c->device = device;
+    c->pdl = std::getenv("MTS_NO_CHAIN_LAUNCH") == nullptr;
     c->alloc.custom = alloc != nullptr;
     if (alloc) c->alloc.a = *alloc;
     if (cuda_stream) {

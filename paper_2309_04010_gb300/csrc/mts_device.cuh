@@ -37,6 +37,15 @@ __device__ __forceinline__ void ldg_vec(R (&o)[N], const R *p) {
     }
 }
 
+// Programmatic dependent launch (sm_90+): chain_trigger lets the next kernel
+// of a substep chain be scheduled once every block of this one has started;
+// chain_wait blocks until the previous kernel of the chain has completed and
+// its writes are visible.  Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void chain_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <class R, int N>
 __device__ __forceinline__ void ld_vec(R (&o)[N], const R *p) {
     if constexpr (sizeof(R) == 4 && N == 4) {

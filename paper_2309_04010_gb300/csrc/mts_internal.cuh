@@ -155,6 +155,7 @@ struct mts_ctx {
     int device;
     cudaStream_t stream;
     bool own_stream;
+    bool pdl;             // programmatic dependent launch in captured substep chains
     mts::Alloc alloc;
     std::vector<void *> live;
 };
@@ -167,6 +168,7 @@ struct mts_body {
     double dx, h, V, cut2;
     int blk_shift;
     int damp_req;         // requested mts_damp_layout
+    bool pdl_now;         // capturing the substep chain with programmatic launches
     int damp_layout;      // resolved: MTS_DAMP_BLOCKS or MTS_DAMP_WIDE
     int ax_shift[3];      // owner-block width per axis (kWholeAxis = unblocked)
     int level_cap;        // pairs per sub-colour of one group (0 = none)

@@ -454,7 +454,8 @@ __global__ void k_greedy(const long long *gstart, long long g0, long long g1, lo
     nsub[g] = maxc + 1;
 }
 
-// offset class: cell(b) - cell(a), sign-folded, base (2R+1) digits
+// offset class: cell(b) - cell(a), sign-folded, base (2R+1) digits; the greedy
+// visits a group's classes in descending order
 __global__ void k_pair_class(const int32_t *pa, const int32_t *pb, const long long *gscan,
                              long long m, const int *cell, int dim, int R,
                              unsigned long long *key) {
@@ -468,7 +469,8 @@ __global__ void k_pair_class(const int32_t *pa, const int32_t *pb, const long lo
         if (o[k] != 0) sg = o[k] > 0 ? 1 : -1;
     long long c = 0, base = 2 * R + 1;
     for (int k = dim - 1; k >= 0; --k) c = c * base + (sg * o[k] + R);
-    key[p] = ((unsigned long long)(gscan[p] - 1) << 16) | (unsigned long long)c;
+    // classes in descending order within a group (c < 2^16)
+    key[p] = ((unsigned long long)(gscan[p] - 1) << 16) | (unsigned long long)(0xffff - c);
 }
 
 template <class T>
@@ -933,6 +935,10 @@ mts_status build_damping(mts_body *b, Tmp &tmp, cudaStream_t st, const int *cell
 
     // visit order of the greedy: owner group, offset class, then (a, b)
     const int Rr = (int)std::floor(2.0 * b->h / b->dx) + 1;
+    if (std::pow(2.0 * Rr + 1.0, (double)D) > 65536.0) {
+        set_error("smoothing length of %.3g cells: offset classes exceed 16 bits", b->h / b->dx);
+        return MTS_ERR_INVALID_ARG;
+    }
     int32_t *pa2 = tmp.get<int32_t>(mm), *pb2 = tmp.get<int32_t>(mm);
     long long *ord3 = tmp.get<long long>(mm);
     NEED(pa2); NEED(pb2); NEED(ord3);

@@ -710,7 +710,8 @@ def test_colouring_matches_independent_greedy(dim, counts):
             if b > a:
                 owner = np.minimum(blk[a], blk[b])
                 col = sum(int(owner[k] & 1) << k for k in range(dim))
-                recs.append([col, mkey(owner), oclass(a, int(b)), a, int(b)])
+                # classes visited in descending order
+                recs.append([col, mkey(owner), -oclass(a, int(b)), a, int(b)])
     recs.sort()
     recs = [[r[0], r[1], r[3], r[4]] for r in recs]
     used = {}
