@@ -49,10 +49,7 @@ __device__ __forceinline__ void compute_F(const Args<R> &A, const R *sX, const R
     const uint16_t *row = A.lell + A.lell_off[t] + threadIdx.x;
     const int w = A.tile_w[t];
     const R inv_h = A.inv_h, kcoef = A.kcoef;
-    for_each_neighbour(row, T, w, [&](int l) {
-        R xb[P], ub[P];
-        ld_vec<R, P>(xb, sX + l * P);
-        ld_vec<R, P>(ub, sU + l * P);
+    auto accumulate = [&](const R (&xb)[P], const R (&ub)[P]) {
         R d[D], r2 = R(0);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -67,6 +64,12 @@ __device__ __forceinline__ void compute_F(const Args<R> &A, const R *sX, const R
 #pragma unroll
             for (int c = 0; c < D; ++c) G[r][c] += du * d[c];
         }
+    };
+    for_each_neighbour(row, T, w, [&](int l) {
+        R xb[P], ub[P];
+        ld_vec<R, P>(xb, sX + l * P);
+        ld_vec<R, P>(ub, sU + l * P);
+        accumulate(xb, ub);
     });
     R B[D][D];
     ldg_mat<R, D>(B, A.B0 + i * MatS<D>::v);
@@ -100,6 +103,8 @@ __device__ __forceinline__ void unscale_F(const Args<R> &A, R (&F)[3][3]) {
 // --------------------------------------------------------------------- K_A
 template <class R, int D, int MAT>
 __global__ void __launch_bounds__(256) k_stress(Args<R> A) {
+    chain_trigger();
+    chain_wait();
     if (A.ctrl->done) return;
     constexpr int P = Pad<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -163,6 +168,8 @@ __global__ void __launch_bounds__(256) k_stress(Args<R> A) {
 // --------------------------------------------------------------------- K_B
 template <class R, int D>
 __global__ void __launch_bounds__(256) k_force(Args<R> A) {
+    chain_trigger();
+    chain_wait();
     if (A.ctrl->done) return;
     constexpr int P = Pad<D>::v;
     constexpr int MS = MatS<D>::v;
@@ -204,8 +211,7 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
         const uint16_t *row = A.lell + A.lell_off[t] + threadIdx.x;
         const int w = A.tile_w[t];
         const R inv_h = A.inv_h, kcoef = A.kcoef;
-        for_each_neighbour(row, T, w, [&](int l) {
-            R q[12];
+        auto load_rec = [&](int l, R (&q)[12]) {
             if constexpr (D == 2) {
                 ld_vec<R, 2>(*reinterpret_cast<R(*)[2]>(q), sX + l * 2);
                 ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(q + 3), sP + l * 4);
@@ -214,6 +220,8 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
                 ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(q + 4), sP + l * 12 + 4);
                 ld_vec<R, 4>(*reinterpret_cast<R(*)[4]>(q + 8), sP + l * 12 + 8);
             }
+        };
+        auto accumulate = [&](const R (&q)[12]) {
             R d[D], r2 = R(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
@@ -234,6 +242,11 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
                 for (int c = 0; c < D; ++c) sum += q[3 + D * r + c] * d[c];
                 acc[r] += sum;
             }
+        };
+        for_each_neighbour(row, T, w, [&](int l) {
+            R q[12];
+            load_rec(l, q);
+            accumulate(q);
         });
 #pragma unroll
         for (int r = 0; r < D; ++r)
@@ -418,6 +431,7 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     constexpr int NB = 1 << D;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long g = g_begin + (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    chain_trigger();
     if (g >= g_end) return;
     // every scalar the group needs, issued together (one memory latency)
     int ts[NB], tc[NB];
@@ -428,26 +442,32 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     }
     const int l0 = __ldg(A.grp_lvl + g), l1 = __ldg(A.grp_lvl + g + 1);
     const bool cons = __ldg(A.grp_cons + g) != 0;
-    const int done = A.ctrl->done;
-    const double dt = A.ctrl->dt;
-    if (done) return;
     const int nl = l1 - l0;
     const int mb = A.mb;
     unsigned char *base = smem + (size_t)warp * DampSmem<R, D>::bytes(mb, A.max_group_levels);
     R *sv = reinterpret_cast<R *>(base);                 // NB * mb slots + 1 dummy slot
     R *sg = reinterpret_cast<R *>(base + DampSmem<R, D>::vbytes(mb));
     uint32_t *sab = reinterpret_cast<uint32_t *>(sg + 32 * A.max_group_levels);
-    // asynchronous staging: velocities of the touched blocks, and the group's
-    // padded level slots (contiguous, 16-byte aligned: 32 slots per level)
-#pragma unroll
-    for (int e = 0; e < NB; ++e)
-        for (int t = lane; t < tc[e]; t += 32)
-            cp_async_reals<R, P>(sv + (size_t)(e * mb + t) * P, A.v + (size_t)(ts[e] + t) * P);
+    // asynchronous staging of the group's padded level slots (contiguous,
+    // 16-byte aligned: 32 slots per level; set-up data, so it may overlap the
+    // previous kernel of the chain), then, once that kernel has completed, of
+    // the touched blocks' velocities
     const uint32_t *gab = A.pair_ab + 32LL * l0;
     const R *gg = A.pair_g + 32LL * l0;
     for (int k = 4 * lane; k < 32 * nl; k += 128) cp_async(sab + k, gab + k, 16);
     constexpr int GPER = 16 / (int)sizeof(R);
     for (int k = GPER * lane; k < 32 * nl; k += 32 * GPER) cp_async(sg + k, gg + k, 16);
+    chain_wait();
+    const int done = A.ctrl->done;
+    const double dt = A.ctrl->dt;
+    if (done) {
+        cp_async_wait_all();
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < NB; ++e)
+        for (int t = lane; t < tc[e]; t += 32)
+            cp_async_reals<R, P>(sv + (size_t)(e * mb + t) * P, A.v + (size_t)(ts[e] + t) * P);
     if (lane == 0) {
         R z[P];
 #pragma unroll
@@ -563,6 +583,8 @@ __device__ __forceinline__ void wide_sweep(bool fwd, int nl, const int32_t *slv,
 
 template <class R, int D>
 __global__ void __launch_bounds__(kWideThreads) k_damp_wide(Args<R> A, long long g_begin, int mode) {
+    chain_trigger();
+    chain_wait();
     if (A.ctrl->done) return;
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int P = Pad<D>::v;
@@ -701,6 +723,8 @@ __global__ void k_pair_fixsign(R *kg, const long long *slot, const int32_t *pa, 
 // it inside ordinary graphs
 template <class R, int D, bool COND>
 __global__ void __launch_bounds__(kBlock) k_drift(Args<R> A) {
+    chain_trigger();
+    chain_wait();
     Control *C = A.ctrl;
     if (C->done) {
         // defensive: a loop iteration that starts after the stop ends the loop
@@ -1404,6 +1428,26 @@ template <class R, int D> size_t smem_damp(const mts_body *b) {
     return DampSmem<R, D>::bytes(b->mb, b->max_group_levels) * damp_warps<R, D>(b);
 }
 
+// Launch a kernel of the substep chain.  While a body captures its chain
+// (pdl_now), the launch allows programmatic dependent launch: the kernel's
+// blocks may be scheduled while the previous kernel drains and run their
+// set-up-data prologue; chain_wait() in the kernel orders everything else.
+template <typename... KP, typename... AP>
+cudaError_t launch_chain(mts_body *b, void (*k)(KP...), unsigned grid, unsigned block,
+                         size_t smem, AP &&...args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = b->ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = b->pdl_now ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<AP>(args)...);
+}
+
 template <class R, int D>
 mts_status stress_t(mts_body *b) {
     Args<R> A = make_args<R>(b);
@@ -1418,8 +1462,8 @@ mts_status stress_t(mts_body *b) {
 
 template <class R, int D>
 mts_status force_t(mts_body *b) {
-    k_force<R, D><<<(unsigned)b->ntiles, b->T, smem_force<R, D>(b), b->ctx->stream>>>(make_args<R>(b));
-    MTS_CUDA(cudaGetLastError());
+    MTS_CUDA(launch_chain(b, k_force<R, D>, (unsigned)b->ntiles, (unsigned)b->T,
+                          smem_force<R, D>(b), make_args<R>(b)));
     return MTS_OK;
 }
 
@@ -1436,12 +1480,12 @@ mts_status damping_run(mts_body *b, const Args<R> &A, long long *nlaunch) {
     auto launch = [&](int c, int mode) -> mts_status {
         const long long g0 = b->col_off[c], g1 = b->col_off[c + 1];
         if (wide) {
-            k_damp_wide<R, D><<<(unsigned)(g1 - g0), kWideThreads, smem, b->ctx->stream>>>(A, g0, mode);
+            MTS_CUDA(launch_chain(b, k_damp_wide<R, D>, (unsigned)(g1 - g0), (unsigned)kWideThreads,
+                                  smem, A, g0, mode));
         } else {
             const unsigned grid = (unsigned)((g1 - g0 + W - 1) / W);
-            k_damp<R, D><<<grid, W * 32, smem, b->ctx->stream>>>(A, g0, g1, mode);
+            MTS_CUDA(launch_chain(b, k_damp<R, D>, grid, (unsigned)(W * 32), smem, A, g0, g1, mode));
         }
-        MTS_CUDA(cudaGetLastError());
         if (nlaunch) ++*nlaunch;
         return MTS_OK;
     };
@@ -1519,10 +1563,11 @@ mts_status prepare_t(mts_body *b) {
 template <class R, int D>
 mts_status drift_t(mts_body *b) {
     if (b->use_cond)
-        k_drift<R, D, true><<<grid_of(b->n), kBlock, 0, b->ctx->stream>>>(make_args<R>(b));
+        MTS_CUDA(launch_chain(b, k_drift<R, D, true>, grid_of(b->n), (unsigned)kBlock, 0,
+                              make_args<R>(b)));
     else
-        k_drift<R, D, false><<<grid_of(b->n), kBlock, 0, b->ctx->stream>>>(make_args<R>(b));
-    MTS_CUDA(cudaGetLastError());
+        MTS_CUDA(launch_chain(b, k_drift<R, D, false>, grid_of(b->n), (unsigned)kBlock, 0,
+                              make_args<R>(b)));
     return MTS_OK;
 }
 
