@@ -86,7 +86,8 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every 20 ms; each line
+    is stamped with the host clock so a window can be selected afterwards."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -101,7 +102,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -110,9 +111,17 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
-    def stop(self):
+    def wait_first(self, timeout: float = 5.0):
+        """Block until the sampler has produced a line (so it covers what follows)."""
+        t_end = time.monotonic() + timeout
+        while self.proc is not None and not self.lines and time.monotonic() < t_end:
+            time.sleep(0.01)
+
+    def stop(self, windows):
+        """Summarise the samples of the first window (host monotonic times) that
+        holds at least 5 of them, else of the last window."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -121,22 +130,29 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.t.join(timeout=2)
-        sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                smax = float(parts[1])
-            except ValueError:
-                continue
-            for nm, val in zip(names, parts[4:8]):
-                if val.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = None
+        for label, (a, b) in windows:
+            sm, smax, reasons = [], None, set()
+            for ts, ln in self.lines:
+                if ts < a or ts > b:
+                    continue
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax = float(parts[1])
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[4:8]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+            out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                   "reasons": sorted(reasons), "samples": len(sm), "window": label}
+            if len(sm) >= 5:
+                break
+        return out
 
 
 def source_hash() -> str:
@@ -427,8 +443,10 @@ def run_ours(args, rank, world, local):
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
+    clocks.wait_first()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    t_timed0 = time.monotonic()
     e0.record(stream)
     substeps, launches = 0, 0
     reps = []
@@ -439,8 +457,8 @@ def run_ours(args, rank, world, local):
         reps.append(r)
     e1.record(stream)
     torch.cuda.synchronize()
+    t_timed1 = time.monotonic()
     ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
 
     # profiled replay: the next K slow steps with CUDA events recorded inside
     # the captured graph (host-checked chunks of 4 substeps) around each
@@ -456,6 +474,12 @@ def run_ours(args, rank, world, local):
         stage_ms[st] = stage_ms.get(st, 0.0) + r.prof_ms
         stage_n[st] = stage_n.get(st, 0) + r.prof_count
     gb.set_profiling(0)
+    torch.cuda.synchronize()
+    # clocks of the timed region; a region shorter than five samples is
+    # widened by the profiled replay of the same workload that follows it
+    clk = clocks.stop([("timed region", (t_timed0, t_timed1)),
+                       ("timed region and the profiled replay that follows",
+                        (t_timed0, time.monotonic()))])
     stage_avg = {k: stage_ms[k] / stage_n[k] for k in stage_ms if stage_n[k]}
     dom = max(stage_avg, key=stage_avg.get) if stage_avg else 2
     prof_ms, prof_n = stage_ms.get(dom, 0.0), stage_n.get(dom, 0)
