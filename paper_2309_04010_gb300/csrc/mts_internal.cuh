@@ -34,6 +34,17 @@ constexpr int kTipBit = 16;
 constexpr int kCHeldBit = 32;
 constexpr int kBlock = 256;  // threads per block of the per-particle kernels
 constexpr int kLevelCap = 32;  // pairs per damping level: one warp-wide pass
+
+// Shared-memory position of velocity slot s in the warp-per-group damping
+// kernel.  With 16-byte slots (FP32 3D), slots are permuted inside aligned
+// groups of eight (one 128-byte row of the 32 banks) so that the lattice-
+// regular slots of one level spread over the banks; other slot sizes keep
+// their order.  The slot area is padded to whole groups of eight (the dummy
+// slot of empty level entries is slot nb * mb).
+__host__ __device__ __forceinline__ int damp_slot_pos(int s, int slot_bytes) {
+    return slot_bytes == 16 ? (s ^ (((s >> 3) * 3) & 7)) : s;
+}
+__host__ __device__ __forceinline__ int damp_slot_count(int nb_mb) { return (nb_mb + 1 + 7) & ~7; }
 constexpr int kWholeAxis = 62; // owner-block shift of an unblocked axis
 constexpr int kWideThreads = 256;   // threads of the CTA-per-group damping kernel
 constexpr int kWideRing = 8;        // level buffers of its pair-data ring

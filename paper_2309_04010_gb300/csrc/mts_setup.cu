@@ -484,17 +484,77 @@ __global__ void k_scatter(const T *src, const long long *order, long long m, T *
 // slot words hold byte offsets (slot index * bytes per velocity slot) of the
 // two particles in the damping kernel's staged velocities
 __global__ void k_fill_slots(const unsigned long long *key2s, long long m, const int32_t *grp_lvl,
-                             const long long *lvl_pair, const uint32_t *ab, long long *slot,
-                             uint32_t *kab, int bps) {
+                             const long long *lvl_pair, const uint32_t *ab, const int8_t *lane,
+                             long long *slot, uint32_t *kab, int bps) {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= m) return;
     const long long g = (long long)(key2s[p] >> 8);
     const int s = (int)(key2s[p] & 255);
     const long long L = grp_lvl[g] + s;
-    const long long sl = 32 * L + (p - lvl_pair[L]);
+    const long long sl = 32 * L + lane[p];
     slot[p] = sl;
-    const uint32_t la = ab[p] & 0xffffu, lb = ab[p] >> 16;
+    const uint32_t la = (uint32_t)damp_slot_pos((int)(ab[p] & 0xffffu), bps);
+    const uint32_t lb = (uint32_t)damp_slot_pos((int)(ab[p] >> 16), bps);
     kab[sl] = (la * (uint32_t)bps) | ((lb * (uint32_t)bps) << 16);
+}
+
+// Lane of each pair inside its level (a level's pairs touch disjoint
+// particles, so any assignment gives the same result).  With 16-byte slots a
+// 128-bit shared access is served per quarter-warp, and two lanes of one
+// quarter that hit different slots of one 16-byte bank group conflict; the
+// pairs are placed, the most crowded bank groups first, in the quarter that
+// keeps the largest per-quarter count of their a and b bank groups lowest.
+// Other slot sizes keep the canonical order.
+__global__ void k_level_lanes(const long long *lvl_pair, long long nlev, const uint32_t *ab,
+                              int bps, int8_t *lane) {
+    const long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (L >= nlev) return;
+    const long long p0 = lvl_pair[L];
+    const int n = (int)(lvl_pair[L + 1] - p0);
+    if (bps != 16 || n <= 8 || n > 32) {
+        for (int k = 0; k < n; ++k) lane[p0 + k] = (int8_t)k;
+        return;
+    }
+    int ga[32], gb[32], ord[32];
+    int fa[8] = {0, 0, 0, 0, 0, 0, 0, 0}, fb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < n; ++k) {
+        ga[k] = damp_slot_pos((int)(ab[p0 + k] & 0xffffu), bps) & 7;
+        gb[k] = damp_slot_pos((int)(ab[p0 + k] >> 16), bps) & 7;
+        ++fa[ga[k]];
+        ++fb[gb[k]];
+    }
+    // visit order: descending fa[ga] + fb[gb], ties by canonical position
+    for (int k = 0; k < n; ++k) ord[k] = k;
+    for (int i = 1; i < n; ++i) {
+        const int x = ord[i], kx = fa[ga[x]] + fb[gb[x]];
+        int j = i - 1;
+        while (j >= 0 && fa[ga[ord[j]]] + fb[gb[ord[j]]] < kx) {
+            ord[j + 1] = ord[j];
+            --j;
+        }
+        ord[j + 1] = x;
+    }
+    int ca[4][8], cb[4][8], size[4] = {0, 0, 0, 0}, ma[4] = {0, 0, 0, 0}, mxb[4] = {0, 0, 0, 0};
+    for (int q = 0; q < 4; ++q)
+        for (int k = 0; k < 8; ++k) ca[q][k] = cb[q][k] = 0;
+    for (int i = 0; i < n; ++i) {
+        const int k = ord[i];
+        int best = -1, bc0 = 0, bc1 = 0;
+        for (int q = 0; q < 4; ++q) {
+            if (size[q] >= 8) continue;
+            const int c0 = max(ca[q][ga[k]] + 1, ma[q]) + max(cb[q][gb[k]] + 1, mxb[q]);
+            const int c1 = ca[q][ga[k]] + cb[q][gb[k]];
+            if (best < 0 || c0 < bc0 || (c0 == bc0 && (c1 < bc1 || (c1 == bc1 && size[q] < size[best])))) {
+                best = q;
+                bc0 = c0;
+                bc1 = c1;
+            }
+        }
+        lane[p0 + k] = (int8_t)(best * 8 + size[best]);
+        ++size[best];
+        ma[best] = max(ma[best], ++ca[best][ga[k]]);
+        mxb[best] = max(mxb[best], ++cb[best][gb[k]]);
+    }
 }
 
 __global__ void k_fill_dummy(uint32_t *kab, long long ns, uint32_t dummy) {
@@ -1057,16 +1117,20 @@ mts_status build_damping(mts_body *b, Tmp &tmp, cudaStream_t st, const int *cell
         MTS_TRY(dalloc_t(ctx, &b->kpad_ab, std::max(ns, 4LL)));
         MTS_TRY(dalloc_into(ctx, &b->kpad_g, std::max(ns, 4LL) * sizeof(R) + 16));
         const int bps = Pad<D>::v * (int)sizeof(R);
-        const long long dummy = (long long)nbk * b->mb * bps;   // byte offset of the dummy slot
-        if (dummy > 65535) {
+        // byte offset of the dummy slot; every slot position fits 16 bits
+        const long long dummy = (long long)damp_slot_pos(nbk * b->mb, bps) * bps;
+        if ((long long)(damp_slot_count(nbk * b->mb) - 1) * bps > 65535) {
             set_error("damping blocks too large for 16-bit byte offsets (%d particles)", b->mb);
             return MTS_ERR_INVALID_ARG;
         }
         k_fill_dummy<<<grid_for(std::max(ns, 4LL)), TPB, 0, st>>>(b->kpad_ab, std::max(ns, 4LL),
                                                                  (uint32_t)dummy);
         MTS_CUDA(cudaMemsetAsync(b->kpad_g, 0, std::max(ns, 4LL) * sizeof(R), st));
+        int8_t *lane = tmp.get<int8_t>(mm);
+        NEED(lane);
+        k_level_lanes<<<grid_for(nlev), TPB, 0, st>>>(b->lvl_pair, nlev, b->pair_ab, bps, lane);
         k_fill_slots<<<grid_for(m), TPB, 0, st>>>(k2s, m, b->grp_lvl, b->lvl_pair, b->pair_ab,
-                                                  b->pair_slot, b->kpad_ab, bps);
+                                                  lane, b->pair_slot, b->kpad_ab, bps);
         k_fill_slot_g<R><<<grid_for(m), TPB, 0, st>>>((const R *)b->pair_g, b->pair_slot, m,
                                                        (R *)b->kpad_g);
         MTS_TRY(dalloc_t(ctx, &b->grp_cons, ngg));

@@ -298,10 +298,12 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
 // the constrained axes, so no flags are staged)
 template <class R, int D>
 struct DampSmem {
-    // velocities (+1 dummy slot, padded to 16 bytes), 32 slots per level of
-    // coefficients and pair words (16-byte aligned for cp.async)
+    // velocities (+1 dummy slot, padded to a whole group of eight slots), 32
+    // slots per level of coefficients and pair words (16-byte aligned for
+    // cp.async)
     __host__ __device__ static size_t vbytes(int mb) {
-        return (((size_t)((1 << D) * mb + 1) * Pad<D>::v * sizeof(R)) + 15) & ~size_t(15);
+        return (((size_t)damp_slot_count((1 << D) * mb) * Pad<D>::v * sizeof(R)) + 15) &
+               ~size_t(15);
     }
     __host__ __device__ static size_t bytes(int mb, int maxl) {
         size_t b = vbytes(mb) + (size_t)32 * maxl * sizeof(R) + (size_t)32 * maxl * 4;
@@ -464,15 +466,18 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
         cp_async_wait_all();
         return;
     }
+    constexpr int SB = P * (int)sizeof(R);   // bytes per velocity slot
 #pragma unroll
     for (int e = 0; e < NB; ++e)
         for (int t = lane; t < tc[e]; t += 32)
-            cp_async_reals<R, P>(sv + (size_t)(e * mb + t) * P, A.v + (size_t)(ts[e] + t) * P);
+            cp_async_reals<R, P>(sv + (size_t)damp_slot_pos(e * mb + t, SB) * P,
+                                 A.v + (size_t)(ts[e] + t) * P);
     if (lane == 0) {
         R z[P];
 #pragma unroll
         for (int q = 0; q < P; ++q) z[q] = R(0);
-        st_vec<R, P>(sv + (size_t)NB * mb * P, z);      // dummy slot of the empty level slots
+        // dummy slot of the empty level slots
+        st_vec<R, P>(sv + (size_t)damp_slot_pos(NB * mb, SB) * P, z);
     }
     cp_async_wait_all();
     __syncwarp();
@@ -520,7 +525,7 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     for (int e = 0; e < NB; ++e)
         for (int t = lane; t < tc[e]; t += 32) {
             R vv[P];
-            ld_vec<R, P>(vv, sv + (e * mb + t) * P);
+            ld_vec<R, P>(vv, sv + (size_t)damp_slot_pos(e * mb + t, SB) * P);
             st_vec<R, P>(A.v + (long long)(ts[e] + t) * P, vv);
         }
 }
