@@ -425,6 +425,32 @@ __device__ __forceinline__ void damp_pair_coded(uint32_t w, R g, unsigned char *
     st_vec<R, P>(pb, vb);
 }
 
+// One half-sweep of a warp over its group's levels (forward or reverse),
+// prefetching the next level's slot off the velocity chain.  CONS: the group
+// touches a constrained particle, so a level that holds a constrained pair
+// (a warp vote) takes the coded path.
+template <class R, int D, bool CONS, bool FWD>
+__device__ __forceinline__ void damp_sweep(int nl, const uint32_t *sab, const R *sg, int lane,
+                                           unsigned char *svb, R hcim, bool tr) {
+    int l = FWD ? 0 : nl - 1;
+    uint32_t wn = sab[32 * l + lane];
+    R gn = sg[32 * l + lane];
+    for (int k = 0; k < nl; ++k, l += FWD ? 1 : -1) {
+        const uint32_t w = wn;
+        const R gc = gn;
+        if (k + 1 < nl) {
+            const int ln = FWD ? l + 1 : l - 1;
+            wn = sab[32 * ln + lane];
+            gn = sg[32 * ln + lane];
+        }
+        if (CONS && __any_sync(0xffffffffu, gc < R(0)))
+            damp_pair_coded<R, D>(w, gc, svb, hcim, tr);
+        else
+            damp_pair_free<R, D>(w, gc, svb, hcim);
+        __syncwarp();
+    }
+}
+
 template <class R, int D>
 __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long long g_end,
                                              int mode) {
@@ -487,38 +513,15 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     unsigned char *svb = reinterpret_cast<unsigned char *>(sv);
     // a group that touches no constrained particle has no negative coefficient;
     // in one that does, a level without a constrained pair takes the free code
-    auto level = [&](uint32_t w, R gc) {
-        if (cons && __any_sync(0xffffffffu, gc < R(0)))
-            damp_pair_coded<R, D>(w, gc, svb, hcim, tr);
-        else
-            damp_pair_free<R, D>(w, gc, svb, hcim);
-    };
-    if (nl > 0 && (mode & 1)) {
-        uint32_t wn = sab[lane];
-        R gn = sg[lane];
-        for (int l = 0; l < nl; ++l) {
-            const uint32_t w = wn;
-            const R gc = gn;
-            if (l + 1 < nl) {                 // next level's slot, off the v chain
-                wn = sab[32 * (l + 1) + lane];
-                gn = sg[32 * (l + 1) + lane];
-            }
-            level(w, gc);
-            __syncwarp();
-        }
-    }
-    if (nl > 0 && (mode & 2)) {
-        uint32_t wn = sab[32 * (nl - 1) + lane];
-        R gn = sg[32 * (nl - 1) + lane];
-        for (int l = nl - 1; l >= 0; --l) {
-            const uint32_t w = wn;
-            const R gc = gn;
-            if (l > 0) {
-                wn = sab[32 * (l - 1) + lane];
-                gn = sg[32 * (l - 1) + lane];
-            }
-            level(w, gc);
-            __syncwarp();
+    // a group that touches no constrained particle has no negative
+    // coefficient and runs the free-pair loop alone
+    if (nl > 0) {
+        if (cons) {
+            if (mode & 1) damp_sweep<R, D, true, true>(nl, sab, sg, lane, svb, hcim, tr);
+            if (mode & 2) damp_sweep<R, D, true, false>(nl, sab, sg, lane, svb, hcim, tr);
+        } else {
+            if (mode & 1) damp_sweep<R, D, false, true>(nl, sab, sg, lane, svb, hcim, tr);
+            if (mode & 2) damp_sweep<R, D, false, false>(nl, sab, sg, lane, svb, hcim, tr);
         }
     }
 #pragma unroll
