@@ -14,8 +14,8 @@
 //   kick     a-bar = dt v-bar on free axes, plus the end-force adjoint
 //   force    (P B0^T)-bar_c = -(1/rho0) sum_b (a-bar_b - a-bar_c) (x) g_cb
 //   P B0^T   P-bar = (P B0^T)-bar B0
-//   stress   Jacobian columns from forward-mode duals, contracted with the
-//            output adjoints (P, C-bar_p^-1', alpha')
+//   stress   one reverse sweep through the constitutive law (mts_vjp.cuh)
+//            from the output adjoints (P, C-bar_p^-1', alpha')
 //   F        G-bar = F-bar B0^T;  u-bar_c -= sum_b (G-bar_c + G-bar_b) g_cb
 //   diffusion  y = c-bar on free-c particles; c-bar = y + dt L(y), L the
 //            pairwise Laplacian of the forward step; D-bar from c before it
@@ -24,7 +24,7 @@
 #include <cmath>
 
 #include "mts_device.cuh"
-#include "mts_dual.cuh"
+#include "mts_vjp.cuh"
 #include "mts_internal.cuh"
 #include "mts_tiles.cuh"
 
@@ -33,7 +33,6 @@ namespace mts {
 namespace {
 
 constexpr int kTh = 8;          // parameter slots: E, s0, sinf, delta, H, D, beta, (spare)
-constexpr int kDualN = 8;       // derivative directions per dual pass
 
 inline unsigned grid_n(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
@@ -154,55 +153,58 @@ __device__ void stress_vjp(const Args<double> &A, const double (&F)[3][3], const
                            double c, double beta, double dK, double dmu, const double (&yb)[16],
                            double (&xb)[StressDirs<D, MAT>::n]) {
     using S = StressDirs<D, MAT>;
-    using T = Dual<double, kDualN>;
-    for (int base = 0; base < S::n; base += kDualN) {
-        auto seed = [&](double v, int idx, double scale) {
-            T x(v);
-            if (idx >= base && idx < base + kDualN) x.d[idx - base] = scale;
-            return x;
-        };
-        T Fd[3][3];
+    const double K = (double)A.K, mu = (double)A.mu;
+    double Pb[3][3], Fbar[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            Pb[r][q] = yb[r * 3 + q];
+            Fbar[r][q] = 0.0;
+        }
+    LawBar lb{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double cpb_in[7] = {0, 0, 0, 0, 0, 0, 0};
+    if constexpr (MAT == MTS_NEOHOOKE_J2) {
+        const double cpb_out[7] = {yb[9], yb[10], yb[11], yb[12], yb[13], yb[14], yb[15]};
+        stress_j2_vjp(F, cp, K, mu, (double)A.s0, (double)A.sinf, (double)A.delta,
+                      (double)A.Hlin, Pb, cpb_out, Fbar, cpb_in, lb);
+    } else {
+        stress_svk_vjp(F, K - mu * (2.0 / 3.0), mu, Pb, Fbar, lb);
+    }
+    double cb = 0.0, betab = 0.0;
+    if (A.swelling) {
+        // P -= p cof(F), p = 3 K beta (c - c0)
+        const double dc = c - (double)A.c0;
+        const double p = 3.0 * K * beta * dc;
+        double Cf[3][3], mPb[3][3], pbar = 0.0;
+        m3_cof(F, Cf);
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int q = 0; q < 3; ++q)
-                Fd[r][q] = (r < D && q < D) ? seed(F[r][q], r * D + q, 1.0) : T(F[r][q]);
-        const T K = seed((double)A.K, S::iE, dK), mu = seed((double)A.mu, S::iE, dmu);
-        T Pd[3][3];
-        T cpd[7];
-#pragma unroll
-        for (int k = 0; k < 7; ++k) cpd[k] = T(cp[k]);
-        if constexpr (MAT == MTS_NEOHOOKE_J2) {
-#pragma unroll
-            for (int k = 0; k < 7; ++k) cpd[k] = seed(cp[k], S::nF + k, 1.0);
-            const T s0 = seed((double)A.s0, S::iHard, 1.0), sinf = seed((double)A.sinf, S::iHard + 1, 1.0),
-                    delta = seed((double)A.delta, S::iHard + 2, 1.0),
-                    H = seed((double)A.Hlin, S::iHard + 3, 1.0);
-            stress_j2<T>(Fd, cpd, K, mu, s0, sinf, delta, H, Pd);
-        } else {
-            const T lam = K - mu * T(2.0 / 3.0);
-            stress_svk<T>(Fd, lam, mu, Pd);
-        }
-        if (A.swelling) {
-            const T cd = seed(c, S::iC, 1.0), bd = seed(beta, S::iBeta, 1.0);
-            const T p = T(3.0) * K * bd * (cd - T((double)A.c0));
-            add_swelling<T>(Fd, p, Pd);
-        }
-        for (int j = 0; j < kDualN; ++j) {
-            const int idx = base + j;
-            if (idx >= S::n) break;
-            double s = 0.0;
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int q = 0; q < 3; ++q) s += yb[r * 3 + q] * Pd[r][q].d[j];
-            if constexpr (MAT == MTS_NEOHOOKE_J2) {
-#pragma unroll
-                for (int k = 0; k < 7; ++k) s += yb[9 + k] * cpd[k].d[j];
+            for (int q = 0; q < 3; ++q) {
+                pbar -= Pb[r][q] * Cf[r][q];
+                mPb[r][q] = -p * Pb[r][q];
             }
-            xb[idx] = s;
-        }
+        cof_vjp(F, mPb, Fbar);
+        lb.K += pbar * 3.0 * beta * dc;
+        betab = pbar * 3.0 * K * dc;
+        cb = pbar * 3.0 * K * beta;
     }
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int q = 0; q < D; ++q) xb[r * D + q] = Fbar[r][q];
+    if constexpr (MAT == MTS_NEOHOOKE_J2) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) xb[S::nF + k] = cpb_in[k];
+        xb[S::iHard] = lb.s0;
+        xb[S::iHard + 1] = lb.sinf;
+        xb[S::iHard + 2] = lb.delta;
+        xb[S::iHard + 3] = lb.H;
+    }
+    xb[S::iC] = cb;
+    xb[S::iE] = lb.K * dK + lb.mu * dmu;
+    xb[S::iBeta] = betab;
 }
 
 // force transposed + P B0 transposed + stress transposed, at substep k of the

@@ -5,8 +5,6 @@
 #include <math.h>
 #include <stdint.h>
 
-#include "mts_dual.cuh"
-
 namespace mts {
 
 template <int D> struct Pad { static constexpr int v = (D == 2) ? 2 : 4; };
@@ -220,6 +218,9 @@ __device__ __forceinline__ void stress_svk(const R (&F)[3][3], R lambda, R mu, R
     S[0][0] += lambda * tr; S[1][1] += lambda * tr; S[2][2] += lambda * tr;
     m3_mul(F, S, P);
 }
+
+// Newton tolerance of the return mapping for a real type (FP64 / FP32)
+template <class R> struct NewtonTol { static constexpr double value = sizeof(R) == 8 ? 1e-13 : 1e-6; };
 
 template <class R>
 __device__ __forceinline__ R hard_k(R al, R s0, R sinf, R delta, R H) {
