@@ -28,6 +28,8 @@ namespace mts {
 namespace {
 
 inline unsigned grid_of(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+// the drift kernel's grid: four particles per thread
+inline unsigned drift_grid(long long n) { return (unsigned)((n + 4LL * kBlock - 1) / (4LL * kBlock)); }
 
 // F_a = I + (sum_b V (u_b - u_a) (x) grad_a W_ab) B0_a, 3x3 with F_zz = 1 in 2D;
 // X and u of the halo are in shared memory.
@@ -271,12 +273,18 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
         }
         st_vec<R, P>(A.v + i * P, v);
         st_vec<R, P>(A.acc + i * P, ao);
-        amax = sqrt(a2);
+        amax = a2;                       // max |a|^2; the square root is taken once, at the end
     }
     // block partials (fixed tree order: deterministic)
     __shared__ double sh[4][8];
     amax = warp_max(amax);
-    double f0 = warp_sum(fm[0]), f1 = warp_sum(fm[1]), f2 = warp_sum(fm[2]);
+    // end-force sums only in warps that hold a reported particle
+    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    if (__any_sync(0xffffffffu, fm[0] != 0.0 || fm[1] != 0.0 || fm[2] != 0.0)) {
+        f0 = warp_sum(fm[0]);
+        f1 = warp_sum(fm[1]);
+        f2 = warp_sum(fm[2]);
+    }
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
         sh[0][wid] = amax; sh[1][wid] = f0; sh[2][wid] = f1; sh[3][wid] = f2;
@@ -741,37 +749,43 @@ __global__ void __launch_bounds__(kBlock) k_drift(Args<R> A) {
         return;
     }
     constexpr int P = Pad<D>::v;
-    const long long i = blockIdx.x * (long long)kBlock + threadIdx.x;
-    double ke = 0.0, vmax = 0.0;
-    if (i < A.n) {
+    // each thread drifts several particles (grid stride) and keeps FP64
+    // partials of sum |v|^2 and max |v|^2; 1/2 m and the square root are
+    // applied once, to the totals (max |v| = sqrt(max |v|^2) exactly)
+    double v2sum = 0.0, v2max = 0.0;
+    {
         const double dt = C->dt, ramp = C->ramp;
-        const uint8_t fx = A.flags[i];
-        R v[P];
-        ld_vec<R, P>(v, A.v + i * P);
-        double u[P];
-        ld_vec<double, P>(u, A.u + i * P);
-        double v2 = 0.0;
+        const long long stride = (long long)gridDim.x * kBlock;
+        for (long long i = blockIdx.x * (long long)kBlock + threadIdx.x; i < A.n; i += stride) {
+            const uint8_t fx = A.flags[i];
+            R v[P];
+            ld_vec<R, P>(v, A.v + i * P);
+            double u[P];
+            ld_vec<double, P>(u, A.u + i * P);
+            double v2 = 0.0;
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-            if ((fx >> k) & 1) {
-                v[k] = R(0);
-                u[k] = ramp * A.u_unit[i * P + k];
-            } else {
-                u[k] += dt * (double)v[k];
+            for (int k = 0; k < D; ++k) {
+                if ((fx >> k) & 1) {
+                    v[k] = R(0);
+                    u[k] = ramp * A.u_unit[i * P + k];
+                } else {
+                    u[k] += dt * (double)v[k];
+                }
+                v2 += (double)v[k] * (double)v[k];
             }
-            v2 += (double)v[k] * (double)v[k];
-        }
-        st_vec<R, P>(A.v + i * P, v);
-        st_vec<double, P>(A.u + i * P, u);
-        if constexpr (sizeof(R) == 4) {
-            R uf[P];
+            st_vec<R, P>(A.v + i * P, v);
+            st_vec<double, P>(A.u + i * P, u);
+            if constexpr (sizeof(R) == 4) {
+                R uf[P];
 #pragma unroll
-            for (int k = 0; k < P; ++k) uf[k] = (R)u[k];
-            st_vec<R, P>(A.uf + i * P, uf);
+                for (int k = 0; k < P; ++k) uf[k] = (R)u[k];
+                st_vec<R, P>(A.uf + i * P, uf);
+            }
+            v2sum += v2;
+            v2max = fmax(v2max, v2);
         }
-        ke = 0.5 * A.mass * v2;
-        vmax = sqrt(v2);
     }
+    double ke = v2sum, vmax = v2max;
     __shared__ double sh[2][kBlock / 32];
     __shared__ int is_last;
     ke = warp_sum(ke);
@@ -844,7 +858,7 @@ __global__ void __launch_bounds__(kBlock) k_drift(Args<R> A) {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double KE = red[0][0], VM = red[1][0], AM = red[2][0];
+        const double KE = 0.5 * A.mass * red[0][0], VM = sqrt(red[1][0]), AM = sqrt(red[2][0]);
         C->ke = KE;
         C->vmax = VM;
         C->amax = AM;
@@ -1571,10 +1585,10 @@ mts_status prepare_t(mts_body *b) {
 template <class R, int D>
 mts_status drift_t(mts_body *b) {
     if (b->use_cond)
-        MTS_CUDA(launch_chain(b, k_drift<R, D, true>, grid_of(b->n), (unsigned)kBlock, 0,
+        MTS_CUDA(launch_chain(b, k_drift<R, D, true>, drift_grid(b->n), (unsigned)kBlock, 0,
                               make_args<R>(b)));
     else
-        MTS_CUDA(launch_chain(b, k_drift<R, D, false>, grid_of(b->n), (unsigned)kBlock, 0,
+        MTS_CUDA(launch_chain(b, k_drift<R, D, false>, drift_grid(b->n), (unsigned)kBlock, 0,
                               make_args<R>(b)));
     return MTS_OK;
 }
