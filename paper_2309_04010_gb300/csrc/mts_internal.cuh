@@ -33,6 +33,11 @@ constexpr int kForceBit = 8;
 constexpr int kTipBit = 16;
 constexpr int kCHeldBit = 32;
 constexpr int kBlock = 256;  // threads per block of the per-particle kernels
+// threads per block (= particles per Morton tile) of the tile kernels: larger
+// FP32 tiles cut the halo per particle (a 512-particle tile of the 3D lattice
+// stages ~3.4 halo particles per tile particle, a 256-particle one ~5.7)
+template <class R> struct TileThreads { static constexpr int v = sizeof(R) == 4 ? 512 : 256; };
+template <class R> constexpr int tile_particles() { return sizeof(R) == 4 ? 512 : 128; }
 constexpr int kLevelCap = 32;  // pairs per damping level: one warp-wide pass
 
 // Shared-memory position of velocity slot s in the warp-per-group damping

@@ -799,8 +799,8 @@ mts_status to_host(T *h, const T *d, size_t count, cudaStream_t st) {
 }
 
 mts_status build_tiles(mts_body *b, Tmp &tmp, cudaStream_t st, int T) {
-    if (T < 64 || T > 256) {   // the force partials buffer holds one slot per 64 particles
-        set_error("tile size %d outside [64, 256]", T);
+    if (T < 64 || T > 512) {   // the force partials buffer holds one slot per 64 particles
+        set_error("tile size %d outside [64, 512]", T);
         return MTS_ERR_STATE;
     }
     mts_ctx *ctx = b->ctx;
@@ -1277,7 +1277,7 @@ mts_status build_typed(mts_body *b, const double *hX) {
         }
     }
     // -- Morton tiles and their halos (particles + neighbours), local ELL
-    MTS_TRY(build_tiles(b, tmp, st, sizeof(R) == 4 ? 256 : 128));
+    MTS_TRY(build_tiles(b, tmp, st, tile_particles<R>()));
 
     // -- setup errors
     unsigned err = 0;

@@ -104,7 +104,7 @@ __device__ __forceinline__ void unscale_F(const Args<R> &A, R (&F)[3][3]) {
 
 // --------------------------------------------------------------------- K_A
 template <class R, int D, int MAT>
-__global__ void __launch_bounds__(256) k_stress(Args<R> A) {
+__global__ void __launch_bounds__(TileThreads<R>::v) k_stress(Args<R> A) {
     chain_trigger();
     chain_wait();
     if (A.ctrl->done) return;
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256) k_stress(Args<R> A) {
 
 // --------------------------------------------------------------------- K_B
 template <class R, int D>
-__global__ void __launch_bounds__(256) k_force(Args<R> A) {
+__global__ void __launch_bounds__(TileThreads<R>::v) k_force(Args<R> A) {
     chain_trigger();
     chain_wait();
     if (A.ctrl->done) return;
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256) k_force(Args<R> A) {
         amax = a2;                       // max |a|^2; the square root is taken once, at the end
     }
     // block partials (fixed tree order: deterministic)
-    __shared__ double sh[4][8];
+    __shared__ double sh[4][TileThreads<R>::v / 32];
     amax = warp_max(amax);
     // end-force sums only in warps that hold a reported particle
     double f0 = 0.0, f1 = 0.0, f2 = 0.0;
@@ -778,7 +778,7 @@ __global__ void __launch_bounds__(kBlock) k_drift(Args<R> A) {
             if constexpr (sizeof(R) == 4) {
                 R uf[P];
 #pragma unroll
-                for (int k = 0; k < P; ++k) uf[k] = (R)u[k];
+                for (int k = 0; k < P; ++k) uf[k] = k < D ? (R)u[k] : R(0);   // padding stays 0
                 st_vec<R, P>(A.uf + i * P, uf);
             }
             v2sum += v2;
@@ -922,7 +922,7 @@ __global__ void k_load(Args<R> A) {
 
 // explicit diffusion (Sec. 2.2 Fick's law as a scalar; Jacobi update)
 template <class R, int D>
-__global__ void __launch_bounds__(256) k_diffuse(Args<R> A, R dt) {
+__global__ void __launch_bounds__(TileThreads<R>::v) k_diffuse(Args<R> A, R dt) {
     constexpr int P = Pad<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
     R *sX = reinterpret_cast<R *>(smem);
@@ -991,7 +991,7 @@ __device__ __forceinline__ void inv_cauchy_green(const R (&F)[3][3], R (&Ci)[3][
 }
 
 template <class R, int D>
-__global__ void __launch_bounds__(256) k_diff_flux(Args<R> A) {
+__global__ void __launch_bounds__(TileThreads<R>::v) k_diff_flux(Args<R> A) {
     constexpr int P = Pad<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
     const size_t o1 = second_off<R, P>(A.max_halo);
@@ -1057,7 +1057,7 @@ __global__ void __launch_bounds__(256) k_diff_flux(Args<R> A) {
 }
 
 template <class R, int D>
-__global__ void __launch_bounds__(256) k_diff_div(Args<R> A, R dt) {
+__global__ void __launch_bounds__(TileThreads<R>::v) k_diff_div(Args<R> A, R dt) {
     constexpr int P = Pad<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
     R *sX = reinterpret_cast<R *>(smem);
@@ -1100,7 +1100,7 @@ __global__ void __launch_bounds__(256) k_diff_div(Args<R> A, R dt) {
 // 2 D |J_x| |C_x^-1 B0_x^T|_inf s1_x with s1_x = sum_b V |grad0 W_xb|_1, then
 // max over rows of sum_b V |grad0 W_ab|_1 (R_a + R_b)
 template <class R, int D>
-__global__ void __launch_bounds__(256) k_ts_rowcoef(Args<R> A, double *Rx) {
+__global__ void __launch_bounds__(TileThreads<R>::v) k_ts_rowcoef(Args<R> A, double *Rx) {
     constexpr int P = Pad<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
     R *sX = reinterpret_cast<R *>(smem);
@@ -1155,7 +1155,7 @@ __global__ void __launch_bounds__(256) k_ts_rowcoef(Args<R> A, double *Rx) {
 }
 
 template <class R, int D>
-__global__ void __launch_bounds__(256) k_ts_bound(Args<R> A, const double *Rx, double *part) {
+__global__ void __launch_bounds__(TileThreads<R>::v) k_ts_bound(Args<R> A, const double *Rx, double *part) {
     constexpr int P = Pad<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
     R *sX = reinterpret_cast<R *>(smem);
@@ -1190,7 +1190,7 @@ __global__ void __launch_bounds__(256) k_ts_bound(Args<R> A, const double *Rx, d
         });
     }
     rowsum = warp_max(rowsum);
-    __shared__ double sh[8];
+    __shared__ double sh[TileThreads<R>::v / 32];
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = rowsum;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1238,7 +1238,7 @@ __global__ void k_diff_bound(const double *X64, const long long *off, const int3
 
 // --------------------------------------------------------------------- reads
 template <class R, int D>
-__global__ void __launch_bounds__(256) k_defgrad(Args<R> A, double *out) {
+__global__ void __launch_bounds__(TileThreads<R>::v) k_defgrad(Args<R> A, double *out) {
     constexpr int P = Pad<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
     R *sX = reinterpret_cast<R *>(smem);
