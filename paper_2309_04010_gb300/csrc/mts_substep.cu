@@ -398,11 +398,13 @@ __device__ __forceinline__ void damp_pair_free(uint32_t w, R g, unsigned char *s
 // damp_apply for the warp-per-group kernel, where the pair word carries the
 // constrained axes of both particles in the low three bits of each byte
 // offset (velocity slots are at least 8 bytes, so those bits are free; they
-// are zero for a free pair).  Every lane of a level runs the same code: a
-// free pair takes ca = cb = f2 and the d form, exactly the free-free branch.
-template <class R, int D>
-__device__ __forceinline__ void damp_pair_coded(uint32_t w, R g, unsigned char *svb, R hcim,
-                                                bool transpose) {
+// are zero for a free pair).  Branch-free: both factors are formed and each
+// axis selects its coefficients, so every lane of a level runs the same
+// instructions (a free pair takes ca = cb = f2 and the d form, exactly the
+// free-free branch; data-dependent branches here cost more than the second
+// division).  TR: the transposed 2x2 update for constrained pairs (adjoint).
+template <class R, int D, bool TR>
+__device__ __forceinline__ void damp_pair_coded(uint32_t w, R g, unsigned char *svb, R hcim) {
     constexpr int P = Pad<D>::v;
     const uint32_t fa = w & 7u, fb = (w >> 16) & 7u;
     R *pa = reinterpret_cast<R *>(svb + ((w & 0xffffu) & ~7u));
@@ -419,12 +421,14 @@ __device__ __forceinline__ void damp_pair_coded(uint32_t w, R g, unsigned char *
         const bool a_free = !((fa >> q) & 1u), b_free = !((fb >> q) & 1u);
         const R ca = a_free ? (b_free ? f2 : f1) : R(0);
         const R cb = b_free ? (a_free ? f2 : f1) : R(0);
-        if (transpose && cons) {    // the transposed 2x2 update (adjoint sweep)
+        const R d = va[q] - vb[q];
+        if constexpr (TR) {
             const R t = ca * va[q] - cb * vb[q];
-            va[q] -= t;
-            vb[q] += t;
+            const R na = cons ? va[q] - t : va[q] - ca * d;
+            const R nb = cons ? vb[q] + t : vb[q] + cb * d;
+            va[q] = na;
+            vb[q] = nb;
         } else {
-            const R d = va[q] - vb[q];
             va[q] -= ca * d;
             vb[q] += cb * d;
         }
@@ -435,11 +439,10 @@ __device__ __forceinline__ void damp_pair_coded(uint32_t w, R g, unsigned char *
 
 // One half-sweep of a warp over its group's levels (forward or reverse),
 // prefetching the next level's slot off the velocity chain.  CONS: the group
-// touches a constrained particle, so a level that holds a constrained pair
-// (a warp vote) takes the coded path.
-template <class R, int D, bool CONS, bool FWD>
+// touches a constrained particle, so every level takes the coded update.
+template <class R, int D, bool CONS, bool FWD, bool TR>
 __device__ __forceinline__ void damp_sweep(int nl, const uint32_t *sab, const R *sg, int lane,
-                                           unsigned char *svb, R hcim, bool tr) {
+                                           unsigned char *svb, R hcim) {
     int l = FWD ? 0 : nl - 1;
     uint32_t wn = sab[32 * l + lane];
     R gn = sg[32 * l + lane];
@@ -451,11 +454,23 @@ __device__ __forceinline__ void damp_sweep(int nl, const uint32_t *sab, const R 
             wn = sab[32 * ln + lane];
             gn = sg[32 * ln + lane];
         }
-        if (CONS && __any_sync(0xffffffffu, gc < R(0)))
-            damp_pair_coded<R, D>(w, gc, svb, hcim, tr);
+        if constexpr (CONS)
+            damp_pair_coded<R, D, TR>(w, gc, svb, hcim);
         else
             damp_pair_free<R, D>(w, gc, svb, hcim);
         __syncwarp();
+    }
+}
+
+template <class R, int D, bool TR>
+__device__ __forceinline__ void damp_sweeps(bool cons, int mode, int nl, const uint32_t *sab,
+                                            const R *sg, int lane, unsigned char *svb, R hcim) {
+    if (cons) {
+        if (mode & 1) damp_sweep<R, D, true, true, TR>(nl, sab, sg, lane, svb, hcim);
+        if (mode & 2) damp_sweep<R, D, true, false, TR>(nl, sab, sg, lane, svb, hcim);
+    } else {
+        if (mode & 1) damp_sweep<R, D, false, true, TR>(nl, sab, sg, lane, svb, hcim);
+        if (mode & 2) damp_sweep<R, D, false, false, TR>(nl, sab, sg, lane, svb, hcim);
     }
 }
 
@@ -524,13 +539,10 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     // a group that touches no constrained particle has no negative
     // coefficient and runs the free-pair loop alone
     if (nl > 0) {
-        if (cons) {
-            if (mode & 1) damp_sweep<R, D, true, true>(nl, sab, sg, lane, svb, hcim, tr);
-            if (mode & 2) damp_sweep<R, D, true, false>(nl, sab, sg, lane, svb, hcim, tr);
-        } else {
-            if (mode & 1) damp_sweep<R, D, false, true>(nl, sab, sg, lane, svb, hcim, tr);
-            if (mode & 2) damp_sweep<R, D, false, false>(nl, sab, sg, lane, svb, hcim, tr);
-        }
+        if (tr)
+            damp_sweeps<R, D, true>(cons, mode, nl, sab, sg, lane, svb, hcim);
+        else
+            damp_sweeps<R, D, false>(cons, mode, nl, sab, sg, lane, svb, hcim);
     }
 #pragma unroll
     for (int e = 0; e < NB; ++e)
