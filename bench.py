@@ -502,8 +502,8 @@ def run_ours(args, rank, world, local):
         gb.write(M.F_U, U)
         gb.write(M.F_V, Vv)
         r = slow_step(l0 + s + 1)
-        U[:] = gb.read(M.F_U)
-        Vv[:] = gb.read(M.F_V)
+        gb.read(M.F_U, out=U)
+        gb.read(M.F_V, out=Vv)
         e2e_t += time.perf_counter() - t0
         e2e_sub += r.substeps
     e2e_value = case.n * e2e_sub / e2e_t if e2e_t > 0 else None

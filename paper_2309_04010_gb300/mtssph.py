@@ -417,11 +417,17 @@ class Body:
         return {F_U: self.dim, F_X: self.dim, F_V: self.dim, F_ACC: self.dim, F_DEFGRAD: 9,
                 F_PB: self.dim * self.dim, F_C: 1, F_ALPHA: 1, F_CPINV: 6}[field]
 
-    def read(self, field: int) -> np.ndarray:
+    def read(self, field: int, out: Optional[np.ndarray] = None) -> np.ndarray:
+        """Field in the original particle order (float64); `out`, when given, is
+        a C-contiguous float64 array of n * width values that receives it (for
+        example pinned host memory)."""
         w = self._width(field)
-        out = np.zeros(self.n * w)
+        if out is None:
+            out = np.zeros(self.n * w)
+        elif (out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"] or out.size != self.n * w):
+            raise ValueError("read: out must be a C-contiguous float64 array of n * width values")
         _check(lib().mts_read_field(self._h, field, _ptr(out), out.size), "mts_read_field")
-        return out.reshape(self.n, w) if w > 1 else out
+        return out.reshape(self.n, w) if w > 1 else out.reshape(self.n)
 
     def write(self, field: int, values):
         w = self._width(field)
