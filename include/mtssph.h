@@ -63,7 +63,11 @@ typedef struct {
 
 /* Context: one CUDA device and one stream.  stream = NULL creates a private
  * non-blocking stream owned by the context; otherwise the caller's
- * cudaStream_t is used and stays owned by the caller. */
+ * cudaStream_t is used and stays owned by the caller.  The captured substep
+ * graphs launch their kernels with programmatic dependent launch (each kernel
+ * may start while the previous one drains); setting the environment variable
+ * MTS_NO_CHAIN_LAUNCH before the context is created turns that off, and a
+ * capture that fails with it enabled is retried once without it. */
 mts_status mts_ctx_create(int device, void *cuda_stream, const mts_allocator *alloc,
                           mts_ctx **out);
 /* Destroy every body of the context first: a body keeps a pointer to it. */
