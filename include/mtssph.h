@@ -100,7 +100,9 @@ typedef struct {
     double dx;               /* lattice spacing: particle volume dx^dim               */
     double h_over_dx;        /* smoothing length h = h_over_dx * dx, support 2h       */
     int32_t damp_layout;     /* mts_damp_layout of the pairwise damping order         */
-    int32_t reserved;
+    int32_t tile;            /* particles per Morton tile of the gather kernels (their */
+                             /* block size): 0 = default (512 mixed, 128 FP64), else  */
+                             /* 64, 128, 256 or 512 (mixed) / 64 or 128 (FP64)        */
     double dx_axis[3];       /* lattice spacing per axis (the anisotropic kernel of   */
                              /* thin bodies); all 0 = dx on every axis.  Otherwise dx */
                              /* is ignored, h = h_over_dx * min spacing and the       */
@@ -127,6 +129,29 @@ void mts_body_destroy(mts_body *body);
  * sub-colour of one owner block (0 = none). */
 #define MTS_WHOLE_AXIS 62
 mts_status mts_body_damping_layout(const mts_body *body, int32_t shift[3], int32_t *level_cap);
+
+/* Launch shapes of the substep kernels.  tile: particles per Morton tile of
+ * the gather kernels (= their threads per block; 0 keeps the current tiles,
+ * otherwise as mts_body_desc.tile) — the tiles are rebuilt, which changes the
+ * rounding of the tile-relative positions but not the method; damp_warps:
+ * owner groups (warps) per CTA of the damping kernel, 0 = as many of 4, 2, 1
+ * as fit the shared memory, else 1, 2 or 4 (reduced while it does not fit;
+ * the results do not depend on it).  mts_body_shapes reports the shapes in
+ * use.  Errors: MTS_ERR_INVALID_ARG for other values or a NULL body. */
+mts_status mts_body_set_shapes(mts_body *body, int32_t tile, int32_t damp_warps);
+mts_status mts_body_shapes(const mts_body *body, int32_t *tile, int32_t *damp_warps);
+
+/* Autotuner of the launch shapes: for every candidate (tiles 256 and 512 in
+ * mixed precision, 64 and 128 in FP64; 1, 2 and 4 damping warps per CTA) it
+ * runs one slow step of `substeps` substeps (load scale `ramp`, no
+ * kinetic-energy stop, the production device loop) twice from the body's
+ * current state and times the second run with CUDA events on the context's
+ * stream; the fastest candidate (the first on ties) is applied and the state
+ * is restored (mts_save_state / mts_load_state), so the body continues as if
+ * the tuner had not run.  tile, damp_warps, best_ms: the choice and its time
+ * (may be NULL).  substeps in [1, 1000]. */
+mts_status mts_body_autotune(mts_body *body, int32_t substeps, double ramp, int32_t *tile,
+                             int32_t *damp_warps, double *best_ms);
 
 /* Sorted position -> original index (n entries, host). */
 mts_status mts_body_permutation(const mts_body *body, int64_t *perm);
@@ -252,6 +277,10 @@ mts_status mts_advance_slow_step(mts_body *body, const mts_step_params *params,
 mts_status mts_batch_create(mts_ctx *ctx, int32_t count, mts_body *const *bodies, mts_batch **out);
 mts_status mts_batch_advance(mts_batch *batch, const mts_step_params *params,
                              mts_step_report *reports);
+/* mts_body_autotune on every body of the batch, one after another (each body
+ * keeps its own choice); the batch graph is captured again at the next
+ * advance. */
+mts_status mts_batch_autotune(mts_batch *batch, int32_t substeps, double ramp);
 void mts_batch_destroy(mts_batch *batch);
 
 /* Time one stage of every substep with CUDA events recorded inside the

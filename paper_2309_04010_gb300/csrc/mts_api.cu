@@ -524,6 +524,14 @@ mts_status mts_body_create(mts_ctx *ctx, const mts_body_desc *desc, mts_body **o
                   desc->precision, desc->damp_layout);
         return MTS_ERR_INVALID_ARG;
     }
+    {
+        const int tmax = tile_max(desc->precision == MTS_FP64 ? 8 : 4);
+        const int T = desc->tile;
+        if (T != 0 && (T < 64 || T > tmax || (T & (T - 1)) != 0)) {
+            set_error("mts_body_create: tile %d (0, or a power of two in [64, %d])", T, tmax);
+            return MTS_ERR_INVALID_ARG;
+        }
+    }
     // per-axis spacing (anisotropic kernel): all zero = isotropic
     double dxk[3] = {desc->dx, desc->dx, desc->dx};
     bool any_axis = false;
@@ -563,6 +571,8 @@ mts_status mts_body_create(mts_ctx *ctx, const mts_body_desc *desc, mts_body **o
     b->blk_shift = 0;
     while ((1LL << b->blk_shift) < need) ++b->blk_shift;
     b->damp_req = desc->damp_layout;
+    b->tile_req = desc->tile;
+    b->damp_warps_req = 0;
     b->rsize = b->precision == MTS_FP64 ? 8 : 4;
     b->graph_dirty = true;
     ++b->graph_gen;
@@ -646,6 +656,109 @@ mts_status mts_body_damping_layout(const mts_body *b, int32_t shift[3], int32_t 
     }
     for (int k = 0; k < 3; ++k) shift[k] = b->ax_shift[k] >= kWholeAxis ? MTS_WHOLE_AXIS : b->ax_shift[k];
     *level_cap = b->level_cap;
+    return MTS_OK;
+}
+
+mts_status mts_body_set_shapes(mts_body *b, int32_t tile, int32_t damp_warps) {
+    if (!b) {
+        set_error("mts_body_set_shapes: NULL body");
+        return MTS_ERR_INVALID_ARG;
+    }
+    const int tmax = tile_max((int)b->rsize);
+    if ((tile != 0 && (tile < 64 || tile > tmax || (tile & (tile - 1)) != 0)) ||
+        (damp_warps != 0 && damp_warps != 1 && damp_warps != 2 && damp_warps != 4)) {
+        set_error("mts_body_set_shapes: tile %d (0, or a power of two in [64, %d]), damp_warps %d "
+                  "(0, 1, 2 or 4)", tile, tmax, damp_warps);
+        return MTS_ERR_INVALID_ARG;
+    }
+    MTS_CUDA(cudaSetDevice(b->ctx->device));
+    if (tile != 0 && tile != b->T) {
+        MTS_TRY(retile(b, tile));
+        if (b->adj_cap > 0) MTS_TRY(adjoint_prepare(b));
+    }
+    b->damp_warps_req = damp_warps;
+    b->graph_dirty = true;
+    ++b->graph_gen;
+    return MTS_OK;
+}
+
+mts_status mts_body_shapes(const mts_body *b, int32_t *tile, int32_t *damp_warps) {
+    if (!b || !tile || !damp_warps) {
+        set_error("mts_body_shapes: NULL argument");
+        return MTS_ERR_INVALID_ARG;
+    }
+    *tile = b->T;
+    *damp_warps = damp_warps_of(b);
+    return MTS_OK;
+}
+
+mts_status mts_body_autotune(mts_body *b, int32_t substeps, double ramp, int32_t *tile,
+                             int32_t *damp_warps, double *best_ms) {
+    if (!b || substeps < 1 || substeps > 1000 || !std::isfinite(ramp)) {
+        set_error("mts_body_autotune: NULL body, substeps %d (1..1000) or ramp %g", substeps, ramp);
+        return MTS_ERR_INVALID_ARG;
+    }
+    if (!b->has_material) {
+        set_error("mts_body_autotune: no material set");
+        return MTS_ERR_STATE;
+    }
+    MTS_CUDA(cudaSetDevice(b->ctx->device));
+    size_t bytes = 0;
+    MTS_TRY(mts_save_state(b, nullptr, &bytes));
+    std::vector<unsigned char> saved(bytes);
+    MTS_TRY(mts_save_state(b, saved.data(), &bytes));
+    const int tiles32[2] = {256, 512}, tiles64[2] = {64, 128}, warps[3] = {1, 2, 4};
+    const int *tiles = b->rsize == 4 ? tiles32 : tiles64;
+    mts_step_params p{};
+    p.ramp_value = ramp;
+    p.ke_tol = -1.0;
+    p.ke_ref = 1.0;
+    p.max_substeps = substeps;
+    mts_step_report rep{};
+    cudaEvent_t e0, e1;
+    MTS_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    }
+    mts_status s = MTS_OK;
+    int best_t = b->T, best_w = damp_warps_of(b);
+    double best = 1e300;
+    for (int ti = 0; ti < 2 && s == MTS_OK; ++ti)
+        for (int wi = 0; wi < 3 && s == MTS_OK; ++wi) {
+            s = mts_body_set_shapes(b, tiles[ti], warps[wi]);
+            if (s == MTS_OK && damp_warps_of(b) != warps[wi]) continue;   // does not fit
+            for (int rep_i = 0; rep_i < 2 && s == MTS_OK; ++rep_i) {   // capture, then time
+                s = mts_load_state(b, saved.data(), bytes);
+                if (s != MTS_OK) break;
+                if (rep_i == 1 && cudaEventRecord(e0, b->ctx->stream) != cudaSuccess) {
+                    s = cuda_fail(cudaGetLastError(), "cudaEventRecord");
+                    break;
+                }
+                s = mts_advance_slow_step(b, &p, &rep);
+                if (s == MTS_OK && rep_i == 1) {
+                    cudaError_t e = cudaEventRecord(e1, b->ctx->stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0.0f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e != cudaSuccess) {
+                        s = cuda_fail(e, "autotune timing");
+                    } else if (ms < best) {
+                        best = ms;
+                        best_t = tiles[ti];
+                        best_w = warps[wi];
+                    }
+                }
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == MTS_OK) s = mts_body_set_shapes(b, best_t, best_w);
+    if (s == MTS_OK) s = mts_load_state(b, saved.data(), bytes);
+    if (s != MTS_OK) return s;
+    if (tile) *tile = best_t;
+    if (damp_warps) *damp_warps = best_w;
+    if (best_ms) *best_ms = best;
     return MTS_OK;
 }
 
@@ -957,6 +1070,16 @@ mts_status mts_batch_create(mts_ctx *ctx, int32_t count, mts_body *const *bodies
     bt->bodies = std::move(v);
     bt->graph = nullptr;
     *out = bt;
+    return MTS_OK;
+}
+
+mts_status mts_batch_autotune(mts_batch *bt, int32_t substeps, double ramp) {
+    if (!bt) {
+        set_error("mts_batch_autotune: NULL batch");
+        return MTS_ERR_INVALID_ARG;
+    }
+    for (mts_body *b : bt->bodies)
+        MTS_TRY(mts_body_autotune(b, substeps, ramp, nullptr, nullptr, nullptr));
     return MTS_OK;
 }
 

@@ -38,6 +38,9 @@ constexpr int kBlock = 256;  // threads per block of the per-particle kernels
 // stages ~3.4 halo particles per tile particle, a 256-particle one ~5.7)
 template <class R> struct TileThreads { static constexpr int v = sizeof(R) == 4 ? 512 : 256; };
 template <class R> constexpr int tile_particles() { return sizeof(R) == 4 ? 512 : 128; }
+// largest tile a body of this precision may use (the FP64 reverse-mode
+// kernels are built for blocks of at most 128 threads)
+inline int tile_max(int rsize) { return rsize == 4 ? 512 : 128; }
 constexpr int kLevelCap = 32;  // pairs per damping level: one warp-wide pass
 
 // Shared-memory position of velocity slot s in the warp-per-group damping
@@ -184,6 +187,8 @@ struct mts_body {
     double dx, h, V, cut2;
     int blk_shift;
     int damp_req;         // requested mts_damp_layout
+    int damp_warps_req;   // damping warps per CTA: 0 = as many of 4, 2, 1 as fit
+    int tile_req;         // particles per Morton tile requested at creation (0 = default)
     bool pdl_now;         // capturing the substep chain with programmatic launches
     int damp_layout;      // resolved: MTS_DAMP_BLOCKS or MTS_DAMP_WIDE
     int ax_shift[3];      // owner-block width per axis (kWholeAxis = unblocked)
@@ -319,6 +324,8 @@ mts_status adjoint_out(mts_body *b, int field, double *out_dev);
 mts_status adjoint_norm2(mts_body *b, double *part_dev, double *out_dev);
 mts_status launch_drift(mts_body *b);
 mts_status prepare_kernels(mts_body *b);
+mts_status retile(mts_body *b, int T);
+int damp_warps_of(const mts_body *b);
 // shared memory of the CTA-per-group damping kernel for this body's layout
 size_t damp_wide_smem(const mts_body *b);
 mts_status update_pair_fixbits(mts_body *b);

@@ -1277,7 +1277,7 @@ mts_status build_typed(mts_body *b, const double *hX) {
         }
     }
     // -- Morton tiles and their halos (particles + neighbours), local ELL
-    MTS_TRY(build_tiles(b, tmp, st, tile_particles<R>()));
+    MTS_TRY(build_tiles(b, tmp, st, b->tile_req > 0 ? b->tile_req : tile_particles<R>()));
 
     // -- setup errors
     unsigned err = 0;
@@ -1295,6 +1295,24 @@ mts_status build_typed(mts_body *b, const double *hX) {
 }
 
 }  // namespace
+
+// Rebuild the Morton tiles with T particles per tile (the block size of the
+// gather kernels); the previous tile arrays are released first.
+mts_status retile(mts_body *b, int T) {
+    cudaStream_t st = b->ctx->stream;
+    MTS_CUDA(cudaStreamSynchronize(st));
+    void **ptrs[] = {(void **)&b->halo_off, (void **)&b->halo_idx, (void **)&b->halo_x,
+                     (void **)&b->lell_off, (void **)&b->tile_w, (void **)&b->lell,
+                     (void **)&b->lself};
+    for (void **pp : ptrs) {
+        dfree(b->ctx, *pp);
+        *pp = nullptr;
+    }
+    Tmp tmp{b->ctx, {}};
+    MTS_TRY(build_tiles(b, tmp, st, T));
+    MTS_CUDA(cudaStreamSynchronize(st));
+    return MTS_OK;
+}
 
 double kernel_alpha(int dim, double h) {
     if (dim == 2) return 7.0 / (4.0 * M_PI * h * h);

@@ -1452,9 +1452,11 @@ template <class R, int D> size_t smem_force(const mts_body *b) {
 template <class R, int D> size_t smem_diffuse(const mts_body *b) {
     return second_off<R, Pad<D>::v>(b->max_halo) + (size_t)b->max_halo * sizeof(R);
 }
+// damping warps (owner groups) per CTA: the requested count, or 4, reduced
+// while the CTA's staging does not fit the shared-memory budget
 template <class R, int D> int damp_warps(const mts_body *b) {
     const size_t per = DampSmem<R, D>::bytes(b->mb, b->max_group_levels);
-    int w = 4;
+    int w = b->damp_warps_req > 0 ? b->damp_warps_req : 4;
     while (w > 1 && per * w > 200 * 1024) w >>= 1;
     return w;
 }
@@ -1687,6 +1689,11 @@ mts_status field_in_t(mts_body *b, int field) {
 
 }  // namespace
 
+int damp_warps_of(const mts_body *b) {
+    if (b->precision == MTS_FP64)
+        return b->dim == 2 ? damp_warps<double, 2>(b) : damp_warps<double, 3>(b);
+    return b->dim == 2 ? damp_warps<float, 2>(b) : damp_warps<float, 3>(b);
+}
 mts_status launch_stress(mts_body *b) { return DISPATCH(stress_t, b); }
 mts_status launch_force(mts_body *b) { return DISPATCH(force_t, b); }
 mts_status launch_damping(mts_body *b, long long *launches) { return DISPATCH(damping_t, b, launches); }

@@ -63,7 +63,7 @@ class Allocator(C.Structure):
 class BodyDesc(C.Structure):
     _fields_ = [("dim", C.c_int32), ("precision", C.c_int32), ("n", C.c_int64),
                 ("X", C.c_void_p), ("dx", C.c_double), ("h_over_dx", C.c_double),
-                ("damp_layout", C.c_int32), ("reserved", C.c_int32),
+                ("damp_layout", C.c_int32), ("tile", C.c_int32),
                 ("dx_axis", C.c_double * 3)]
 
 
@@ -135,6 +135,10 @@ def lib():
         "mts_read_field": [vp, i32, vp, i64],
         "mts_write_field": [vp, i32, vp, i64],
         "mts_kinetic_energy_noalloc": [vp, i32, i32, i64, d, vp, vp],
+        "mts_body_set_shapes": [vp, i32, i32],
+        "mts_body_shapes": [vp, C.POINTER(i32), C.POINTER(i32)],
+        "mts_body_autotune": [vp, i32, d, C.POINTER(i32), C.POINTER(i32), C.POINTER(d)],
+        "mts_batch_autotune": [vp, i32, d],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -219,16 +223,18 @@ class Body:
     """mts_body: a particle body with its fixed neighbourhood on the GPU."""
 
     def __init__(self, ctx: Context, X: np.ndarray, dx: float, h_over_dx: float = 1.3,
-                 precision: int = FP64, damp_layout: int = DAMP_AUTO, dx_axis=None):
-        """dx_axis: lattice spacing per axis (anisotropic kernel); None = dx."""
+                 precision: int = FP64, damp_layout: int = DAMP_AUTO, dx_axis=None,
+                 tile: int = 0):
+        """dx_axis: lattice spacing per axis (anisotropic kernel); None = dx.
+        tile: particles per Morton tile of the gather kernels (0 = default)."""
         X = np.ascontiguousarray(X, dtype=np.float64)
         self.n, self.dim = X.shape
         self.ctx = ctx
         self.precision = precision
         da = (C.c_double * 3)(*([0.0] * 3 if dx_axis is None else
                                 list(dx_axis) + [0.0] * (3 - len(dx_axis))))
-        desc = BodyDesc(self.dim, precision, self.n, X.ctypes.data, dx, h_over_dx, damp_layout, 0,
-                        da)
+        desc = BodyDesc(self.dim, precision, self.n, X.ctypes.data, dx, h_over_dx, damp_layout,
+                        int(tile), da)
         h = C.c_void_p()
         _check(lib().mts_body_create(ctx.handle, C.byref(desc), C.byref(h)), "mts_body_create")
         self._h = h
@@ -434,6 +440,25 @@ class Body:
         a = np.ascontiguousarray(values, dtype=np.float64).reshape(self.n * w)
         _check(lib().mts_write_field(self._h, field, _ptr(a), a.size), "mts_write_field")
 
+    def set_shapes(self, tile: int = 0, damp_warps: int = 0):
+        """Launch shapes: particles per tile of the gather kernels (0 keeps the
+        tiles) and damping warps per CTA (0 = as many as fit)."""
+        _check(lib().mts_body_set_shapes(self._h, int(tile), int(damp_warps)),
+               "mts_body_set_shapes")
+
+    def shapes(self):
+        t, w = C.c_int32(), C.c_int32()
+        _check(lib().mts_body_shapes(self._h, C.byref(t), C.byref(w)), "mts_body_shapes")
+        return {"tile": t.value, "damp_warps": w.value}
+
+    def autotune(self, substeps: int = 8, ramp: float = 0.0):
+        """Time every candidate launch shape on `substeps` substeps from the
+        current state, apply the fastest and restore the state."""
+        t, w, ms = C.c_int32(), C.c_int32(), C.c_double()
+        _check(lib().mts_body_autotune(self._h, int(substeps), float(ramp), C.byref(t),
+                                       C.byref(w), C.byref(ms)), "mts_body_autotune")
+        return {"tile": t.value, "damp_warps": w.value, "ms": ms.value}
+
     def save_state(self) -> bytes:
         """Snapshot of the evolving state (bit-exact resume with load_state)."""
         nb = C.c_size_t()
@@ -473,6 +498,11 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def autotune(self, substeps: int = 8, ramp: float = 0.0):
+        """mts_batch_autotune: tune every body's launch shapes in turn."""
+        _check(lib().mts_batch_autotune(self._h, int(substeps), float(ramp)), "mts_batch_autotune")
+        return [b.shapes() for b in self.bodies]
 
     def advance(self, params) -> list:
         """One slow step of every body; params: one dict of advance_slow_step
@@ -534,10 +564,11 @@ def slow_steps(body: Body, theta, steps):
     return _SlowSteps.apply(theta)
 
 
-def body_from_case(ctx: Context, case, precision: int = FP64, damp_layout: int = DAMP_AUTO) -> Body:
+def body_from_case(ctx: Context, case, precision: int = FP64, damp_layout: int = DAMP_AUTO,
+                   tile: int = 0) -> Body:
     """Body with the material, damping, diffusion and BCs of a synth Case."""
     b = Body(ctx, case.X, case.dx, case.h_over_dx, precision, damp_layout,
-             getattr(case, "dx_axis", None))
+             getattr(case, "dx_axis", None), tile)
     m = case.material
     b.set_material(ELASTIC_SVK if m.model == "svk" else NEOHOOKE_J2, m.rho0, m.E, m.nu,
                    m.sigma0, m.sigma_inf, m.delta, m.H)
