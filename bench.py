@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--cpu-substeps", type=int, default=2,
                     help="substeps in the oracle CPU-baseline sample (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: launch shapes from the autotuner after the first warm-up step")
     ap.add_argument("--batch-count", type=int, default=64,
                     help="instances of the batched workload (0 = skip)")
     ap.add_argument("--next-rows", type=int, default=1,
@@ -281,6 +283,11 @@ def measure_batch(ctx, args, M, rank=0, world=1, dist=None):
     bodies = [M.body_from_case(ctx, c, M.MIXED) for c in cases]
     bt = M.Batch(ctx, bodies)
     bt.advance([_batch_params(c, b, 1) for c, b in zip(cases, bodies)])      # warm-up
+    # launch shapes per body from the autotuner (untimed set-up)
+    t0 = time.perf_counter()
+    shapes = bt.autotune(substeps=8, ramp=0.0)
+    tune_s = time.perf_counter() - t0
+    bt.advance([_batch_params(c, b, 1) for c, b in zip(cases, bodies)])      # capture
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -308,6 +315,9 @@ def measure_batch(ctx, args, M, rank=0, world=1, dist=None):
             "batched_value": upd_b / tb, "sequential_value": upd_s / ts,
             "speedup": (upd_b / tb) / (upd_s / ts), "unit": UNIT,
             "substeps_range": [int(min(r.substeps for r in reps)), int(max(r.substeps for r in reps))],
+            "shapes": {k: sum(1 for sh in shapes if f"tile {sh['tile']}, {sh['damp_warps']} damping warps" == k)
+                       for k in sorted({f"tile {sh['tile']}, {sh['damp_warps']} damping warps" for sh in shapes})},
+            "autotune_s": tune_s,
             "timing": "host wall clock around one slow step of every instance (slow step 2 "
                       "batched, slow step 3 one body after another), stream synchronised, "
                       "max over ranks"}
@@ -439,9 +449,15 @@ def run_ours(args, rank, world, local):
                                     ke_mode=plan.ke_mode, max_substeps=plan.max_substeps,
                                     check_every=args.check_every)
 
-    # warm-up slow steps on the production path
+    # warm-up slow steps on the production path; the launch shapes come from
+    # the autotuner after the first one (untimed set-up)
+    tune = None
     for w in range(args.warmup):
         slow_step(w + 1)
+        if w == 0 and args.autotune:
+            t0 = time.perf_counter()
+            tune = gb.autotune(substeps=8, ramp=2 / plan.n_ramp)
+            tune["seconds"] = time.perf_counter() - t0
     gb.set_profiling(0)
     torch.cuda.synchronize()
     if dist:
@@ -567,7 +583,8 @@ def run_ours(args, rank, world, local):
                    "substeps_per_step": [r.substeps for r in reps],
                    "converged": [r.converged for r in reps],
                    "l2": "working set larger than L2 (no flush)",
-                   "parallelism": "replicas" if world > 1 else "single", "setup_s": setup_s},
+                   "parallelism": "replicas" if world > 1 else "single", "setup_s": setup_s,
+                   "launch_shapes": gb.shapes(), "autotune": tune},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm if achieved else None,
