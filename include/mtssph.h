@@ -277,9 +277,12 @@ mts_status mts_advance_slow_step(mts_body *body, const mts_step_params *params,
 mts_status mts_batch_create(mts_ctx *ctx, int32_t count, mts_body *const *bodies, mts_batch **out);
 mts_status mts_batch_advance(mts_batch *batch, const mts_step_params *params,
                              mts_step_report *reports);
-/* mts_body_autotune on every body of the batch, one after another (each body
- * keeps its own choice); the batch graph is captured again at the next
- * advance. */
+/* Autotuner of a batch: the bodies run concurrently in the batch graph, so
+ * one launch shape at a time is applied to every body (tile 256 or 512, or
+ * 64 or 128 for FP64 bodies; 1, 2 or 4 damping warps) and one batch slow step
+ * of `substeps` substeps (load scale `ramp`, no stop) is timed from the
+ * bodies' saved states; the fastest shape is applied and the states are
+ * restored.  The batch graph is captured again at the next advance. */
 mts_status mts_batch_autotune(mts_batch *batch, int32_t substeps, double ramp);
 void mts_batch_destroy(mts_batch *batch);
 

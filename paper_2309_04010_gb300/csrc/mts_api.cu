@@ -1074,13 +1074,88 @@ mts_status mts_batch_create(mts_ctx *ctx, int32_t count, mts_body *const *bodies
 }
 
 mts_status mts_batch_autotune(mts_batch *bt, int32_t substeps, double ramp) {
-    if (!bt) {
-        set_error("mts_batch_autotune: NULL batch");
+    if (!bt || substeps < 1 || substeps > 1000 || !std::isfinite(ramp)) {
+        set_error("mts_batch_autotune: NULL batch, substeps %d (1..1000) or ramp %g", substeps, ramp);
         return MTS_ERR_INVALID_ARG;
     }
+    const int nb = (int)bt->bodies.size();
     for (mts_body *b : bt->bodies)
-        MTS_TRY(mts_body_autotune(b, substeps, ramp, nullptr, nullptr, nullptr));
-    return MTS_OK;
+        if (!b->has_material) {
+            set_error("mts_batch_autotune: a body has no material");
+            return MTS_ERR_STATE;
+        }
+    MTS_CUDA(cudaSetDevice(bt->ctx->device));
+    // every body's state, restored before each trial and at the end
+    std::vector<std::vector<unsigned char>> saved(nb);
+    for (int i = 0; i < nb; ++i) {
+        size_t bytes = 0;
+        MTS_TRY(mts_save_state(bt->bodies[i], nullptr, &bytes));
+        saved[i].resize(bytes);
+        MTS_TRY(mts_save_state(bt->bodies[i], saved[i].data(), &bytes));
+    }
+    auto restore = [&]() -> mts_status {
+        for (int i = 0; i < nb; ++i)
+            MTS_TRY(mts_load_state(bt->bodies[i], saved[i].data(), saved[i].size()));
+        return MTS_OK;
+    };
+    std::vector<mts_step_params> p(nb);
+    for (auto &q : p) {
+        q = mts_step_params{};
+        q.ramp_value = ramp;
+        q.ke_tol = -1.0;
+        q.ke_ref = 1.0;
+        q.max_substeps = substeps;
+    }
+    std::vector<mts_step_report> rep(nb);
+    // one shape for the whole batch at a time (the bodies run concurrently,
+    // so the batch is timed as a whole): tile index into each body's tile set
+    const int tiles32[2] = {256, 512}, tiles64[2] = {64, 128}, warps[3] = {1, 2, 4};
+    cudaEvent_t e0, e1;
+    MTS_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    }
+    mts_status s = MTS_OK;
+    int best_ti = 1, best_w = 4;
+    double best = 1e300;
+    for (int ti = 0; ti < 2 && s == MTS_OK; ++ti)
+        for (int wi = 0; wi < 3 && s == MTS_OK; ++wi) {
+            for (mts_body *b : bt->bodies) {
+                s = mts_body_set_shapes(b, b->rsize == 4 ? tiles32[ti] : tiles64[ti], warps[wi]);
+                if (s != MTS_OK) break;
+            }
+            for (int r = 0; r < 2 && s == MTS_OK; ++r) {   // capture, then time
+                s = restore();
+                if (s != MTS_OK) break;
+                if (r == 1 && cudaEventRecord(e0, bt->ctx->stream) != cudaSuccess) {
+                    s = cuda_fail(cudaGetLastError(), "cudaEventRecord");
+                    break;
+                }
+                s = mts_batch_advance(bt, p.data(), rep.data());
+                if (s == MTS_OK && r == 1) {
+                    cudaError_t e = cudaEventRecord(e1, bt->ctx->stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0.0f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e != cudaSuccess) {
+                        s = cuda_fail(e, "batch autotune timing");
+                    } else if (ms < best) {
+                        best = ms;
+                        best_ti = ti;
+                        best_w = warps[wi];
+                    }
+                }
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (mts_body *b : bt->bodies) {
+        if (s != MTS_OK) break;
+        s = mts_body_set_shapes(b, b->rsize == 4 ? tiles32[best_ti] : tiles64[best_ti], best_w);
+    }
+    if (s == MTS_OK) s = restore();
+    return s;
 }
 
 void mts_batch_destroy(mts_batch *bt) {
