@@ -13,8 +13,8 @@
  * the neighbour test is bit-reproducible.  No blocking, fusion or reordering
  * beyond what the definitions state.
  *
- * Readings of the paper where it is silent or garbled (each one is listed in
- * the design doc):
+ * Readings of the paper where it is silent or garbled (the same readings are
+ * implemented by the CUDA library):
  *   - kernel: Wendland C2 with h = h_over_dx * dx and support 2h (the paper
  *     only says "kernel function", Sec. 3.1);
  *   - grad_a W_ab = W'(r) (X_a - X_b) / r  (derivative with respect to X_a);
