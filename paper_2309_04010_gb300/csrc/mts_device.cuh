@@ -139,6 +139,14 @@ __device__ __forceinline__ void cp_async_wait_group() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// bulk prefetch of [g, g + bytes) into L2 (no completion to wait for; g and
+// bytes multiples of 16)
+__device__ __forceinline__ void prefetch_l2_bulk(const void *g, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(__cvta_generic_to_global(g)),
+                 "r"(bytes)
+                 : "memory");
+}
+
 // ------------------------------------------------------------------ math
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }

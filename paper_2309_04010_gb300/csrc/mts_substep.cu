@@ -167,6 +167,17 @@ __global__ void __launch_bounds__(TileThreads<R>::v) k_stress(Args<R> A) {
     }
 }
 
+// L2 prefetch of the level slots [m0, m1) of one owner group: a damping
+// launch prefetches the next launch's groups, so their slots stream from HBM
+// while its own chains run instead of at the start of the next launch
+template <class R>
+__device__ __forceinline__ void prefetch_group_levels(const Args<R> &A, int m0, int m1) {
+    if (m1 > m0) {
+        prefetch_l2_bulk(A.pair_ab + 32LL * m0, 128u * (unsigned)(m1 - m0));
+        prefetch_l2_bulk(A.pair_g + 32LL * m0, 32u * (unsigned)sizeof(R) * (unsigned)(m1 - m0));
+    }
+}
+
 // --------------------------------------------------------------------- K_B
 template <class R, int D>
 __global__ void __launch_bounds__(TileThreads<R>::v) k_force(Args<R> A) {
@@ -476,7 +487,7 @@ __device__ __forceinline__ void damp_sweeps(bool cons, int mode, int nl, const u
 
 template <class R, int D>
 __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long long g_end,
-                                             int mode) {
+                                             int mode, long long n_begin, long long n_end) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int P = Pad<D>::v;
     constexpr int NB = 1 << D;
@@ -495,6 +506,14 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     const bool cons = __ldg(A.grp_cons + g) != 0;
     const int nl = l1 - l0;
     const int mb = A.mb;
+    // the next launch's group of the same rank, prefetched into L2 while this
+    // warp's chain runs (n_begin = n_end: none)
+    const long long h = n_begin + (g - g_begin);
+    int m0 = 0, m1 = 0;
+    if (lane == 0 && h < n_end) {
+        m0 = __ldg(A.grp_lvl + h);
+        m1 = __ldg(A.grp_lvl + h + 1);
+    }
     unsigned char *base = smem + (size_t)warp * DampSmem<R, D>::bytes(mb, A.max_group_levels);
     R *sv = reinterpret_cast<R *>(base);                 // NB * mb slots + 1 dummy slot
     R *sg = reinterpret_cast<R *>(base + DampSmem<R, D>::vbytes(mb));
@@ -530,12 +549,11 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     }
     cp_async_wait_all();
     __syncwarp();
+    if (lane == 0) prefetch_group_levels<R>(A, m0, m1);
     const R im = (R)(1.0 / A.mass);
     const R hcim = (R)(0.5 * dt) * A.eta * im;   // (dt/2) eta / m
     const bool tr = A.transpose != 0;
     unsigned char *svb = reinterpret_cast<unsigned char *>(sv);
-    // a group that touches no constrained particle has no negative coefficient;
-    // in one that does, a level without a constrained pair takes the free code
     // a group that touches no constrained particle has no negative
     // coefficient and runs the free-pair loop alone
     if (nl > 0) {
@@ -551,6 +569,11 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
             ld_vec<R, P>(vv, sv + (size_t)damp_slot_pos(e * mb + t, SB) * P);
             st_vec<R, P>(A.v + (long long)(ts[e] + t) * P, vv);
         }
+    // a next launch with more groups than this one: the rest, after this
+    // warp's own work
+    if (lane == 0)
+        for (long long hh = h + (g_end - g_begin); hh < n_end; hh += g_end - g_begin)
+            prefetch_group_levels<R>(A, __ldg(A.grp_lvl + hh), __ldg(A.grp_lvl + hh + 1));
 }
 
 // ------------------------------------------------- damping, wide layout
@@ -1513,14 +1536,18 @@ mts_status damping_run(mts_body *b, const Args<R> &A, long long *nlaunch) {
     int cols[8], nc = 0;
     for (int c = 0; c < (1 << D); ++c)
         if (b->col_off[c + 1] > b->col_off[c]) cols[nc++] = c;
-    auto launch = [&](int c, int mode) -> mts_status {
+    // cn: the colour of the next launch (-1: none), whose level slots the
+    // warp-per-group kernel prefetches into L2
+    auto launch = [&](int c, int mode, int cn) -> mts_status {
         const long long g0 = b->col_off[c], g1 = b->col_off[c + 1];
         if (wide) {
             MTS_CUDA(launch_chain(b, k_damp_wide<R, D>, (unsigned)(g1 - g0), (unsigned)kWideThreads,
                                   smem, A, g0, mode));
         } else {
+            const long long n0 = cn >= 0 ? b->col_off[cn] : 0, n1 = cn >= 0 ? b->col_off[cn + 1] : 0;
             const unsigned grid = (unsigned)((g1 - g0 + W - 1) / W);
-            MTS_CUDA(launch_chain(b, k_damp<R, D>, grid, (unsigned)(W * 32), smem, A, g0, g1, mode));
+            MTS_CUDA(launch_chain(b, k_damp<R, D>, grid, (unsigned)(W * 32), smem, A, g0, g1, mode,
+                                  n0, n1));
         }
         if (nlaunch) ++*nlaunch;
         return MTS_OK;
@@ -1528,9 +1555,9 @@ mts_status damping_run(mts_body *b, const Args<R> &A, long long *nlaunch) {
     // symmetric sweep over the non-empty colours: forward on all but the
     // last, forward + reverse fused on the last, then reverse
     if (nc == 0) return MTS_OK;
-    for (int i = 0; i < nc - 1; ++i) MTS_TRY(launch(cols[i], 1));
-    MTS_TRY(launch(cols[nc - 1], 3));
-    for (int i = nc - 2; i >= 0; --i) MTS_TRY(launch(cols[i], 2));
+    for (int i = 0; i < nc - 1; ++i) MTS_TRY(launch(cols[i], 1, cols[i + 1]));
+    MTS_TRY(launch(cols[nc - 1], 3, nc >= 2 ? cols[nc - 2] : -1));
+    for (int i = nc - 2; i >= 0; --i) MTS_TRY(launch(cols[i], 2, i > 0 ? cols[i - 1] : -1));
     return MTS_OK;
 }
 
