@@ -53,8 +53,12 @@ typedef struct mts_body mts_body;
 typedef struct mts_batch mts_batch;
 
 /* Device allocator hook.  alloc returns a device pointer (NULL on failure),
- * release frees it.  Pass NULL to mts_ctx_create to use cudaMalloc/cudaFree.
- * The Python binding passes PyTorch's caching allocator here. */
+ * aligned to at least 16 bytes (the kernels move arrays with 16-byte vector
+ * loads and asynchronous copies; cudaMalloc and PyTorch's caching allocator
+ * align to 256 bytes or more); release frees it.  A misaligned pointer is
+ * released again and the call fails with MTS_ERR_INVALID_ARG.  Pass NULL to
+ * mts_ctx_create to use cudaMalloc/cudaFree.  The Python binding passes
+ * PyTorch's caching allocator here. */
 typedef struct {
     void *(*alloc)(size_t bytes, void *user);
     void (*release)(void *ptr, size_t bytes, void *user);

@@ -60,6 +60,12 @@ mts_status dalloc_into(mts_ctx *ctx, void **p, size_t bytes) {
         set_error("device allocation of %zu bytes failed", bytes);
         return MTS_ERR_OOM;
     }
+    if (reinterpret_cast<uintptr_t>(*p) & 15u) {
+        dfree(ctx, *p);
+        *p = nullptr;
+        set_error("the allocator returned a pointer not aligned to 16 bytes");
+        return MTS_ERR_INVALID_ARG;
+    }
     return MTS_OK;
 }
 

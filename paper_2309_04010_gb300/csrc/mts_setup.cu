@@ -747,6 +747,10 @@ struct Tmp {
     template <class T>
     T *get(size_t count) {
         void *p = dalloc(ctx, count * sizeof(T) + 16);
+        if (p && (reinterpret_cast<uintptr_t>(p) & 15u)) {   // see dalloc_into
+            dfree(ctx, p);
+            p = nullptr;
+        }
         if (p) ptrs.push_back(p);
         return (T *)p;
     }

@@ -189,3 +189,36 @@ def test_roller_bcs_adjoint_dot_product(ctx):
     lhs = float((jv.numpy() * lam).sum())
     rhs = float((dth.numpy() * th_g).sum())
     assert abs(lhs - rhs) <= 1e-9 * max(abs(lhs), abs(rhs)), (lhs, rhs)
+
+
+def test_misaligned_allocator_is_refused():
+    """An allocator hook whose pointers are off the 16-byte grid: body creation
+    fails with an invalid-argument status and every block is given back."""
+    import ctypes as C
+    import torch
+    live = {}
+
+    def _alloc(nbytes, user):
+        t = torch.empty(int(nbytes) + 16, dtype=torch.uint8, device="cuda")
+        p = t.data_ptr() + 8
+        live[p] = t
+        return p
+
+    def _release(ptr, nbytes, user):
+        live.pop(ptr, None)
+
+    cb = (M.Allocator.ALLOC(_alloc), M.Allocator.RELEASE(_release))
+    al = M.Allocator(cb[0], cb[1], None)
+    st = torch.cuda.Stream()
+    h = C.c_void_p()
+    assert M.lib().mts_ctx_create(0, C.c_void_p(st.cuda_stream), C.byref(al), C.byref(h)) == M.OK
+    case = B.bar2d(nx=12, ny=4)
+    X = np.ascontiguousarray(case.X, dtype=np.float64)
+    desc = M.BodyDesc(2, M.MIXED, case.n, X.ctypes.data, case.dx, case.h_over_dx,
+                      M.DAMP_AUTO, 0, (C.c_double * 3)(0.0, 0.0, 0.0))
+    hb = C.c_void_p()
+    s = M.lib().mts_body_create(h, C.byref(desc), C.byref(hb))
+    st.synchronize()
+    M.lib().mts_ctx_destroy(h)
+    assert s == M.ERR_INVALID_ARG
+    assert not live
