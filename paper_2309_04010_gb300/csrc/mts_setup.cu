@@ -688,6 +688,10 @@ __device__ int find_slot(const int32_t *h, long long len, int32_t key) {
     return (int)lo;
 }
 
+// longest neighbour list whose visiting order is bank-balanced (longer lists
+// keep the CSR order)
+constexpr int kEllOrderCap = 128;
+
 __global__ void k_local_ell(const long long *off, const int32_t *idx, long long n, int T,
                             long long ntiles, const long long *hoff, const int32_t *halo,
                             const long long *loff, int32_t *tw, uint16_t *lell, uint16_t *lself) {
@@ -706,9 +710,40 @@ __global__ void k_local_ell(const long long *off, const int32_t *idx, long long 
     int self = find_slot(h, hl, (int32_t)i);
     lself[i] = (uint16_t)self;
     long long deg = off[i + 1] - off[i];
-    for (long long j = 0; j < width; ++j)
-        lell[loff[t] + j * T + lane] =
-            (uint16_t)(j < deg ? find_slot(h, hl, idx[off[i] + j]) : self);
+    uint16_t *out = lell + loff[t] + lane;
+    if (width > kEllOrderCap) {   // CSR order
+        for (long long j = 0; j < width; ++j)
+            out[j * T] = (uint16_t)(j < deg ? find_slot(h, hl, idx[off[i] + j]) : self);
+        return;
+    }
+    // Visiting order: the gathers stage one 16-byte unit (or a 48-byte record
+    // of three) per halo slot, so slot s sits in bank group s mod 8 (3s mod 8).
+    // At step j, lane k of a quarter-warp takes its first unvisited slot with
+    // s = k + j (mod 8), else its first unvisited slot: the eight lanes of a
+    // 16-byte shared load then read distinct bank groups whenever their lists
+    // allow.  Padding entries (the particle itself, zero contribution) take
+    // part like any slot.
+    uint16_t sl[kEllOrderCap];
+    for (long long e = 0; e < width; ++e)
+        sl[e] = (uint16_t)(e < deg ? find_slot(h, hl, idx[off[i] + e]) : self);
+    uint32_t used[kEllOrderCap / 32];
+    for (int q = 0; q < kEllOrderCap / 32; ++q) used[q] = 0u;
+    const int k = lane & 7;
+    for (long long j = 0; j < width; ++j) {
+        const int r = (int)((k + j) & 7);
+        int pick = -1, any = -1;
+        for (int e = 0; e < (int)width; ++e) {
+            if ((used[e >> 5] >> (e & 31)) & 1u) continue;
+            if (any < 0) any = e;
+            if ((sl[e] & 7) == r) {
+                pick = e;
+                break;
+            }
+        }
+        if (pick < 0) pick = any;
+        used[pick >> 5] |= 1u << (pick & 31);
+        out[j * T] = sl[pick];
+    }
 }
 
 __global__ void k_group_max(const long long *lvl_pair, const int32_t *grp_lvl, long long ng,
