@@ -692,7 +692,7 @@ __device__ int find_slot(const int32_t *h, long long len, int32_t key) {
 // keep the CSR order)
 constexpr int kEllOrderCap = 128;
 
-__global__ void k_local_ell(const long long *off, const int32_t *idx, long long n, int T,
+__global__ void k_local_ell(const long long *off, const int32_t *idx, long long n, int T, int dim,
                             long long ntiles, const long long *hoff, const int32_t *halo,
                             const long long *loff, int32_t *tw, uint16_t *lell, uint16_t *lself) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -716,26 +716,29 @@ __global__ void k_local_ell(const long long *off, const int32_t *idx, long long 
             out[j * T] = (uint16_t)(j < deg ? find_slot(h, hl, idx[off[i] + j]) : self);
         return;
     }
-    // Visiting order: the gathers stage one 16-byte unit (or a 48-byte record
-    // of three) per halo slot, so slot s sits in bank group s mod 8 (3s mod 8).
-    // At step j, lane k of a quarter-warp takes its first unvisited slot with
-    // s = k + j (mod 8), else its first unvisited slot: the eight lanes of a
-    // 16-byte shared load then read distinct bank groups whenever their lists
-    // allow.  Padding entries (the particle itself, zero contribution) take
-    // part like any slot.
+    // Visiting order: the 3D gathers stage one 16-byte unit (or a 48-byte
+    // record of three) per halo slot, so slot s sits in bank group s mod 8
+    // (3s mod 8) and a 16-byte shared load serves eight lanes at a time.  At
+    // step j, lane k takes its first unvisited slot with s = k + j (mod M),
+    // else its first unvisited slot: the lanes served together then read
+    // distinct banks whenever their lists allow.  M = 8 in 3D; M = 16 in 2D,
+    // where the positions are 8-byte slots loaded sixteen lanes at a time.
+    // Padding entries (the particle itself, zero contribution) take part like
+    // any slot.
     uint16_t sl[kEllOrderCap];
     for (long long e = 0; e < width; ++e)
         sl[e] = (uint16_t)(e < deg ? find_slot(h, hl, idx[off[i] + e]) : self);
     uint32_t used[kEllOrderCap / 32];
     for (int q = 0; q < kEllOrderCap / 32; ++q) used[q] = 0u;
-    const int k = lane & 7;
+    const int mask = dim == 2 ? 15 : 7;
+    const int k = lane & mask;
     for (long long j = 0; j < width; ++j) {
-        const int r = (int)((k + j) & 7);
+        const int r = (int)((k + j) & mask);
         int pick = -1, any = -1;
         for (int e = 0; e < (int)width; ++e) {
             if ((used[e >> 5] >> (e & 31)) & 1u) continue;
             if (any < 0) any = e;
-            if ((sl[e] & 7) == r) {
+            if ((sl[e] & mask) == r) {
                 pick = e;
                 break;
             }
@@ -904,7 +907,7 @@ mts_status build_tiles(mts_body *b, Tmp &tmp, cudaStream_t st, int T) {
     MTS_TRY(to_host(&len, b->lell_off + ntiles, 1, st));
     MTS_TRY(dalloc_t(ctx, &b->lell, std::max(len, 1LL)));
     MTS_TRY(dalloc_t(ctx, &b->lself, n));
-    k_local_ell<<<grid_for(ntiles * T), TPB, 0, st>>>(b->nb_off, b->nb_idx, n, T, ntiles,
+    k_local_ell<<<grid_for(ntiles * T), TPB, 0, st>>>(b->nb_off, b->nb_idx, n, T, b->dim, ntiles,
                                                         b->halo_off, b->halo_idx, b->lell_off,
                                                         b->tile_w, b->lell, b->lself);
     b->T = T;
