@@ -1240,6 +1240,34 @@ mts_status mts_substep_partial(mts_body *b, double dt, double ramp, int32_t upto
     return MTS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// index of the first NaN or infinity of x[0, n), -1 if none.  A double is not
+// finite exactly when its eleven exponent bits are all ones; the test runs on
+// the bit patterns in blocks with a branch-free count (vectorised by the
+// compiler), and only a block that holds one is searched element by element.
+int64_t first_nonfinite(const double *x, int64_t n) {
+    constexpr uint64_t kExp = 0x7ff0000000000000ull;
+    constexpr int64_t kB = 4096;
+    for (int64_t b0 = 0; b0 < n; b0 += kB) {
+        const int64_t b1 = std::min(n, b0 + kB);
+        uint64_t bad = 0;
+        for (int64_t i = b0; i < b1; ++i) {
+            uint64_t v;
+            std::memcpy(&v, x + i, sizeof v);
+            bad += (v & kExp) == kExp;
+        }
+        if (bad)
+            for (int64_t i = b0; i < b1; ++i)
+                if (!std::isfinite(x[i])) return i;
+    }
+    return -1;
+}
+}  // namespace
+
+extern "C" {
+
 mts_status mts_read_field(mts_body *b, int32_t field, double *out, int64_t len) {
     if (!b || !out || !valid_field(field)) {
         set_error("mts_read_field: invalid arguments");
@@ -1268,11 +1296,10 @@ mts_status mts_write_field(mts_body *b, int32_t field, const double *in, int64_t
         set_error("mts_write_field: len %lld, expected %lld", (long long)len, (long long)(b->n * w));
         return MTS_ERR_INVALID_ARG;
     }
-    for (int64_t t = 0; t < len; ++t)
-        if (!std::isfinite(in[t])) {
-            set_error("mts_write_field: non-finite value at %lld", (long long)t);
-            return MTS_ERR_NONFINITE;
-        }
+    if (const int64_t t = first_nonfinite(in, len); t >= 0) {
+        set_error("mts_write_field: non-finite value at %lld", (long long)t);
+        return MTS_ERR_NONFINITE;
+    }
     MTS_CUDA(cudaSetDevice(b->ctx->device));
     MTS_CUDA(cudaMemcpyAsync(b->scratch, in, len * 8, cudaMemcpyHostToDevice, b->ctx->stream));
     MTS_TRY(scratch_to_field(b, field));

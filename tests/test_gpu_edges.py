@@ -258,3 +258,22 @@ def test_wide_support_every_stage(ctx, precision, tol):
         assert rel(gb.read(M.F_PB), ob.read(O.F_PB)) < tol
         assert rel(gb.read(M.F_V), ob.read(O.F_V)) < tol
         assert rel(gb.read(M.F_U), ob.read(O.F_U)) < tol
+
+
+def test_write_rejects_one_nonfinite_value(ctx):
+    """A single infinity deep inside an otherwise finite field is found (its
+    index is reported) and the field is left as it was."""
+    case = B.bar2d(nx=200, ny=20)         # 8,000 values
+    gb = M.body_from_case(ctx, case, M.MIXED)
+    before = gb.read(M.F_U)
+    U = B.random_field(case.n, 2, 1e-6, 31)
+    k = 2 * case.n - 7                    # flat index, past the first 4096-value block
+    U.reshape(-1)[k] = -np.inf
+    with pytest.raises(M.MtsError) as e:
+        gb.write(M.F_U, U)
+    assert e.value.status == M.ERR_NONFINITE
+    assert f"at {k}" in str(e.value)
+    assert np.array_equal(gb.read(M.F_U), before)
+    U.reshape(-1)[k] = 0.0
+    gb.write(M.F_U, U)
+    assert np.array_equal(gb.read(M.F_U), U)
