@@ -1296,12 +1296,15 @@ mts_status mts_write_field(mts_body *b, int32_t field, const double *in, int64_t
         set_error("mts_write_field: len %lld, expected %lld", (long long)len, (long long)(b->n * w));
         return MTS_ERR_INVALID_ARG;
     }
+    // the copy into the scratch buffer runs while the host checks the values;
+    // only a clean field is moved from there into the body's state
+    MTS_CUDA(cudaSetDevice(b->ctx->device));
+    MTS_CUDA(cudaMemcpyAsync(b->scratch, in, len * 8, cudaMemcpyHostToDevice, b->ctx->stream));
     if (const int64_t t = first_nonfinite(in, len); t >= 0) {
+        MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));   // the copy has read `in`
         set_error("mts_write_field: non-finite value at %lld", (long long)t);
         return MTS_ERR_NONFINITE;
     }
-    MTS_CUDA(cudaSetDevice(b->ctx->device));
-    MTS_CUDA(cudaMemcpyAsync(b->scratch, in, len * 8, cudaMemcpyHostToDevice, b->ctx->stream));
     MTS_TRY(scratch_to_field(b, field));
     MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
     return MTS_OK;
