@@ -398,8 +398,9 @@ mts_status mts_adjoint_equilibrium(mts_body *body, int64_t max_iters, double tol
  * afford the device-wide synchronisation of cudaMalloc/cudaFree, and code that
  * must not be able to fail with out-of-memory after set-up.
  *
- * Computes E_k = sum_i 1/2 mass |v_i|^2 and max_i |v_i| (FP64 accumulation,
- * the reduction the slow-step driver applies after every substep).
+ * Computes E_k = sum_i 1/2 mass |v_i|^2 and max_i |v_i| (|v_i|^2 formed in the
+ * velocities' precision, then FP64 accumulation: the reduction the slow-step
+ * driver applies after every substep).
  *   v_dev   device, n x dim contiguous velocities: float for MTS_MIXED,
  *           double for MTS_FP64 (caller-owned, read only)
  *   out_dev device, 2 doubles (caller-owned): out_dev[0] = E_k, out_dev[1] = max |v|

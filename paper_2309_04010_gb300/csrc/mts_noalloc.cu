@@ -45,12 +45,11 @@ __global__ void __launch_bounds__(kThreads) k_ke_partials(const R *v, long long 
     double ke = 0.0, vmax = 0.0;
     for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n;
          i += (long long)gridDim.x * kThreads) {
-        double v2 = 0.0;
+        // |v|^2 in the velocities' own precision, as the substep loop forms it
+        R v2r = R(0);
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-            const double x = (double)v[i * D + k];
-            v2 += x * x;
-        }
+        for (int k = 0; k < D; ++k) v2r += v[i * D + k] * v[i * D + k];
+        const double v2 = (double)v2r;
         ke += half_m * v2;
         vmax = fmax(vmax, sqrt(v2));
     }
