@@ -226,7 +226,8 @@ typedef struct {
     double dt_slow;          /* diffusion step; 0 = no diffusion this slow step         */
     double ramp_value;       /* load scale: prescribed u = ramp * u_unit (Sec. 4.1 dt_l) */
     double dt_sub_override;  /* > 0: fixed substep size instead of the Sec. 4.1 rule     */
-    double ke_tol;           /* stop when E_k <= ke_tol * ke_ref; < 0 disables the stop  */
+    double ke_tol;           /* stop when E_k <= ke_tol * ke_ref once E_k has passed its */
+                             /* peak (see mts_advance_slow_step); < 0 disables the stop */
     double ke_ref;           /* reference energy (mode 0) or energy density (mode 1)    */
     int64_t max_substeps;    /* cap on substeps (>= 1); reaching it is not an error     */
     int32_t ke_mode;         /* 0: total E_k; 1: E_k per unit volume                    */
@@ -255,7 +256,11 @@ typedef struct {
 /* One slow step: jump prescribed axes to ramp * u_unit (v = 0 there), run
  * the diffusion step if dt_slow > 0, then substeps (stress, force and kick,
  * symmetric pairwise damping, BC and drift, FP64 kinetic energy) until
- * E_k <= ke_tol * ke_ref or max_substeps.  The substep size follows
+ * E_k <= ke_tol * ke_ref or max_substeps.  After the load or diffusion event
+ * the kinetic energy first rises, then decays under the damping to the
+ * criterion (Sec. 5.1 and 5.3), so the criterion is only tested from the
+ * first substep n whose E_k(n) <= E_k(n-1), with E_k(0) = 0 (a body that
+ * does not move at all is armed at its first substep).  The substep size follows
  * Sec. 4.1: dt0 = 0.6 h / c_s, then 0.6 min(h / (c_s + |v|max),
  * sqrt(h / |dv/dt|max)) with c_s = sqrt(K / rho0).  The stop flag lives on the
  * device; with check_every = 0 a conditional WHILE graph node runs exactly the

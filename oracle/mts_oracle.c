@@ -37,7 +37,9 @@
  *   - diffusion (Sec. 3.2 reduced to a scalar): one-pass pairwise Laplacian
  *     dc_i/dt = 2 D sum_j V (c_i - c_j) W'(r_ij)/r_ij in the reference
  *     configuration, Jacobi update;
- *   - time step Sec. 4.1 with |v|max, |dv/dt|max from the previous substep.
+ *   - time step Sec. 4.1 with |v|max, |dv/dt|max from the previous substep;
+ *   - kinetic-energy stop (Sec. 4.2): tested once E_k has passed its peak
+ *     after the slow step's load or diffusion event (Sec. 5.1, 5.3).
  */
 #include <math.h>
 #include <stdint.h>
@@ -1211,6 +1213,14 @@ int ob_diffusion_step(ob_body *b, double dt) {
 /* ------------------------------------------------------------------ */
 /* Slow step (Sec. 4.2): outer increment, then damped substeps until the */
 /* kinetic-energy criterion holds or max_substeps is reached.           */
+/* After a load or diffusion event the kinetic energy first rises to a   */
+/* peak and then decays under the damping to the criterion (Sec. 5.1 and */
+/* Sec. 5.3, the kinetic-energy evolution after one stretching or one    */
+/* diffusion step).  The criterion is therefore tested only once the     */
+/* energy has stopped rising: from the first substep n with              */
+/* E_k(n) <= E_k(n-1), where E_k(0) = 0 (the relaxation starts from the  */
+/* event; a body that does not move at all is armed at once).  Once      */
+/* armed it stays armed for the rest of the slow step.                   */
 /* ------------------------------------------------------------------ */
 int ob_advance_slow_step(ob_body *b, const ob_step_params *p, ob_report *rep) {
     memset(rep, 0, sizeof(*rep));
@@ -1237,13 +1247,17 @@ int ob_advance_slow_step(ob_body *b, const ob_step_params *p, ob_report *rep) {
     int64_t nsub = 0;
     double ke = 0, vmax = 0, amax = 0;
     int converged = 0;
+    double ke_prev = 0.0;   /* E_k(0) */
+    int armed = 0;
     for (;;) {
         int st = ob_substep(b, dt, p->ramp_value, &ke, &vmax, &amax);
         if (st != OB_OK) { rep->status = st; rep->substeps = nsub + 1; return st; }
         nsub++;
         rep->dt_last = dt;
+        if (ke <= ke_prev) armed = 1;       /* past the peak of E_k */
+        ke_prev = ke;
         double crit = p->ke_mode == 1 ? ke / volume : ke;
-        if (p->ke_tol >= 0.0 && crit <= p->ke_tol * p->ke_ref) { converged = 1; break; }
+        if (p->ke_tol >= 0.0 && armed && crit <= p->ke_tol * p->ke_ref) { converged = 1; break; }
         if (nsub >= p->max_substeps) break;
         if (p->dt_sub_override > 0) dt = p->dt_sub_override;
         else {

@@ -80,7 +80,8 @@ struct Control {
     double end_force[3];
     long long nsub, max_sub;
     int done, converged, status, ke_mode;
-    int use_tol, pad0;
+    int use_tol;
+    int armed;                // kinetic energy has stopped rising in this slow step
     unsigned int counter;     // last-block-done counter of the drift kernel
     unsigned int err;         // setup error bits
 };

@@ -13,7 +13,8 @@
 //   k_drift   BC (fixed axes v = 0, u = ramp u_unit) and drift u += dt v in
 //             FP64; FP64 block partials of E_k and |v|max; the last block to
 //             finish reduces all partials in a fixed order, applies the
-//             kinetic-energy stop (Sec. 4.2) and sets the next dt (Sec. 4.1).
+//             kinetic-energy stop (Sec. 4.2; tested once E_k has passed its
+//             peak after the slow step's event) and sets the next dt (Sec. 4.1).
 // Every kernel returns at once when the device stop flag is set, so a captured
 // chunk of substeps can run past convergence without changing the state.
 #include <algorithm>
@@ -899,6 +900,10 @@ __global__ void __launch_bounds__(kBlock) k_drift(Args<R> A) {
     }
     if (threadIdx.x == 0) {
         const double KE = 0.5 * A.mass * red[0][0], VM = sqrt(red[1][0]), AM = sqrt(red[2][0]);
+        // Sec. 4.2 with Sec. 5.1/5.3: after the slow step's event E_k rises to a
+        // peak, then decays to the criterion; the test is armed from the first
+        // substep with E_k(n) <= E_k(n-1) (E_k(0) = 0, the value C->ke is reset to)
+        if (KE <= C->ke) C->armed = 1;
         C->ke = KE;
         C->vmax = VM;
         C->amax = AM;
@@ -910,7 +915,7 @@ __global__ void __launch_bounds__(kBlock) k_drift(Args<R> A) {
             C->done = 1;
         } else {
             const double crit = C->ke_mode == 1 ? KE / C->volume : KE;
-            if (C->use_tol && crit <= C->ke_thr) {
+            if (C->use_tol && C->armed && crit <= C->ke_thr) {
                 C->done = 1;
                 C->converged = 1;
             } else if (C->nsub >= C->max_sub) {
@@ -938,7 +943,7 @@ __global__ void k_reset_ctrl(Control *C, double dt, double dt_fixed, double ramp
     C->dt = dt; C->dt_fixed = dt_fixed; C->ramp = ramp;
     C->max_sub = max_sub; C->ke_thr = ke_thr; C->ke_mode = ke_mode; C->use_tol = use_tol;
     C->volume = volume;
-    C->nsub = 0; C->done = 0; C->converged = 0; C->status = 0; C->counter = 0;
+    C->nsub = 0; C->done = 0; C->converged = 0; C->status = 0; C->counter = 0; C->armed = 0;
     C->ke = 0; C->vmax = 0; C->amax = 0; C->dt_last = 0;
     C->end_force[0] = C->end_force[1] = C->end_force[2] = 0;
 }
