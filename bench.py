@@ -70,7 +70,58 @@ def parse():
                     help="slow steps reversed in the FP64 reverse-mode measurement (0 = skip)")
     ap.add_argument("--ref-substeps", type=int, default=1,
                     help="oracle substeps per reference-arm step")
+    ap.add_argument("--profile-case", default=None,
+                    choices=["bar2d", "cylinder3d", "strip2d", "plate3d", "membrane_droplet3d"],
+                    help="instead of the benchmark: build this workload and run --substeps "
+                         "substeps of its first slow step(s) (the command under ncu)")
+    ap.add_argument("--substeps", type=int, default=2, help="substeps per slow step of --profile-case")
+    ap.add_argument("--slow-steps", type=int, default=1, help="slow steps of --profile-case")
+    ap.add_argument("--diffusion-mode", type=int, default=0, help="diffusion form of --profile-case")
+    ap.add_argument("--reverse", action="store_true",
+                    help="--profile-case: also reverse the last slow step (FP64 reverse mode)")
+    ap.add_argument("--membrane-mm", type=float, default=10.0,
+                    help="--profile-case membrane_droplet3d: in-plane size (the paper's is 10 mm)")
     return ap.parse_args()
+
+
+def run_profile_case(args):
+    """A known, small number of launches for an ncu capture: build the
+    workload's body (set-up), apply its first load increment (or, for the
+    diffusion workloads, one diffusion step of the stable size) and run
+    --substeps substeps with the kinetic-energy stop disabled; --reverse then
+    reverses the last slow step.  Prints one line with the substep count."""
+    from paper_2309_04010_gb300 import _build
+    _build.build()
+    from paper_2309_04010_gb300 import mtssph as M
+    from synth import bodies as B
+
+    if args.profile_case == "membrane_droplet3d":
+        case = B.membrane_droplet3d(Lx=args.membrane_mm * 1e-3, Ly=args.membrane_mm * 1e-3)
+    else:
+        case = getattr(B, args.profile_case)()
+    ctx = M.Context(0)
+    prec = M.MIXED if args.precision == "mixed" else M.FP64
+    gb = M.body_from_case(ctx, case, prec)
+    if args.diffusion_mode:
+        gb.set_diffusion_mode(args.diffusion_mode)
+    off, _ = gb.neighbors()
+    total, p, ck = 0, None, None
+    for l in range(1, args.slow_steps + 1):
+        ramp = l / case.plan.n_ramp if case.plan.n_ramp else 0.0
+        p = dict(ramp=ramp, ke_tol=-1.0, max_substeps=args.substeps, check_every=args.substeps)
+        if case.diffusion is not None:
+            p.update(dt_slow=gb.diffusion_dt()[1], ke_mode=1, force_dt=True)
+        ck = gb.save_state()
+        total += gb.advance_slow_step(**p).substeps
+    if args.reverse:
+        gb.adjoint_enable(args.substeps)
+        gb.adjoint_seed(tip_bar=[1.0] * case.dim, force_bar=[1.0] * case.dim)
+        gb.load_state(ck)
+        gb.adjoint_slow_step(args.substeps, **p)
+    print(f"profile_case workload={args.profile_case} n={case.n} nnz={int(off[-1])} "
+          f"precision={args.precision} substeps={total}")
+    gb.close()
+    ctx.close()
 
 
 def dist_env():
@@ -658,6 +709,9 @@ def run_ours(args, rank, world, local):
 
 def main():
     args = parse()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank)

@@ -15,13 +15,17 @@ relaxed through many damped substeps:
   bimetal-beam curvature (swelling coupling of App. B.2), also when the
   profile comes from the oracle's own diffusion steps (Sec. 2.2, Sec. 4.1).
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
 
 import oracle as O
 from synth import bodies as B
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")
 
 
 # --------------------------------------------------------------------------
@@ -255,3 +259,45 @@ def test_diffused_profile_bends_with_closed_form_curvature():
     kappa, tip = _relaxed_curvature(ob, idx, nx, dx, E, nu, beta)
     assert kappa == pytest.approx(k_cf, rel=0.08)
     assert tip == pytest.approx((1 - math.cos(k_cf * L)) / k_cf, rel=0.05)
+
+
+# --------------------------------------------------------------------------
+# P16: substeps per slow step against the paper's efficiency tables
+# --------------------------------------------------------------------------
+def test_necking_substeps_per_slow_step_in_paper_range():
+    """The paper's 2D necking specimen (Sec. 5.1: 53.334 x 12.826 mm at
+    spacing 0.25652 mm, its J2 material table, eta = 1e4, 10 mm of symmetric
+    stretch in 10,000 steps, stop at 0.5 % of E_e) takes 3.26e5 substeps over
+    1e4 slow steps, 32.6 per slow step.  The oracle's first slow steps on the
+    same body (without the 1.8 % imperfection) must lie within a factor of
+    ten of that (same order of magnitude; not a parity target)."""
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    s, mat = g["necking_2d_setup"], g["necking_material"]
+    eff = g["efficiency_tables"]["necking_2d"]
+    per_slow = eff["substeps"] / eff["slow_steps"]
+    dp = s["spacing_m"]
+    nx, ny = int(round(s["length_m"] / dp)), int(round(s["width_m"] / dp))
+    X, idx, _ = B.box_body((nx, ny), dp, seed=B.SEED_BASE + 11)
+    K, mu = mat["bulk_modulus_pa"], mat["shear_modulus_pa"]
+    E, nu = B.moduli_from_K_mu(K, mu)
+    ob = O.OracleBody(X, dp)
+    ob.set_material(O.J2, 7850.0, E, nu, mat["initial_flow_stress_pa"],
+                    mat["saturation_flow_stress_pa"], mat["saturation_exponent"],
+                    mat["linear_hardening_pa"])
+    ob.set_damping(s["eta"])
+    half = 0.5 * s["total_stretch_m"]
+    left, right = B.layer_ids(idx, 0, 0, 3), B.layer_ids(idx, 0, nx - 3, 3)
+    ul, ur = np.zeros((left.size, 2)), np.zeros((right.size, 2))
+    ul[:, 0], ur[:, 0] = -half, half
+    ob.set_bc_displacement(left, 0b11, ul)
+    ob.set_bc_displacement(right, 0b11, ur, report_force=True)
+    ke_ref = 0.5 * mat["saturation_flow_stress_pa"] * ny * dp * s["total_stretch_m"]
+    subs = []
+    for l in range(1, 4):
+        r = ob.advance(ramp=l / s["stretching_steps"], ke_tol=s["ke_tol"], ke_ref=ke_ref,
+                       max_substeps=100000)
+        assert r.converged == 1
+        subs.append(r.substeps)
+    mean = float(np.mean(subs))
+    assert per_slow / 10 <= mean <= per_slow * 10, (subs, per_slow)

@@ -6,8 +6,9 @@ cannot afford cudaMalloc's device-wide synchronisation, code that must not hit
 out-of-memory after set-up).  This test calls it through the C ABI on
 caller-owned buffers and checks its result against the kinetic energy and
 maximum speed that the slow-step entry point reports for the same velocities,
-on two calls in a row (the second call reuses the library's static scratch).
-Kept in its own file, collected last.
+and against a plain FP64 NumPy sum over the velocities read back, on two calls
+in a row (the second call reuses the library's static scratch).  Kept in its
+own file, collected last.
 """
 import numpy as np
 import pytest
@@ -37,6 +38,12 @@ def test_noalloc_kinetic_energy_matches_slow_step_report(precision):
             dim = V.shape[1]
             mass = case.material.rho0 * case.dx ** dim
             stream = torch.cuda.current_stream().cuda_stream
+            # independent FP64 values from the velocities as read back; in mixed
+            # precision each |v|^2 is formed in FP32 by the library, so the two
+            # agree to FP32 rounding of the squares
+            v2 = (V.astype(np.float64) ** 2).sum(axis=1)
+            ke_np, vmax_np = 0.5 * mass * v2.sum(), float(np.sqrt(v2.max()))
+            tol_np = 1e-12 if precision == "fp64" else 1e-6
             for _ in range(2):                     # two calls in a row share the scratch
                 M.kinetic_energy_noalloc(v_dev.data_ptr(), prec, dim, case.n, mass,
                                          out.data_ptr(), stream)
@@ -44,6 +51,8 @@ def test_noalloc_kinetic_energy_matches_slow_step_report(precision):
                 ke, vmax = out.cpu().numpy()
                 assert abs(ke - rep.ke_final) <= 1e-12 * rep.ke_final
                 assert abs(vmax - rep.max_v) <= 1e-12 * rep.max_v
+                assert abs(ke - ke_np) <= tol_np * ke_np
+                assert abs(vmax - vmax_np) <= tol_np * vmax_np
                 out.fill_(-1.0)
             gb.close()
     finally:
