@@ -340,7 +340,7 @@ mts_status mts_save_state(const mts_body *body, void *host_buf, size_t *bytes);
 mts_status mts_load_state(mts_body *body, const void *host_buf, size_t bytes);
 
 /* ------------------------------------------------------------------ */
-/* Reverse mode (derivatives of slow steps), FP64 bodies                */
+/* Reverse mode (derivatives of slow steps), FP64 arithmetic            */
 /* ------------------------------------------------------------------ */
 /* With the substep sizes and counts of a forward run held fixed (the size
  * rule of Sec. 4.1 and the kinetic-energy stop of Sec. 4.2 are not
@@ -350,9 +350,19 @@ mts_status mts_load_state(mts_body *body, const void *host_buf, size_t bytes);
  * parameters theta = (E at fixed nu, sigma_0, sigma_inf, delta, H of the
  * hardening law App. A.3, D of Sec. 2.2, beta of App. B.2).
  *
+ * The adjoint arithmetic and its accumulators are FP64 for both precisions.
+ * A mixed-precision body (FP32 per-particle arithmetic) is reversed about its
+ * own forward states: the forward recomputation runs on the body and tapes
+ * its states in FP64, and the transposed substeps run on an FP64 twin that
+ * mts_adjoint_enable builds from the body's positions (same order, neighbour
+ * lists and damping order; it takes the body's parameters and boundary
+ * conditions at every reverse-mode call), so the gradient is that of the
+ * FP32 trajectory up to the FP32 rounding of the linearisation point.
+ *
  * mts_adjoint_enable: allocate the tape for up to max_substeps substeps of one
- *   slow step (n x 12 doubles per substep in 3D) and a zero adjoint state;
- *   MTS_ERR_STATE for a mixed-precision body.
+ *   slow step (n x 12 doubles per substep in 3D) and a zero adjoint state
+ *   (for a mixed-precision body also its FP64 twin); MTS_ERR_STATE for an
+ *   anisotropic-kernel body.
  * mts_adjoint_reset: zero the adjoint state and the pending seeds.
  * mts_adjoint_seed: add to the adjoint state the derivative of an objective
  *   with respect to the outputs of the step about to be reversed: u_bar

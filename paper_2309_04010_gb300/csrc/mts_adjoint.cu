@@ -1,4 +1,5 @@
-// mts_adjoint.cu -- reverse mode of the slow step, FP64 bodies.
+// mts_adjoint.cu -- reverse mode of the slow step (FP64 arithmetic; a mixed-
+// precision body is reversed on its FP64 twin about its own taped states).
 //
 // With its substep sizes and count held at the values of the forward run, a
 // slow step (Sec. 4.2) is a fixed composition of maps on the state (u, v,
@@ -36,13 +37,22 @@ constexpr int kTh = 8;          // parameter slots: E, s0, sinf, delta, H, D, be
 
 inline unsigned grid_n(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
-__global__ void k_tape(const double *u, const double *cp, const Control *C, long long n, int pad,
+// cp: the plastic state in the forward body's storage precision (a mixed-
+// precision body's is FP32; the tape is FP64 either way)
+template <class R>
+__global__ void k_tape(const double *u, const R *cp, const Control *C, long long n, int pad,
                        long long k, double *tape_u, double *tape_cp, double *tape_dt) {
     const long long i = blockIdx.x * (long long)kBlock + threadIdx.x;
     if (i == 0) tape_dt[k] = C->dt;
     if (i >= n) return;
     for (int q = 0; q < pad; ++q) tape_u[k * n * pad + i * pad + q] = u[i * pad + q];
-    for (int q = 0; q < 8; ++q) tape_cp[k * n * 8 + i * 8 + q] = cp[i * 8 + q];
+    for (int q = 0; q < 8; ++q) tape_cp[k * n * 8 + i * 8 + q] = (double)cp[i * 8 + q];
+}
+
+template <class R>
+__global__ void k_to_double(const R *x, long long n, double *y) {
+    const long long i = blockIdx.x * (long long)kBlock + threadIdx.x;
+    if (i < n) y[i] = (double)x[i];
 }
 
 __global__ void k_adj_setdt(Control *C, const double *tape_dt, long long k) {
@@ -618,10 +628,27 @@ mts_status adjoint_prepare(mts_body *b) {
     return b->dim == 2 ? prepare_adj<2>(b) : prepare_adj<3>(b);
 }
 
-mts_status adjoint_tape(mts_body *b, long long k) {
-    const int pad = b->dim == 2 ? 2 : 4;
-    k_tape<<<grid_n(b->n), kBlock, 0, b->ctx->stream>>>(b->u, (const double *)b->cp, b->ctrl, b->n,
-                                                         pad, k, b->tape_u, b->tape_cp, b->tape_dt);
+mts_status adjoint_tape(const mts_body *src, mts_body *dst, long long k) {
+    const int pad = src->dim == 2 ? 2 : 4;
+    if (src->rsize == 4)
+        k_tape<float><<<grid_n(src->n), kBlock, 0, src->ctx->stream>>>(
+            src->u, (const float *)src->cp, src->ctrl, src->n, pad, k, dst->tape_u, dst->tape_cp,
+            dst->tape_dt);
+    else
+        k_tape<double><<<grid_n(src->n), kBlock, 0, src->ctx->stream>>>(
+            src->u, (const double *)src->cp, src->ctrl, src->n, pad, k, dst->tape_u, dst->tape_cp,
+            dst->tape_dt);
+    MTS_CUDA(cudaGetLastError());
+    return MTS_OK;
+}
+
+mts_status copy_c_to_double(const mts_body *src, double *dst) {
+    if (src->rsize == 4)
+        k_to_double<float><<<grid_n(src->n), kBlock, 0, src->ctx->stream>>>(
+            (const float *)src->c, src->n, dst);
+    else
+        k_to_double<double><<<grid_n(src->n), kBlock, 0, src->ctx->stream>>>(
+            (const double *)src->c, src->n, dst);
     MTS_CUDA(cudaGetLastError());
     return MTS_OK;
 }

@@ -83,6 +83,10 @@ void free_dev(mts_body *b, T *&p) {
 
 void body_free(mts_body *b) {
     if (!b) return;
+    if (b->shadow) {
+        body_free(b->shadow);
+        b->shadow = nullptr;
+    }
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (cudaEvent_t e : b->prof_ev) cudaEventDestroy(e);
     void **ptrs[] = {(void **)&b->perm, (void **)&b->rank, (void **)&b->X64, (void **)&b->nb_off,
@@ -1433,11 +1437,78 @@ mts_status adjoint_ready(mts_body *b, const char *who) {
         set_error("%s: NULL body", who);
         return MTS_ERR_INVALID_ARG;
     }
-    if (b->adj_cap <= 0) {
+    if ((b->shadow ? b->shadow : b)->adj_cap <= 0) {
         set_error("%s: reverse mode not enabled (mts_adjoint_enable)", who);
         return MTS_ERR_STATE;
     }
     MTS_CUDA(cudaSetDevice(b->ctx->device));
+    return MTS_OK;
+}
+
+// The body that holds the tape and the adjoint state: the body itself (FP64),
+// or the FP64 twin of a mixed-precision body.
+mts_body *adj_of(mts_body *b) { return b->shadow ? b->shadow : b; }
+
+// FP64 twin of a mixed-precision body for its reverse mode: created from the
+// body's own FP64 positions with its damping-order layout, so its Morton
+// order, neighbour lists and damping order are those of the body (checked).
+mts_status make_shadow(mts_body *b) {
+    if (b->shadow) return MTS_OK;
+    std::vector<double> X((size_t)b->n * b->dim);
+    MTS_TRY(mts_read_field(b, MTS_F_X, X.data(), (int64_t)X.size()));
+    mts_body_desc d{};
+    d.dim = b->dim;
+    d.precision = MTS_FP64;
+    d.n = b->n;
+    d.X = X.data();
+    d.dx = b->dx;
+    d.h_over_dx = b->h / b->dx;
+    d.damp_layout = b->damp_layout;
+    d.tile = 0;
+    mts_body *s = nullptr;
+    MTS_TRY(mts_body_create(b->ctx, &d, &s));
+    std::vector<long long> pa((size_t)b->n), pb((size_t)b->n);
+    cudaStream_t st = b->ctx->stream;
+    mts_status e = MTS_OK;
+    if (cudaMemcpyAsync(pa.data(), b->perm, b->n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(pb.data(), s->perm, b->n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        e = cuda_fail(cudaGetLastError(), "make_shadow");
+    } else if (pa != pb || s->npairs != b->npairs || s->nnz != b->nnz) {
+        set_error("mts_adjoint_enable: the FP64 twin of the body has another set-up order");
+        e = MTS_ERR_STATE;
+    }
+    if (e != MTS_OK) {
+        mts_body_destroy(s);
+        return e;
+    }
+    b->shadow = s;
+    return MTS_OK;
+}
+
+// Bring the twin's parameters, boundary conditions and concentration to the
+// body's (both hold the particles in the same order).
+mts_status shadow_sync(mts_body *b) {
+    mts_body *s = b->shadow;
+    if (!s) return MTS_OK;
+    s->has_material = b->has_material;
+    s->model = b->model;
+    s->rho0 = b->rho0; s->E = b->E; s->nu = b->nu; s->K = b->K; s->mu = b->mu;
+    s->lambda = b->lambda; s->s0 = b->s0; s->sinf = b->sinf; s->delta = b->delta;
+    s->Hlin = b->Hlin; s->eta = b->eta;
+    s->has_diff = b->has_diff; s->D = b->D; s->beta = b->beta; s->c0 = b->c0;
+    s->diff_mode = b->diff_mode;
+    s->tip_count = b->tip_count;
+    cudaStream_t st = b->ctx->stream;
+    const size_t pad = b->dim == 2 ? 2 : 4;
+    if (s->h_flags != b->h_flags) {
+        s->h_flags = b->h_flags;
+        MTS_CUDA(cudaMemcpyAsync(s->flags, b->flags, b->n, cudaMemcpyDeviceToDevice, st));
+        MTS_TRY(update_pair_fixbits(s));
+    }
+    MTS_CUDA(cudaMemcpyAsync(s->u_unit, b->u_unit, b->n * pad * 8, cudaMemcpyDeviceToDevice, st));
+    MTS_TRY(copy_c_to_double(b, (double *)s->c));
+    ++s->graph_gen;
     return MTS_OK;
 }
 }  // namespace
@@ -1449,16 +1520,19 @@ mts_status mts_adjoint_enable(mts_body *b, int64_t max_substeps) {
         set_error("mts_adjoint_enable: NULL body or max_substeps < 1");
         return MTS_ERR_INVALID_ARG;
     }
-    if (b->precision != MTS_FP64) {
-        set_error("mts_adjoint_enable: the reverse mode runs on FP64 bodies only");
-        return MTS_ERR_STATE;
-    }
     if (b->aniso) {
         set_error("mts_adjoint_enable: the reverse mode has no anisotropic-kernel form");
         return MTS_ERR_STATE;
     }
     MTS_CUDA(cudaSetDevice(b->ctx->device));
     MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    if (b->precision != MTS_FP64) {
+        // mixed precision: the tape and the adjoint state live on an FP64 twin
+        MTS_TRY(make_shadow(b));
+        MTS_TRY(shadow_sync(b));
+        b = b->shadow;
+        MTS_TRY(prepare_kernels(b));   // its transposed damping sweep runs the FP64 kernel
+    }
     free_adjoint(b);
     const size_t n = (size_t)b->n, pad = b->dim == 2 ? 2 : 4, ms = b->dim == 2 ? 4 : 12;
     const size_t K = (size_t)max_substeps;
@@ -1492,7 +1566,7 @@ mts_status mts_adjoint_enable(mts_body *b, int64_t max_substeps) {
 
 mts_status mts_adjoint_reset(mts_body *b) {
     MTS_TRY(adjoint_ready(b, "mts_adjoint_reset"));
-    MTS_TRY(zero_adjoint(b));
+    MTS_TRY(zero_adjoint(adj_of(b)));
     MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
     return MTS_OK;
 }
@@ -1500,6 +1574,8 @@ mts_status mts_adjoint_reset(mts_body *b) {
 mts_status mts_adjoint_seed(mts_body *b, const double *u_bar, const double *tip_bar,
                             const double *force_bar) {
     MTS_TRY(adjoint_ready(b, "mts_adjoint_seed"));
+    MTS_TRY(shadow_sync(b));
+    b = adj_of(b);
     if (u_bar)
         MTS_CUDA(cudaMemcpyAsync(b->scratch, u_bar, (size_t)b->n * b->dim * 8,
                                  cudaMemcpyHostToDevice, b->ctx->stream));
@@ -1513,9 +1589,10 @@ mts_status mts_adjoint_seed(mts_body *b, const double *u_bar, const double *tip_
 mts_status mts_adjoint_slow_step(mts_body *b, const mts_step_params *p, int64_t substeps,
                                  double *theta_bar) {
     MTS_TRY(adjoint_ready(b, "mts_adjoint_slow_step"));
-    if (!p || !theta_bar || substeps < 1 || substeps > b->adj_cap) {
+    mts_body *a = adj_of(b);     // tape and adjoint state (b itself, or its FP64 twin)
+    if (!p || !theta_bar || substeps < 1 || substeps > a->adj_cap) {
         set_error("mts_adjoint_slow_step: NULL argument or substeps %lld outside [1, %lld]",
-                  (long long)substeps, (long long)b->adj_cap);
+                  (long long)substeps, (long long)a->adj_cap);
         return MTS_ERR_INVALID_ARG;
     }
     if (p->dt_slow > 0 && b->diff_mode != 0) {
@@ -1528,11 +1605,13 @@ mts_status mts_adjoint_slow_step(mts_body *b, const mts_step_params *p, int64_t 
     q.max_substeps = substeps;
     q.ke_tol = -1.0;
     long long launches = 0;
-    MTS_TRY(slow_step_begin(b, &q, &launches, b->tape_c));
+    MTS_TRY(shadow_sync(b));
+    if (a != b) MTS_TRY(copy_c_to_double(b, a->tape_c));   // c before the diffusion step
+    MTS_TRY(slow_step_begin(b, &q, &launches, a == b ? b->tape_c : nullptr));
     MTS_TRY(prepare_kernels(b));
     b->use_cond = 0;
     for (long long k = 0; k < substeps; ++k) {
-        MTS_TRY(adjoint_tape(b, k));
+        MTS_TRY(adjoint_tape(b, a, k));
         MTS_TRY(launch_stress(b));
         MTS_TRY(launch_force(b));
         MTS_TRY(launch_damping(b));
@@ -1546,16 +1625,18 @@ mts_status mts_adjoint_slow_step(mts_body *b, const mts_step_params *p, int64_t 
                   (long long)substeps);
         return MTS_ERR_STATE;
     }
-    // reverse
-    for (long long k = substeps - 1; k >= 0; --k) MTS_TRY(adjoint_substep(b, k, k == substeps - 1));
-    if (q.dt_slow > 0) MTS_TRY(adjoint_diffusion(b, q.dt_slow));
-    MTS_TRY(adjoint_load(b));
+    // reverse (on the twin: the concentration of the substeps, after the
+    // diffusion step, is the one the stress law's transpose reads)
+    if (a != b) MTS_TRY(copy_c_to_double(b, (double *)a->c));
+    for (long long k = substeps - 1; k >= 0; --k) MTS_TRY(adjoint_substep(a, k, k == substeps - 1));
+    if (q.dt_slow > 0) MTS_TRY(adjoint_diffusion(a, q.dt_slow));
+    MTS_TRY(adjoint_load(a));
     double th[8];
-    MTS_CUDA(cudaMemcpyAsync(th, b->adj_theta, sizeof(th), cudaMemcpyDeviceToHost, st));
-    MTS_CUDA(cudaMemsetAsync(b->adj_theta, 0, sizeof(th), st));
+    MTS_CUDA(cudaMemcpyAsync(th, a->adj_theta, sizeof(th), cudaMemcpyDeviceToHost, st));
+    MTS_CUDA(cudaMemsetAsync(a->adj_theta, 0, sizeof(th), st));
     MTS_CUDA(cudaStreamSynchronize(st));
     for (int k = 0; k < 7; ++k) theta_bar[k] += th[k];
-    for (int k = 0; k < 3; ++k) b->adj_force_seed[k] = 0.0;
+    for (int k = 0; k < 3; ++k) a->adj_force_seed[k] = 0.0;
     return MTS_OK;
 }
 
@@ -1571,8 +1652,9 @@ mts_status mts_read_adjoint(mts_body *b, int32_t field, double *out, int64_t len
         set_error("mts_read_adjoint: len %lld, expected %lld", (long long)len, (long long)(b->n * w));
         return MTS_ERR_INVALID_ARG;
     }
-    MTS_TRY(adjoint_out(b, field, b->scratch));
-    MTS_CUDA(cudaMemcpyAsync(out, b->scratch, len * 8, cudaMemcpyDeviceToHost, b->ctx->stream));
+    MTS_TRY(adjoint_out(adj_of(b), field, adj_of(b)->scratch));
+    MTS_CUDA(cudaMemcpyAsync(out, adj_of(b)->scratch, len * 8, cudaMemcpyDeviceToHost,
+                             b->ctx->stream));
     MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
     return MTS_OK;
 }
@@ -1592,8 +1674,12 @@ extern "C" mts_status mts_adjoint_equilibrium(mts_body *b, int64_t max_iters, do
     }
     cudaStream_t st = b->ctx->stream;
     // the held state, with the size the next substep would take, is the one
-    // taped entry every transposed substep linearises about
-    MTS_TRY(adjoint_tape(b, 0));
+    // taped entry every transposed substep linearises about (a mixed-precision
+    // body's state, taped into its FP64 twin, which runs the iteration)
+    MTS_TRY(shadow_sync(b));
+    mts_body *const src = b;
+    b = adj_of(b);
+    MTS_TRY(adjoint_tape(src, b, 0));
     // norm scratch: one double per block of the drift grid (part_drift holds two)
     double *part = b->part_drift, *nrm = b->scratch;
     double h[2];

@@ -192,6 +192,8 @@ struct mts_body {
     int tile_req;         // particles per Morton tile requested at creation (0 = default)
     bool pdl_now;         // capturing the substep chain with programmatic launches
     int damp_layout;      // resolved: MTS_DAMP_BLOCKS or MTS_DAMP_WIDE
+    bool damp_ring;       // BLOCKS kernel streams the level slots through a ring (set by
+                          // prepare_kernels from the groups per colour and the SM count)
     int ax_shift[3];      // owner-block width per axis (kWholeAxis = unblocked)
     int level_cap;        // pairs per sub-colour of one group (0 = none)
     double Xmin[3];
@@ -284,6 +286,10 @@ struct mts_body {
     double *adj_theta, *adj_part; // 8 parameter accumulators, per-tile partials
     mts::Control *adj_ctrl;       // dt of the substep being reversed
     double adj_force_seed[3];     // pending end-force adjoint of the next reversed step
+    // mixed-precision bodies: an FP64 twin (same positions, so the same order,
+    // neighbours and damping order) that holds the tape and the adjoint state;
+    // the forward recomputation runs on the body itself
+    mts_body *shadow;
 };
 
 struct mts_batch {
@@ -316,7 +322,11 @@ mts_status launch_damping_adjoint(mts_body *b, double *vbar, Control *ctrl);
 template <class R> Args<R> make_args(mts_body *b);
 // reverse mode (mts_adjoint.cu), FP64 bodies
 mts_status adjoint_prepare(mts_body *b);
-mts_status adjoint_tape(mts_body *b, long long k);
+// tape entry k: u, C_p^-1 / alpha and dt of `src` (FP64 or mixed) into the tape of
+// `dst` (the FP64 body that runs the transposed substeps: src itself, or its twin)
+mts_status adjoint_tape(const mts_body *src, mts_body *dst, long long k);
+// concentration of `src` (storage precision) into an FP64 device array
+mts_status copy_c_to_double(const mts_body *src, double *dst);
 mts_status adjoint_substep(mts_body *b, long long k, bool last);
 mts_status adjoint_diffusion(mts_body *b, double dt);
 mts_status adjoint_load(mts_body *b);

@@ -313,21 +313,22 @@ __global__ void __launch_bounds__(TileThreads<R>::v) k_force(Args<R> A) {
 }
 
 // --------------------------------------------------------------------- K_C
-// shared-memory layout of one damping warp: velocities of the 2^d touched
-// blocks, the owner group's pair coefficients and pair words (the words carry
-// the constrained axes, so no flags are staged)
+// shared-memory layout of one damping warp: the velocities of the 2^d touched
+// blocks (+1 dummy slot, padded to a whole group of eight slots, 16-byte
+// aligned for cp.async), then the level slots; the pair words carry the
+// constrained axes, so no flags are staged
+constexpr int kDampChunk = 16;   // levels per chunk of the damping warp's level ring
 template <class R, int D>
 struct DampSmem {
-    // velocities (+1 dummy slot, padded to a whole group of eight slots), 32
-    // slots per level of coefficients and pair words (16-byte aligned for
-    // cp.async)
     __host__ __device__ static size_t vbytes(int mb) {
         return (((size_t)damp_slot_count((1 << D) * mb) * Pad<D>::v * sizeof(R)) + 15) &
                ~size_t(15);
     }
-    __host__ __device__ static size_t bytes(int mb, int maxl) {
-        size_t b = vbytes(mb) + (size_t)32 * maxl * sizeof(R) + (size_t)32 * maxl * 4;
-        return (b + 15) & ~size_t(15);
+    // + the level slots (word, coefficient) x 32 per level: every level of the
+    // group (RING = false) or a ring of two chunks of kDampChunk levels
+    __host__ __device__ static size_t bytes(int mb, int maxl, bool ring) {
+        const size_t lv = ring ? (size_t)2 * kDampChunk : (size_t)maxl;
+        return (vbytes(mb) + lv * 32 * (4 + sizeof(R)) + 15) & ~size_t(15);
     }
 };
 
@@ -449,12 +450,64 @@ __device__ __forceinline__ void damp_pair_coded(uint32_t w, R g, unsigned char *
     st_vec<R, P>(pb, vb);
 }
 
-// One half-sweep of a warp over its group's levels (forward or reverse),
-// prefetching the next level's slot off the velocity chain.  CONS: the group
-// touches a constrained particle, so every level takes the coded update.
+// One half-sweep of a warp over its group's levels (forward or reverse).  The
+// level slots (lane-indexed: lane k only ever reads slot k of a level) stream
+// through a per-warp ring of two chunks of kDampChunk levels in shared memory:
+// each lane copies its own slots with cp.async a chunk ahead of the one being
+// applied, so the ring needs no barrier and the warp's shared memory stays
+// small (more warps per SM than staging every level would allow).  primed:
+// the caller has already issued chunks 0 and 1 of this sweep.  CONS: the
+// group touches a constrained particle, so every level takes the coded update.
+template <class R>
+__device__ __forceinline__ void damp_stage_chunk(int c, int nl, bool fwd, const uint32_t *gab,
+                                                 const R *gg, uint32_t *rw, R *rg, int lane) {
+    const int b = c & 1;
+#pragma unroll 4
+    for (int j = 0; j < kDampChunk; ++j) {
+        const int k = c * kDampChunk + j;
+        if (k < nl) {
+            const int l = fwd ? k : nl - 1 - k;
+            cp_async(rw + (b * kDampChunk + j) * 32 + lane, gab + 32 * l + lane, 4);
+            cp_async(rg + (b * kDampChunk + j) * 32 + lane, gg + 32 * l + lane, (int)sizeof(R));
+        }
+    }
+    cp_async_commit();
+}
+
 template <class R, int D, bool CONS, bool FWD, bool TR>
-__device__ __forceinline__ void damp_sweep(int nl, const uint32_t *sab, const R *sg, int lane,
-                                           unsigned char *svb, R hcim) {
+__device__ __forceinline__ void damp_sweep(int nl, const uint32_t *gab, const R *gg, int lane,
+                                           unsigned char *svb, R hcim, uint32_t *rw, R *rg,
+                                           bool primed) {
+    if (!primed) {
+        damp_stage_chunk<R>(0, nl, FWD, gab, gg, rw, rg, lane);
+        damp_stage_chunk<R>(1, nl, FWD, gab, gg, rw, rg, lane);
+    }
+    const int nch = (nl + kDampChunk - 1) / kDampChunk;
+    for (int c = 0; c < nch; ++c) {
+        cp_async_wait_group<1>();           // chunk c has landed (c + 1 may be in flight)
+        const int b = c & 1;
+        const int kend = min(kDampChunk, nl - c * kDampChunk);
+        for (int j = 0; j < kend; ++j) {
+            const uint32_t w = rw[(b * kDampChunk + j) * 32 + lane];
+            const R gc = rg[(b * kDampChunk + j) * 32 + lane];
+            if constexpr (CONS)
+                damp_pair_coded<R, D, TR>(w, gc, svb, hcim);
+            else
+                damp_pair_free<R, D>(w, gc, svb, hcim);
+            __syncwarp();
+        }
+        // this lane has consumed its slots of buffer b: refill it with chunk c + 2
+        damp_stage_chunk<R>(c + 2, nl, FWD, gab, gg, rw, rg, lane);
+    }
+    cp_async_wait_all();
+}
+
+// The same half-sweep with every level of the group already in shared memory
+// (sab, sg: 32 slots per level), prefetching the next level's slot off the
+// velocity chain.
+template <class R, int D, bool CONS, bool FWD, bool TR>
+__device__ __forceinline__ void damp_sweep_staged(int nl, const uint32_t *sab, const R *sg, int lane,
+                                                  unsigned char *svb, R hcim) {
     int l = FWD ? 0 : nl - 1;
     uint32_t wn = sab[32 * l + lane];
     R gn = sg[32 * l + lane];
@@ -474,21 +527,38 @@ __device__ __forceinline__ void damp_sweep(int nl, const uint32_t *sab, const R 
     }
 }
 
-template <class R, int D, bool TR>
-__device__ __forceinline__ void damp_sweeps(bool cons, int mode, int nl, const uint32_t *sab,
-                                            const R *sg, int lane, unsigned char *svb, R hcim) {
-    if (cons) {
-        if (mode & 1) damp_sweep<R, D, true, true, TR>(nl, sab, sg, lane, svb, hcim);
-        if (mode & 2) damp_sweep<R, D, true, false, TR>(nl, sab, sg, lane, svb, hcim);
+template <class R, int D, bool CONS, bool TR, bool RING>
+__device__ __forceinline__ void damp_sweeps_c(int mode, int nl, const uint32_t *gab, const R *gg,
+                                              int lane, unsigned char *svb, R hcim, uint32_t *rw,
+                                              R *rg) {
+    if constexpr (RING) {
+        // the first sweep's chunks 0 and 1 were issued before the chain wait
+        if (mode & 1) damp_sweep<R, D, CONS, true, TR>(nl, gab, gg, lane, svb, hcim, rw, rg, true);
+        if (mode & 2)
+            damp_sweep<R, D, CONS, false, TR>(nl, gab, gg, lane, svb, hcim, rw, rg, !(mode & 1));
     } else {
-        if (mode & 1) damp_sweep<R, D, false, true, TR>(nl, sab, sg, lane, svb, hcim);
-        if (mode & 2) damp_sweep<R, D, false, false, TR>(nl, sab, sg, lane, svb, hcim);
+        if (mode & 1) damp_sweep_staged<R, D, CONS, true, TR>(nl, rw, rg, lane, svb, hcim);
+        if (mode & 2) damp_sweep_staged<R, D, CONS, false, TR>(nl, rw, rg, lane, svb, hcim);
     }
 }
 
-template <class R, int D>
-__global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long long g_end,
-                                             int mode, long long n_begin, long long n_end) {
+template <class R, int D, bool TR, bool RING>
+__device__ __forceinline__ void damp_sweeps(bool cons, int mode, int nl, const uint32_t *gab,
+                                            const R *gg, int lane, unsigned char *svb, R hcim,
+                                            uint32_t *rw, R *rg) {
+    if (cons)
+        damp_sweeps_c<R, D, true, TR, RING>(mode, nl, gab, gg, lane, svb, hcim, rw, rg);
+    else
+        damp_sweeps_c<R, D, false, TR, RING>(mode, nl, gab, gg, lane, svb, hcim, rw, rg);
+}
+
+// RING: the level slots stream through the two-chunk ring (small shared
+// memory per warp: many warps per SM, for bodies with many groups per colour);
+// otherwise every level of the group is staged before the chain wait (the
+// shortest chain, for bodies with few groups per SM).
+template <class R, int D, bool RING>
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 4) k_damp(Args<R> A, long long g_begin, long long g_end,
+                                                                         int mode, long long n_begin, long long n_end) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int P = Pad<D>::v;
     constexpr int NB = 1 << D;
@@ -515,19 +585,24 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
         m0 = __ldg(A.grp_lvl + h);
         m1 = __ldg(A.grp_lvl + h + 1);
     }
-    unsigned char *base = smem + (size_t)warp * DampSmem<R, D>::bytes(mb, A.max_group_levels);
-    R *sv = reinterpret_cast<R *>(base);                 // NB * mb slots + 1 dummy slot
-    R *sg = reinterpret_cast<R *>(base + DampSmem<R, D>::vbytes(mb));
-    uint32_t *sab = reinterpret_cast<uint32_t *>(sg + 32 * A.max_group_levels);
-    // asynchronous staging of the group's padded level slots (contiguous,
-    // 16-byte aligned: 32 slots per level; set-up data, so it may overlap the
-    // previous kernel of the chain), then, once that kernel has completed, of
-    // the touched blocks' velocities
+    unsigned char *base =
+        smem + (size_t)warp * DampSmem<R, D>::bytes(mb, A.max_group_levels, RING);
+    R *sv = reinterpret_cast<R *>(base);
+    uint32_t *rw = reinterpret_cast<uint32_t *>(base + DampSmem<R, D>::vbytes(mb));
+    R *rg = reinterpret_cast<R *>(rw + 32 * (RING ? 2 * kDampChunk : A.max_group_levels));
+    // 32 slots per level: pair word and coefficient (set-up data, so they are
+    // issued before the chain wait and may overlap the previous kernel: the
+    // first two chunks of the first sweep, or every level)
     const uint32_t *gab = A.pair_ab + 32LL * l0;
     const R *gg = A.pair_g + 32LL * l0;
-    for (int k = 4 * lane; k < 32 * nl; k += 128) cp_async(sab + k, gab + k, 16);
-    constexpr int GPER = 16 / (int)sizeof(R);
-    for (int k = GPER * lane; k < 32 * nl; k += 32 * GPER) cp_async(sg + k, gg + k, 16);
+    if constexpr (RING) {
+        damp_stage_chunk<R>(0, nl, (mode & 1) != 0, gab, gg, rw, rg, lane);
+        damp_stage_chunk<R>(1, nl, (mode & 1) != 0, gab, gg, rw, rg, lane);
+    } else {
+        for (int k = 4 * lane; k < 32 * nl; k += 128) cp_async(rw + k, gab + k, 16);
+        constexpr int GPER = 16 / (int)sizeof(R);
+        for (int k = GPER * lane; k < 32 * nl; k += 32 * GPER) cp_async(rg + k, gg + k, 16);
+    }
     chain_wait();
     const int done = A.ctrl->done;
     const double dt = A.ctrl->dt;
@@ -535,6 +610,7 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
         cp_async_wait_all();
         return;
     }
+    // the touched blocks' velocities, once the previous kernel has completed
     constexpr int SB = P * (int)sizeof(R);   // bytes per velocity slot
 #pragma unroll
     for (int e = 0; e < NB; ++e)
@@ -559,9 +635,9 @@ __global__ void __launch_bounds__(128) k_damp(Args<R> A, long long g_begin, long
     // coefficient and runs the free-pair loop alone
     if (nl > 0) {
         if (tr)
-            damp_sweeps<R, D, true>(cons, mode, nl, sab, sg, lane, svb, hcim);
+            damp_sweeps<R, D, true, RING>(cons, mode, nl, gab, gg, lane, svb, hcim, rw, rg);
         else
-            damp_sweeps<R, D, false>(cons, mode, nl, sab, sg, lane, svb, hcim);
+            damp_sweeps<R, D, false, RING>(cons, mode, nl, gab, gg, lane, svb, hcim, rw, rg);
     }
 #pragma unroll
     for (int e = 0; e < NB; ++e)
@@ -1488,13 +1564,13 @@ template <class R, int D> size_t smem_diffuse(const mts_body *b) {
 // damping warps (owner groups) per CTA: the requested count, or 4, reduced
 // while the CTA's staging does not fit the shared-memory budget
 template <class R, int D> int damp_warps(const mts_body *b) {
-    const size_t per = DampSmem<R, D>::bytes(b->mb, b->max_group_levels);
+    const size_t per = DampSmem<R, D>::bytes(b->mb, b->max_group_levels, b->damp_ring);
     int w = b->damp_warps_req > 0 ? b->damp_warps_req : 4;
     while (w > 1 && per * w > 200 * 1024) w >>= 1;
     return w;
 }
 template <class R, int D> size_t smem_damp(const mts_body *b) {
-    return DampSmem<R, D>::bytes(b->mb, b->max_group_levels) * damp_warps<R, D>(b);
+    return DampSmem<R, D>::bytes(b->mb, b->max_group_levels, b->damp_ring) * damp_warps<R, D>(b);
 }
 
 // Launch a kernel of the substep chain.  While a body captures its chain
@@ -1556,8 +1632,12 @@ mts_status damping_run(mts_body *b, const Args<R> &A, long long *nlaunch) {
         } else {
             const long long n0 = cn >= 0 ? b->col_off[cn] : 0, n1 = cn >= 0 ? b->col_off[cn + 1] : 0;
             const unsigned grid = (unsigned)((g1 - g0 + W - 1) / W);
-            MTS_CUDA(launch_chain(b, k_damp<R, D>, grid, (unsigned)(W * 32), smem, A, g0, g1, mode,
-                                  n0, n1));
+            if (b->damp_ring)
+                MTS_CUDA(launch_chain(b, k_damp<R, D, true>, grid, (unsigned)(W * 32), smem, A, g0,
+                                      g1, mode, n0, n1));
+            else
+                MTS_CUDA(launch_chain(b, k_damp<R, D, false>, grid, (unsigned)(W * 32), smem, A,
+                                      g0, g1, mode, n0, n1));
         }
         if (nlaunch) ++*nlaunch;
         return MTS_OK;
@@ -1614,10 +1694,27 @@ mts_status prepare_t(mts_body *b) {
         MTS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
         return MTS_OK;
     };
-    if (wide)
+    if (wide) {
         MTS_TRY(attr((const void *)k_damp_wide<R, D>, damp_wide_smem(b), "damping (wide)"));
-    else
-        MTS_TRY(attr((const void *)k_damp<R, D>, smem_damp<R, D>(b), "damping"));
+    } else {
+        // Level staging: with every level staged a warp needs room for the
+        // group's longest chain, which caps the warps per SM; when a colour has
+        // more groups than the SMs can then hold at once, the two-chunk ring
+        // (a fraction of the shared memory, several times the warps) wins.
+        int sms = 0;
+        MTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->ctx->device));
+        const size_t full = DampSmem<R, D>::bytes(b->mb, b->max_group_levels, false);
+        const long long per_sm = std::max<long long>(1, (long long)(optin / full));
+        long long gmax = 0;
+        for (int c = 0; c < (1 << D); ++c) gmax = std::max<long long>(gmax, b->col_off[c + 1] - b->col_off[c]);
+        b->damp_ring = gmax > 2LL * sms * per_sm;
+        MTS_TRY(attr((const void *)k_damp<R, D, false>,
+                     DampSmem<R, D>::bytes(b->mb, b->max_group_levels, false) * damp_warps<R, D>(b),
+                     "damping"));
+        MTS_TRY(attr((const void *)k_damp<R, D, true>,
+                     DampSmem<R, D>::bytes(b->mb, b->max_group_levels, true) * damp_warps<R, D>(b),
+                     "damping"));
+    }
     const size_t sa = smem_stress<R, D>(b);
     MTS_TRY(attr((const void *)k_stress<R, D, MTS_ELASTIC_SVK>, sa, "stress"));
     MTS_TRY(attr((const void *)k_stress<R, D, MTS_NEOHOOKE_J2>, sa, "stress"));

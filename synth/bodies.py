@@ -249,10 +249,24 @@ def _swelling_case(name, counts, dx, seed, E, nu, rho0, eta, D, beta, c0,
                 tuple(counts))
 
 
+# Kinetic-energy criteria of the swelling workloads.  The paper fixes its
+# criterion values per case by lowering them until the result stops changing
+# (Sec. 5.1 and 5.3 criterion studies); its values (0.05 % / 0.1 % of p^l)
+# belong to its own beam and membrane.  The same study on the 40,000-particle
+# strip (tip elongation after 30 slow steps, criterion lowered by decades from
+# 5e-4) settles at 5e-8 of 3 K beta: 5e-4 -> 1.54 mm, 5e-6 -> 1.03 mm,
+# 5e-8 -> 0.912 mm, 5e-10 -> 0.925 mm, 5e-12 -> 0.919 mm.  On the 2.5 M-particle
+# plate the study does not settle within 3e4 substeps per slow step; its
+# criterion is 1e-5, two decades below the paper's 3D value (tip elongation
+# after 4 slow steps: 1e-3 -> 0.105 mm, 1e-5 -> 0.338 mm, 1e-7 -> 0.591 mm).
+STRIP_KE_TOL = 5e-8
+PLATE_KE_TOL = 1e-5
+
+
 def strip2d(nx: int = 2000, ny: int = 20, dx: float = 1e-5, seed: int = SEED_BASE + 3,
             E: float = 200e6, nu: float = 0.4, rho0: float = 2000.0, eta: float = 1e3,
             D: float = 1e-10, beta: float = 0.1, c0: float = 0.0,
-            ke_tol: float = 5e-4, jitter: float = JITTER) -> Case:
+            ke_tol: float = STRIP_KE_TOL, jitter: float = JITTER) -> Case:
     H = ny * dx
     return _swelling_case("strip2d", (nx, ny), dx, seed, E, nu, rho0, eta, D, beta,
                           c0, ke_tol, 2.0 * H * H / D, jitter)
@@ -261,7 +275,7 @@ def strip2d(nx: int = 2000, ny: int = 20, dx: float = 1e-5, seed: int = SEED_BAS
 def plate3d(nx: int = 1000, ny: int = 250, nz: int = 10, dx: float = 2e-5,
             seed: int = SEED_BASE + 4, E: float = 200e6, nu: float = 0.4,
             rho0: float = 2000.0, eta: float = 1e4, D: float = 1e-10, beta: float = 0.1,
-            c0: float = 0.0, ke_tol: float = 1e-3, jitter: float = JITTER) -> Case:
+            c0: float = 0.0, ke_tol: float = PLATE_KE_TOL, jitter: float = JITTER) -> Case:
     H = nz * dx
     return _swelling_case("plate3d", (nx, ny, nz), dx, seed, E, nu, rho0, eta, D,
                           beta, c0, ke_tol, 2.0 * H * H / D, jitter)

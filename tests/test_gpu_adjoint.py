@@ -53,8 +53,8 @@ def _steps(case, gb, nslow, nsub):
             for l in range(1, nslow + 1)]
 
 
-def _gpu_gradient(ctx, case, nslow, nsub, w_tip, w_f, r):
-    gb = M.body_from_case(ctx, case, M.FP64)
+def _gpu_gradient(ctx, case, nslow, nsub, w_tip, w_f, r, precision=M.FP64):
+    gb = M.body_from_case(ctx, case, precision)
     steps = _steps(case, gb, nslow, nsub)
     ckpts, counts = [], []
     for p in steps:
@@ -205,9 +205,14 @@ def test_autograd_function_wraps_the_reverse_mode(ctx):
 
 def test_adjoint_errors(ctx):
     case = small_bar()
+    aniso = B.beam_droplet2d(L=1e-3, aniso=4.0)
+    ga = M.body_from_case(ctx, aniso, M.MIXED)
+    with pytest.raises(M.MtsError) as e:
+        ga.adjoint_enable(4)
+    assert e.value.status == M.ERR_STATE
     gm = M.body_from_case(ctx, case, M.MIXED)
     with pytest.raises(M.MtsError) as e:
-        gm.adjoint_enable(4)
+        gm.adjoint_slow_step(2, ramp=0.1)
     assert e.value.status == M.ERR_STATE
     gb = M.body_from_case(ctx, case, M.FP64)
     with pytest.raises(M.MtsError) as e:
@@ -268,3 +273,145 @@ def test_equilibrium_adjoint_with_end_force_seed_only(ctx):
     th_un = gb.adjoint_slow_step(k, **p)
     assert th_un[0] != 0
     assert abs(th_eq[0] - th_un[0]) <= 1e-5 * abs(th_un[0]), (th_eq[0], th_un[0])
+
+
+def _oracle_relaxed_objective(case, theta, w_tip, w_f, r, relax, c_field=None):
+    """The objective at the oracle's relaxed equilibrium with parameters theta
+    = (E, sigma0, sigma_inf, delta, H, D, beta) (nu fixed)."""
+    ob = O.body_from_case(case)
+    m = case.material
+    ob.set_material(O.SVK if m.model == "svk" else O.J2, m.rho0, theta[0], m.nu, theta[1],
+                    theta[2], theta[3], theta[4])
+    if case.diffusion is not None:
+        ob.set_diffusion(theta[5], theta[6], case.diffusion[2])
+    if c_field is not None:
+        ob.write(O.F_C, c_field)
+    rep = ob.advance(**relax)
+    assert rep.converged == 1
+    d = case.dim
+    return (w_tip @ np.array(rep.tip_deflection[:d]) + w_f @ np.array(rep.end_force[:d]) +
+            float((r * ob.read(O.F_U)).sum()))
+
+
+@pytest.mark.parametrize("which", ["E", "beta"])
+def test_equilibrium_adjoint_matches_oracle_differences(ctx, which):
+    """The implicit-function adjoint of a relaxed equilibrium against central
+    differences of the ORACLE's equilibria, relaxed to machine precision, for
+    the parameters the mechanical equilibrium depends on: Young's modulus (an
+    SVK bar pulled at its grip) and the swelling coefficient (a cantilever
+    strip with a prescribed through-thickness concentration, damping near the
+    critical value of its flexural mode).  The hardening parameters act only
+    through the plastic history and D only through the diffusion step, which
+    the equilibrium adjoint leaves out."""
+    if which == "E":
+        case = B.bar2d(nx=24, ny=6, n_slow=4, eta=1e3)
+        c_field, k, rel_h, tol = None, 0, 1e-5, 1e-5
+        relax = dict(ramp=1.0 / case.plan.n_ramp, ke_tol=1e-26, ke_ref=case.plan.ke_ref,
+                     ke_mode=0, max_substeps=200000)
+    else:
+        case = B.strip2d(nx=30, ny=8, dx=1e-5, beta=1e-3, eta=1.0)
+        c_field = (case.lattice_index[:, 1] + 0.5) / case.counts[1]
+        k, rel_h, tol = 6, 1e-3, 1e-4          # the response is nearly linear in beta
+        K = case.material.E / (3 * (1 - 2 * case.material.nu))
+        relax = dict(ramp=0.0, ke_tol=1e-22, ke_ref=3 * K * case.diffusion[1], ke_mode=1,
+                     max_substeps=200000)
+    w_tip, w_f, r = _weights(case, seed=8)
+    r *= 1e-3
+    gb = M.body_from_case(ctx, case, M.FP64)
+    if c_field is not None:
+        gb.write(M.F_C, c_field)
+    theta0 = gb.parameters()
+    rep = gb.advance_slow_step(**relax)
+    assert rep.converged == 1
+    gb.adjoint_enable(1)
+    gb.adjoint_seed(u_bar=r, tip_bar=w_tip, force_bar=w_f)
+    th, iters = gb.adjoint_equilibrium(max_iters=400000, tol=1e-11)
+    gb.close()
+    h = rel_h * theta0[k]
+    tp, tm = theta0.copy(), theta0.copy()
+    tp[k] += h
+    tm[k] -= h
+    fd = (_oracle_relaxed_objective(case, tp, w_tip, w_f, r, relax, c_field) -
+          _oracle_relaxed_objective(case, tm, w_tip, w_f, r, relax, c_field)) / (2 * h)
+    assert fd != 0
+    assert abs(th[k] - fd) <= tol * abs(fd), (which, th[k], fd)
+
+
+# --------------------------------------------------------------------------
+# Mixed precision: FP32 forward, FP64 reverse about the FP32 trajectory
+# --------------------------------------------------------------------------
+# Tolerance.  The mixed forward run differs from the FP64 one by the FP32
+# rounding of the per-particle arithmetic: here <= 1e-5 relative in u (the
+# parity tests bound it by 1e-4).  The reverse mode is the exact FP64
+# transpose of the linearisation about that trajectory, so its gradient
+# differs from the oracle's (the FP64 trajectory) by the change of the
+# Jacobian between the two linearisation points: of the same relative order
+# as the state difference times the relative curvature of the maps, well
+# below 1e-3 for these small-strain steps.  1e-3 is therefore the bound
+# tested, for every parameter the objective depends on and for the adjoint
+# of the initial displacement.
+MIXED_ADJ_TOL = 1e-3
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_adjoint_matches_reverse_mode_oracle(ctx, name):
+    make, nslow, nsub = CASES[name]
+    case = make()
+    w_tip, w_f, r = _weights(case)
+    gb, th_g, steps, u_end = _gpu_gradient(ctx, case, nslow, nsub, w_tip, w_f, r, M.MIXED)
+    th_o, u0_o, u_o = _oracle_gradient(case, gb, steps, nsub, w_tip, w_f, r)
+    assert np.max(np.abs(u_end - u_o)) <= 1e-4 * np.max(np.abs(u_o))   # FP32 forward run
+    used = [0] if case.material.model == "svk" else [0, 1, 2, 3, 4]
+    if case.diffusion is not None:
+        used += [5, 6]
+    for k in used:
+        assert abs(th_g[k] - th_o[k]) <= MIXED_ADJ_TOL * abs(th_o[k]), (
+            A.THETA_NAMES[k], th_g[k], th_o[k])
+    u0_g = gb.read_adjoint(M.F_U)
+    assert np.max(np.abs(u0_g - u0_o)) <= MIXED_ADJ_TOL * np.max(np.abs(u0_o))
+
+
+def test_mixed_batch_members_reverse_mode(ctx):
+    """Four uneven members of the batched workload (two swelling strips, two
+    J2 bars) advanced together in mixed precision by batch launches, then
+    each member's slow steps reversed: gradients of tip deflection and end
+    force with respect to every parameter its objective depends on, against
+    the reverse-mode oracle run with the members' substep counts."""
+    cases = B.batch_instances(count=4, n_min=400, n_max=1500, seed=B.SEED_BASE + 51)
+    for c in cases:
+        c.eta = 1.0 if c.diffusion is not None else c.eta
+    bodies = [M.body_from_case(ctx, c, M.MIXED) for c in cases]
+    bt = M.Batch(ctx, bodies)
+    nsub = 8
+    ck = [[] for _ in cases]
+    steps = []
+    for l in (1, 2):
+        ps = []
+        for c, b in zip(cases, bodies):
+            p = dict(dt_slow=b.diffusion_dt()[1] if c.diffusion is not None else 0.0,
+                     ramp=l / max(c.plan.n_ramp, 1), ke_tol=-1.0, ke_ref=c.plan.ke_ref,
+                     max_substeps=nsub, check_every=0)
+            ps.append(p)
+        for k, b in enumerate(bodies):
+            ck[k].append(b.save_state())
+        reps = bt.advance(ps)
+        assert all(r.substeps == nsub for r in reps)
+        steps.append(ps)
+    bt.close()
+    for k, (c, b) in enumerate(zip(cases, bodies)):
+        w_tip, w_f, _ = _weights(c, seed=20 + k)
+        r = np.zeros((c.n, c.dim))
+        b.adjoint_enable(nsub)
+        b.adjoint_seed(tip_bar=w_tip, force_bar=w_f)
+        th = np.zeros(7)
+        for l in (1, 0):
+            b.load_state(ck[k][l])
+            th += b.adjoint_slow_step(nsub, **steps[l][k])
+        th_o, _, _ = _oracle_gradient(c, b, [steps[0][k], steps[1][k]], nsub, w_tip, w_f, r)
+        used = [0] if c.material.model == "svk" else [0, 1, 2, 3, 4]
+        if c.diffusion is not None:
+            used += [5, 6]
+        for q in used:
+            assert abs(th[q] - th_o[q]) <= MIXED_ADJ_TOL * abs(th_o[q]), (
+                c.name, A.THETA_NAMES[q], th[q], th_o[q])
+        b.close()

@@ -1,0 +1,120 @@
+"""Slow steps relaxed to the kinetic-energy criterion on the GPU.
+
+* A plate-shaped body (the benchmark plate's spacing, material, damping,
+  diffusion and boundary conditions on a 64 x 16 x 10 lattice: 10,240
+  particles, many 512-particle tiles, all eight block colours of the damping
+  order) in diffusion mode 0, through several slow steps stopped by the
+  criterion on the device, against the oracle: FP64 with the same stop
+  substeps (<= 1e-9), mixed precision at the GPU's substep counts
+  (u <= 1e-4, c <= 1e-5), normwise and element by element.
+* Substeps per slow step at full size against the paper's efficiency tables
+  (Sec. 5.1-5.4): same order of magnitude (a sanity check, not parity).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2309_04010_gb300 import mtssph as M
+from synth import bodies as B
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = M.Context(0)
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    den = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (den if den > 0 else 1.0))
+
+
+def elementwise(a, b, floor):
+    """Largest |a - b| / (|b| + floor * max|b|) over all components: a relative
+    error per element, with a floor for components near zero."""
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    scale = np.abs(b) + floor * np.max(np.abs(b))
+    return float(np.max(np.abs(a - b) / scale))
+
+
+@pytest.mark.parametrize("precision,tol_u,tol_c", [(M.FP64, 1e-9, 1e-12), (M.MIXED, 1e-4, 1e-5)])
+def test_plate_shaped_body_to_kinetic_energy_stop(ctx, precision, tol_u, tol_c):
+    case = B.plate3d(nx=64, ny=16, nz=10)
+    gb = M.body_from_case(ctx, case, precision)
+    ob = O.body_from_case(case, damp_layout=gb.damping_layout())
+    col = gb.colouring()[2]
+    assert len(set(col.tolist())) == 8 and case.n > 8 * 512
+    kw = dict(ke_tol=1e-3, ke_ref=case.plan.ke_ref, ke_mode=1, max_substeps=20000)
+    counts = []
+    for _ in range(3):
+        dts = ob.diffusion_dt()[1]
+        rg = gb.advance_slow_step(dt_slow=dts, **kw)
+        assert rg.converged == 1
+        if precision == M.FP64:
+            ro = ob.advance(dt_slow=dts, **kw)
+            assert ro.converged == 1 and rg.substeps == ro.substeps
+        else:
+            ro = ob.advance(dt_slow=dts, ke_tol=-1.0, ke_mode=1, max_substeps=rg.substeps)
+        counts.append(rg.substeps)
+    assert max(counts) > 1
+    u_g, u_o = gb.read(M.F_U), ob.read(O.F_U)
+    c_g, c_o = gb.read(M.F_C), ob.read(O.F_C)
+    assert np.max(np.abs(u_o)) > 0
+    assert rel(u_g, u_o) < tol_u and rel(c_g, c_o) < tol_c
+    assert elementwise(u_g, u_o, 1e-3) < 10 * tol_u
+    assert elementwise(c_g, c_o, 1e-3) < 10 * tol_c
+    gb.close()
+
+
+def _paper_per_slow_step(name):
+    with open(GOLDEN) as f:
+        e = json.load(f)["efficiency_tables"][name]
+    return e["substeps"] / e["slow_steps"]
+
+
+def test_cylinder_substeps_per_slow_step_in_paper_range(ctx):
+    """The 3D J2 cylinder (252,800 particles) under its stretch schedule with
+    the paper's 0.5 % criterion: substeps per slow step within a factor of ten
+    of the paper's 3D necking (3.21e5 / 1e4 = 32.1)."""
+    case = B.cylinder3d()
+    gb = M.body_from_case(ctx, case, M.MIXED)
+    plan = case.plan
+    subs = []
+    for l in range(1, 9):
+        r = gb.advance_slow_step(ramp=l / plan.n_ramp, ke_tol=plan.ke_tol, ke_ref=plan.ke_ref,
+                                 max_substeps=100000)
+        assert r.converged == 1
+        subs.append(r.substeps)
+    gb.close()
+    ref = _paper_per_slow_step("necking_3d")
+    mean = float(np.mean(subs[1:]))
+    assert ref / 10 <= mean <= ref * 10, (subs, ref)
+
+
+def test_strip_substeps_per_slow_step_in_paper_range(ctx):
+    """The 40,000-particle strip with its converged criterion (5e-8 of 3 K
+    beta): substeps per slow step over slow steps 2-11 within a factor of ten
+    of the paper's 2D swelling beam (2.76e5 / 125 = 2,208)."""
+    case = B.strip2d()
+    gb = M.body_from_case(ctx, case, M.MIXED)
+    plan = case.plan
+    dts = gb.diffusion_dt()[1]
+    subs = []
+    for _ in range(11):
+        r = gb.advance_slow_step(dt_slow=dts, ke_tol=plan.ke_tol, ke_ref=plan.ke_ref, ke_mode=1,
+                                 max_substeps=400000)
+        assert r.converged == 1
+        subs.append(r.substeps)
+    gb.close()
+    ref = _paper_per_slow_step("fsi_2d")
+    mean = float(np.mean(subs[1:]))
+    assert ref / 10 <= mean <= ref * 10, (subs, ref)
