@@ -129,6 +129,10 @@ def parse():
                     help="--profile-case membrane_droplet3d: in-plane size (the paper's is 10 mm)")
     ap.add_argument("--plate-size", default="1000x250x10",
                     help="--profile-case plate3d: lattice (a smaller plate for full ncu sets)")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="--profile-case: particles per Morton tile (0 = default)")
+    ap.add_argument("--damp-warps", type=int, default=0,
+                    help="--profile-case: damping warps per CTA (0 = default)")
     return ap.parse_args()
 
 
@@ -971,6 +975,8 @@ def run_profile_case(args):
     ctx = M.Context(0)
     prec = M.MIXED if args.precision == "mixed" else M.FP64
     gb = M.body_from_case(ctx, case, prec)
+    if args.tile or args.damp_warps:
+        gb.set_shapes(tile=args.tile, damp_warps=args.damp_warps)
     if args.diffusion_mode:
         gb.set_diffusion_mode(args.diffusion_mode)
     off, _ = gb.neighbors()
@@ -988,7 +994,7 @@ def run_profile_case(args):
         gb.load_state(ck)
         gb.adjoint_slow_step(args.substeps, **p)
     print(f"profile_case workload={args.profile_case} n={case.n} nnz={int(off[-1])} "
-          f"precision={args.precision} substeps={total}")
+          f"precision={args.precision} substeps={total} shapes={gb.shapes()}")
     gb.close()
     ctx.close()
 

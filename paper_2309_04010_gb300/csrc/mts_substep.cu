@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(TileThreads<R>::v) k_force(Args<R> A) {
 // blocks (+1 dummy slot, padded to a whole group of eight slots, 16-byte
 // aligned for cp.async), then the level slots; the pair words carry the
 // constrained axes, so no flags are staged
-constexpr int kDampChunk = 16;   // levels per chunk of the damping warp's level ring
+constexpr int kDampChunk = 8;    // levels per chunk of the damping warp's level ring
 template <class R, int D>
 struct DampSmem {
     __host__ __device__ static size_t vbytes(int mb) {
@@ -1701,13 +1701,19 @@ mts_status prepare_t(mts_body *b) {
         // group's longest chain, which caps the warps per SM; when a colour has
         // more groups than the SMs can then hold at once, the two-chunk ring
         // (a fraction of the shared memory, several times the warps) wins.
+        // Compare the rounds of warps a colour launch needs in each form (the
+        // ring's warps run a little slower, so it takes strictly fewer rounds).
         int sms = 0;
         MTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->ctx->device));
-        const size_t full = DampSmem<R, D>::bytes(b->mb, b->max_group_levels, false);
-        const long long per_sm = std::max<long long>(1, (long long)(optin / full));
-        long long gmax = 0;
-        for (int c = 0; c < (1 << D); ++c) gmax = std::max<long long>(gmax, b->col_off[c + 1] - b->col_off[c]);
-        b->damp_ring = gmax > 2LL * sms * per_sm;
+        auto rounds = [&](bool ring) {
+            const size_t per = DampSmem<R, D>::bytes(b->mb, b->max_group_levels, ring);
+            const long long per_sm = std::max<long long>(1, std::min<long long>(32, (long long)(optin / per)));
+            long long gmax = 0;
+            for (int c = 0; c < (1 << D); ++c)
+                gmax = std::max<long long>(gmax, b->col_off[c + 1] - b->col_off[c]);
+            return (gmax + sms * per_sm - 1) / (sms * per_sm);
+        };
+        b->damp_ring = rounds(true) < rounds(false);
         MTS_TRY(attr((const void *)k_damp<R, D, false>,
                      DampSmem<R, D>::bytes(b->mb, b->max_group_levels, false) * damp_warps<R, D>(b),
                      "damping"));
