@@ -106,7 +106,8 @@ void body_free(mts_body *b) {
                      (void **)&b->tape_dt, (void **)&b->tape_c, (void **)&b->adj_u,
                      (void **)&b->adj_v, (void **)&b->adj_cp, (void **)&b->adj_c,
                      (void **)&b->adj_a, (void **)&b->adj_G, (void **)&b->adj_theta,
-                     (void **)&b->adj_part, (void **)&b->adj_ctrl};
+                     (void **)&b->adj_part, (void **)&b->adj_ctrl, (void **)&b->pd_blk,
+                     (void **)&b->pd_req, (void **)&b->pd_done};
     for (void **pp : ptrs) {
         dfree(b->ctx, *pp);
         *pp = nullptr;
@@ -389,7 +390,11 @@ mts_status slow_step_report(mts_body *b, mts_step_report *rep, long long launche
     rep->kernel_launches = launches;
     for (int k = 0; k < 3; ++k) rep->tip_deflection[k] = tip[k];
     if (C.status != MTS_OK) {
-        set_error("non-finite kinetic energy after substep %lld", (long long)C.nsub);
+        if (C.status == MTS_ERR_TIMEOUT)
+            set_error("damping sweep: a wait for an earlier pair update ran out of time "
+                      "(substep %lld)", (long long)C.nsub);
+        else
+            set_error("non-finite kinetic energy after substep %lld", (long long)C.nsub);
         return (mts_status)C.status;
     }
     return MTS_OK;

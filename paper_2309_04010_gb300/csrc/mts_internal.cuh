@@ -194,6 +194,19 @@ struct mts_body {
     int damp_layout;      // resolved: MTS_DAMP_BLOCKS or MTS_DAMP_WIDE
     bool damp_ring;       // BLOCKS kernel streams the level slots through a ring (set by
                           // prepare_kernels from the groups per colour and the SM count)
+    // one-launch damping sweep (BLOCKS layout): every (colour launch, group)
+    // of the symmetric sweep is a task taken from a queue in sweep order; a
+    // task waits until the earlier tasks that touch its blocks have finished
+    int32_t *pd_blk;      // per group x 2^d touched blocks: block index (-1: none)
+    uint8_t *pd_req;      // per task x 2^d: earlier tasks of the sweep touching that block
+    unsigned *pd_done;    // per block: finished tasks touching it; [pd_nblocks]: the queue
+    long long pd_ntasks, pd_nblocks;
+    int pd_nph;                 // colour launches of the multi-launch form it replaces
+    long long pd_off[17];       // first task of each of them
+    long long pd_goff[16];      // first group of its colour
+    int pd_mode[16];            // 1 forward, 2 reverse, 3 both
+    int pd_grid;                // CTAs of the launch (resident capacity)
+    bool pd_on;                 // tables built and the one-launch form in use
     int ax_shift[3];      // owner-block width per axis (kWholeAxis = unblocked)
     int level_cap;        // pairs per sub-colour of one group (0 = none)
     double Xmin[3];

@@ -18,6 +18,8 @@
 // Every kernel returns at once when the device stop flag is set, so a captured
 // chunk of substeps can run past convergence without changing the state.
 #include <algorithm>
+#include <cstdlib>
+#include <vector>
 #include <cmath>
 
 #include "mts_device.cuh"
@@ -651,6 +653,169 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 4) k_damp(Args<R> A,
     if (lane == 0)
         for (long long hh = h + (g_end - g_begin); hh < n_end; hh += g_end - g_begin)
             prefetch_group_levels<R>(A, __ldg(A.grp_lvl + hh), __ldg(A.grp_lvl + hh + 1));
+}
+
+// ------------------------------------------------- damping, one launch
+// The symmetric sweep as one launch (BLOCKS layout).  The multi-launch form
+// runs one launch per colour (forward on all but the last colour, forward and
+// reverse fused on the last, then reverse), with the whole GPU between two
+// launches.  Here every (launch, group) pair of that sequence is a task, taken
+// by a warp from a queue in sweep order; before it touches the velocities, a
+// task waits until every earlier task touching one of its 2^d blocks has
+// finished (a per-block count of finished tasks, written with release and
+// read with acquire semantics).  Each task then computes exactly what its
+// group computes in the multi-launch form, on the same velocities, so the
+// results are bit for bit the same.  Tasks are taken in sweep order and wait
+// only on earlier tasks, all held by running warps, so the queue always
+// progresses; a wait that exceeds kPersistWaitNs nonetheless gives up, flags
+// MTS_ERR_TIMEOUT in the control block and stops the slow step.
+constexpr unsigned long long kPersistWaitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+struct PersistArgs {
+    const int32_t *blk;    // per group x 2^d
+    const uint8_t *req;    // per task x 2^d
+    unsigned *done;        // per block; done[nblocks] = the task queue
+    long long nblocks, ntasks;
+    int nph;
+    long long off[17], goff[16];
+    int mode[16];
+};
+
+__global__ void k_persist_reset(unsigned *done, long long count) {
+    chain_trigger();
+    chain_wait();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        done[i] = 0u;
+}
+
+// velocity slot in, bypassing L1 (another SM may have written it in this launch)
+template <class R, int P>
+__device__ __forceinline__ void stage_velocity_l2(R *s, const R *g) {
+    if constexpr (P * sizeof(R) == 8) {
+        const float2 t = __ldcg(reinterpret_cast<const float2 *>(g));
+        *reinterpret_cast<float2 *>(s) = t;
+    } else {
+        cp_async_reals<R, P>(s, g);      // 16-byte copies: cp.async.cg, L2 only
+    }
+}
+
+template <class R, int D, bool RING>
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 4) k_damp_persist(Args<R> A, PersistArgs Q) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int P = Pad<D>::v;
+    constexpr int NB = 1 << D;
+    constexpr int SB = P * (int)sizeof(R);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    chain_trigger();
+    chain_wait();
+    if (A.ctrl->done) return;
+    const double dt = A.ctrl->dt;
+    const int mb = A.mb;
+    unsigned char *base =
+        smem + (size_t)warp * DampSmem<R, D>::bytes(mb, A.max_group_levels, RING);
+    R *sv = reinterpret_cast<R *>(base);
+    uint32_t *rw = reinterpret_cast<uint32_t *>(base + DampSmem<R, D>::vbytes(mb));
+    R *rg = reinterpret_cast<R *>(rw + 32 * (RING ? 2 * kDampChunk : A.max_group_levels));
+    const R im = (R)(1.0 / A.mass);
+    const R hcim = (R)(0.5 * dt) * A.eta * im;
+    unsigned char *svb = reinterpret_cast<unsigned char *>(sv);
+    unsigned *queue = Q.done + Q.nblocks;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(queue, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if ((long long)t >= Q.ntasks) break;
+        int p = 0;
+        while (p + 1 < Q.nph && (long long)t >= Q.off[p + 1]) ++p;
+        const long long g = Q.goff[p] + ((long long)t - Q.off[p]);
+        const int mode = Q.mode[p];
+        int ts[NB], tc[NB], bk[NB];
+#pragma unroll
+        for (int e = 0; e < NB; ++e) {
+            ts[e] = __ldg(A.touch_start + g * NB + e);
+            tc[e] = __ldg(A.touch_cnt + g * NB + e);
+            bk[e] = __ldg(Q.blk + g * NB + e);
+        }
+        const int l0 = __ldg(A.grp_lvl + g), l1 = __ldg(A.grp_lvl + g + 1);
+        const bool cons = __ldg(A.grp_cons + g) != 0;
+        const int nl = l1 - l0;
+        const uint32_t *gab = A.pair_ab + 32LL * l0;
+        const R *gg = A.pair_g + 32LL * l0;
+        // set-up data first: it does not depend on the earlier tasks
+        if constexpr (RING) {
+            damp_stage_chunk<R>(0, nl, (mode & 1) != 0, gab, gg, rw, rg, lane);
+            damp_stage_chunk<R>(1, nl, (mode & 1) != 0, gab, gg, rw, rg, lane);
+        } else {
+            for (int k = 4 * lane; k < 32 * nl; k += 128) cp_async(rw + k, gab + k, 16);
+            constexpr int GPER = 16 / (int)sizeof(R);
+            for (int k = GPER * lane; k < 32 * nl; k += 32 * GPER) cp_async(rg + k, gg + k, 16);
+        }
+        // lane e < 2^d looks after touched block e
+        int my_tc = 0, my_bk = 0;
+#pragma unroll
+        for (int e = 0; e < NB; ++e)
+            if (lane == e) {
+                my_tc = tc[e];
+                my_bk = bk[e];
+            }
+        // wait for the earlier tasks on this group's blocks
+        if (lane < NB && my_tc > 0) {
+            const unsigned need = __ldg(Q.req + t * NB + lane);
+            const unsigned *cnt = Q.done + my_bk;
+            if (ld_acquire_u32(cnt) < need) {
+                const unsigned long long t0 = global_ns();
+                while (ld_acquire_u32(cnt) < need) {
+                    __nanosleep(64);
+                    if (global_ns() - t0 > kPersistWaitNs) {
+                        atomicExch(&A.ctrl->status, (int)MTS_ERR_TIMEOUT);
+                        atomicExch(&A.ctrl->done, 1);
+                        break;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < NB; ++e)
+            for (int k = lane; k < tc[e]; k += 32)
+                stage_velocity_l2<R, P>(sv + (size_t)damp_slot_pos(e * mb + k, SB) * P,
+                                        A.v + (size_t)(ts[e] + k) * P);
+        if (lane == 0) {
+            R z[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) z[q] = R(0);
+            st_vec<R, P>(sv + (size_t)damp_slot_pos(NB * mb, SB) * P, z);
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        if (nl > 0) damp_sweeps<R, D, false, RING>(cons, mode, nl, gab, gg, lane, svb, hcim, rw, rg);
+#pragma unroll
+        for (int e = 0; e < NB; ++e)
+            for (int k = lane; k < tc[e]; k += 32) {
+                R vv[P];
+                ld_vec<R, P>(vv, sv + (size_t)damp_slot_pos(e * mb + k, SB) * P);
+                st_vec<R, P>(A.v + (long long)(ts[e] + k) * P, vv);
+            }
+        __syncwarp();
+        // release: this warp's velocity stores before the counts the next tasks read
+        if (lane < NB && my_tc > 0) {
+            __threadfence();
+            atomicAdd(Q.done + my_bk, 1u);
+        }
+        __syncwarp();
+    }
 }
 
 // ------------------------------------------------- damping, wide layout
@@ -1612,10 +1777,105 @@ mts_status force_t(mts_body *b) {
     return MTS_OK;
 }
 
+// Task tables of the one-launch sweep: the colour launches of the multi-launch
+// form in their order, each group of a launch one task; per task and touched
+// block, the number of earlier tasks that touch that block.
+mts_status build_persist_tables(mts_body *b) {
+    const int NB = 1 << b->dim;
+    const long long ng = b->n_groups;
+    cudaStream_t st = b->ctx->stream;
+    std::vector<int32_t> ts((size_t)ng * NB), tc((size_t)ng * NB);
+    MTS_CUDA(cudaMemcpyAsync(ts.data(), b->touch_start, ts.size() * 4, cudaMemcpyDeviceToHost, st));
+    MTS_CUDA(cudaMemcpyAsync(tc.data(), b->touch_cnt, tc.size() * 4, cudaMemcpyDeviceToHost, st));
+    MTS_CUDA(cudaStreamSynchronize(st));
+    // a touched block is known by its first particle
+    std::vector<int32_t> starts;
+    for (size_t q = 0; q < ts.size(); ++q)
+        if (tc[q] > 0) starts.push_back(ts[q]);
+    std::sort(starts.begin(), starts.end());
+    starts.erase(std::unique(starts.begin(), starts.end()), starts.end());
+    std::vector<int32_t> blk(ts.size(), -1);
+    for (size_t q = 0; q < ts.size(); ++q)
+        if (tc[q] > 0)
+            blk[q] = (int32_t)(std::lower_bound(starts.begin(), starts.end(), ts[q]) - starts.begin());
+    int cols[8], nc = 0;
+    for (int c = 0; c < NB; ++c)
+        if (b->col_off[c + 1] > b->col_off[c]) cols[nc++] = c;
+    int pcol[16], pmode[16], nph = 0;
+    for (int i = 0; i < nc - 1; ++i) { pcol[nph] = cols[i]; pmode[nph++] = 1; }
+    if (nc > 0) { pcol[nph] = cols[nc - 1]; pmode[nph++] = 3; }
+    for (int i = nc - 2; i >= 0; --i) { pcol[nph] = cols[i]; pmode[nph++] = 2; }
+    long long ntasks = 0;
+    for (int p = 0; p < nph; ++p) {
+        b->pd_off[p] = ntasks;
+        b->pd_goff[p] = b->col_off[pcol[p]];
+        b->pd_mode[p] = pmode[p];
+        ntasks += b->col_off[pcol[p] + 1] - b->col_off[pcol[p]];
+    }
+    b->pd_off[nph] = ntasks;
+    std::vector<uint8_t> req((size_t)ntasks * NB, 0);
+    std::vector<int> cnt(starts.size(), 0);
+    for (int p = 0; p < nph; ++p)
+        for (long long t = b->pd_off[p]; t < b->pd_off[p + 1]; ++t) {
+            const long long g = b->pd_goff[p] + (t - b->pd_off[p]);
+            for (int e = 0; e < NB; ++e) {
+                const int32_t k = blk[g * NB + e];
+                if (k < 0) continue;
+                if (cnt[k] > 255) {
+                    set_error("one-launch damping: a block is touched by more than 255 tasks");
+                    return MTS_ERR_STATE;
+                }
+                req[t * NB + e] = (uint8_t)cnt[k]++;   // a launch touches a block at most once
+            }
+        }
+    MTS_TRY(dalloc_t(b->ctx, &b->pd_blk, blk.size()));
+    MTS_TRY(dalloc_t(b->ctx, &b->pd_req, std::max<size_t>(req.size(), 1)));
+    MTS_TRY(dalloc_t(b->ctx, &b->pd_done, starts.size() + 1));
+    MTS_CUDA(cudaMemcpyAsync(b->pd_blk, blk.data(), blk.size() * 4, cudaMemcpyHostToDevice, st));
+    if (!req.empty())
+        MTS_CUDA(cudaMemcpyAsync(b->pd_req, req.data(), req.size(), cudaMemcpyHostToDevice, st));
+    MTS_CUDA(cudaMemsetAsync(b->pd_done, 0, (starts.size() + 1) * 4, st));
+    MTS_CUDA(cudaStreamSynchronize(st));
+    b->pd_ntasks = ntasks;
+    b->pd_nblocks = (long long)starts.size();
+    b->pd_nph = nph;
+    return MTS_OK;
+}
+
+template <class R, int D>
+mts_status damping_persist(mts_body *b, const Args<R> &A, long long *nlaunch) {
+    PersistArgs Q{};
+    Q.blk = b->pd_blk;
+    Q.req = b->pd_req;
+    Q.done = b->pd_done;
+    Q.nblocks = b->pd_nblocks;
+    Q.ntasks = b->pd_ntasks;
+    Q.nph = b->pd_nph;
+    for (int p = 0; p <= b->pd_nph; ++p) Q.off[p] = b->pd_off[p];
+    for (int p = 0; p < b->pd_nph; ++p) {
+        Q.goff[p] = b->pd_goff[p];
+        Q.mode[p] = b->pd_mode[p];
+    }
+    const int W = damp_warps<R, D>(b);
+    const size_t smem = smem_damp<R, D>(b);
+    MTS_CUDA(launch_chain(b, k_persist_reset, 1u, 256u, (size_t)0, b->pd_done,
+                          b->pd_nblocks + 1));
+    if (b->damp_ring)
+        MTS_CUDA(launch_chain(b, k_damp_persist<R, D, true>, (unsigned)b->pd_grid,
+                              (unsigned)(W * 32), smem, A, Q));
+    else
+        MTS_CUDA(launch_chain(b, k_damp_persist<R, D, false>, (unsigned)b->pd_grid,
+                              (unsigned)(W * 32), smem, A, Q));
+    if (nlaunch) *nlaunch = 2;
+    return MTS_OK;
+}
+
 template <class R, int D>
 mts_status damping_run(mts_body *b, const Args<R> &A, long long *nlaunch) {
     if (nlaunch) *nlaunch = 0;
     if (b->eta == 0.0 || b->npairs == 0) return MTS_OK;
+    if (b->pd_on && !A.transpose && b->damp_layout != MTS_DAMP_WIDE)
+        return damping_persist<R, D>(b, A, nlaunch);
     const bool wide = b->damp_layout == MTS_DAMP_WIDE;
     const size_t smem = wide ? damp_wide_smem(b) : smem_damp<R, D>(b);
     const int W = damp_warps<R, D>(b);
@@ -1713,13 +1973,45 @@ mts_status prepare_t(mts_body *b) {
                 gmax = std::max<long long>(gmax, b->col_off[c + 1] - b->col_off[c]);
             return (gmax + sms * per_sm - 1) / (sms * per_sm);
         };
-        b->damp_ring = rounds(true) < rounds(false);
+        const long long rounds_ring = rounds(true);
+        b->damp_ring = rounds_ring < rounds(false);
         MTS_TRY(attr((const void *)k_damp<R, D, false>,
                      DampSmem<R, D>::bytes(b->mb, b->max_group_levels, false) * damp_warps<R, D>(b),
                      "damping"));
         MTS_TRY(attr((const void *)k_damp<R, D, true>,
                      DampSmem<R, D>::bytes(b->mb, b->max_group_levels, true) * damp_warps<R, D>(b),
                      "damping"));
+        // The one-launch form where a colour launch needs several rounds of warps
+        // even in the ring form: there it removes the launch boundaries and the
+        // tails of each round (the 2.5 M-particle plate, 3 rounds: 1.05 -> 0.85
+        // ms per substep).  With one round per launch the chain of dependent
+        // tasks is the critical path and separate launches are faster (the
+        // 252,800-particle cylinder: 0.18 vs 0.37 ms; a 625,000-particle plate:
+        // 0.37 vs 0.60 ms).  MTS_DAMP_MULTILAUNCH=1 keeps the multi-launch form
+        // (for comparisons; the results are the same bits).
+        const char *ml = std::getenv("MTS_DAMP_MULTILAUNCH");
+        const bool want = !(ml && ml[0] == '1') && b->damp_ring && rounds_ring >= 2 &&
+                          b->npairs > 0 && b->n_groups > 0;
+        if (want && !b->pd_blk) MTS_TRY(build_persist_tables(b));
+        b->pd_on = want;
+        if (want) {
+            MTS_TRY(attr((const void *)k_damp_persist<R, D, false>,
+                         DampSmem<R, D>::bytes(b->mb, b->max_group_levels, false) *
+                             damp_warps<R, D>(b), "damping (one launch)"));
+            MTS_TRY(attr((const void *)k_damp_persist<R, D, true>,
+                         DampSmem<R, D>::bytes(b->mb, b->max_group_levels, true) *
+                             damp_warps<R, D>(b), "damping (one launch)"));
+            const int W = damp_warps<R, D>(b);
+            int per_sm = 0;
+            if (b->damp_ring)
+                MTS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per_sm, k_damp_persist<R, D, true>, W * 32, smem_damp<R, D>(b)));
+            else
+                MTS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per_sm, k_damp_persist<R, D, false>, W * 32, smem_damp<R, D>(b)));
+            const long long need = (b->pd_ntasks + W - 1) / W;
+            b->pd_grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)std::max(per_sm, 1) * sms));
+        }
     }
     const size_t sa = smem_stress<R, D>(b);
     MTS_TRY(attr((const void *)k_stress<R, D, MTS_ELASTIC_SVK>, sa, "stress"));

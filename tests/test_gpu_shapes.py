@@ -122,3 +122,32 @@ def test_batch_autotune_matches_single_bodies(ctx):
         assert np.array_equal(single.read(M.F_U), b.read(M.F_U))
         single.close()
     bt.close()
+
+
+def test_one_launch_damping_equals_multi_launch():
+    """A body with many damping groups per SM (the 2.5 M-particle plate) runs
+    its damping sweep as one launch with a task queue; the same body with the
+    multi-launch form (MTS_DAMP_MULTILAUNCH=1) gives the same bits: every task
+    computes what its group computes in its colour launch."""
+    import os
+    ctx = M.Context(0)
+    case = B.plate3d()
+    out = []
+    for multi in (False, True):
+        if multi:
+            os.environ["MTS_DAMP_MULTILAUNCH"] = "1"
+        try:
+            gb = M.body_from_case(ctx, case, M.MIXED)
+            dts = gb.diffusion_dt()[1]
+            for _ in range(2):
+                r = gb.advance_slow_step(dt_slow=dts, ke_tol=-1.0, ke_ref=case.plan.ke_ref,
+                                         ke_mode=1, max_substeps=12)
+                assert r.substeps == 12
+            out.append((gb.read(M.F_U), gb.read(M.F_V), r.kernel_launches))
+            gb.close()
+        finally:
+            os.environ.pop("MTS_DAMP_MULTILAUNCH", None)
+    (u1, v1, k1), (u2, v2, k2) = out
+    assert k1 < k2                     # the one-launch form really ran
+    assert np.array_equal(u1, u2) and np.array_equal(v1, v2)
+    ctx.close()
