@@ -406,8 +406,13 @@ __device__ __forceinline__ void damp_pair_free(uint32_t w, R g, unsigned char *s
         va[q] -= f2 * d;
         vb[q] += f2 * d;
     }
-    st_vec<R, P>(pa, va);
-    st_vec<R, P>(pb, vb);
+    // an empty slot (coefficient 0, both offsets on the dummy slot) stores
+    // nothing: several empty lanes of a quarter-warp would store to one
+    // address and replay; loads of one address are a broadcast
+    if (g != R(0)) {
+        st_vec<R, P>(pa, va);
+        st_vec<R, P>(pb, vb);
+    }
 }
 
 // damp_apply for the warp-per-group kernel, where the pair word carries the
@@ -448,8 +453,10 @@ __device__ __forceinline__ void damp_pair_coded(uint32_t w, R g, unsigned char *
             vb[q] += cb * d;
         }
     }
-    st_vec<R, P>(pa, va);
-    st_vec<R, P>(pb, vb);
+    if (g != R(0)) {        // empty slots store nothing (see damp_pair_free)
+        st_vec<R, P>(pa, va);
+        st_vec<R, P>(pb, vb);
+    }
 }
 
 // One half-sweep of a warp over its group's levels (forward or reverse).  The

