@@ -324,7 +324,7 @@ class Body:
             self.set_diffusion(th[5], th[6], self._diffusion[2])
             self.write(F_C, c)
 
-    # -- reverse mode (FP64 bodies)
+    # -- reverse mode (FP64 arithmetic; a mixed-precision body is reversed on its FP64 twin)
     def adjoint_enable(self, max_substeps: int):
         _check(lib().mts_adjoint_enable(self._h, int(max_substeps)), "mts_adjoint_enable")
         self._adj_cap = int(max_substeps)
@@ -525,8 +525,9 @@ def slow_steps(body: Body, theta, steps):
     each) with parameters theta = (E, sigma0, sigma_inf, delta, H, D, beta)
     and return the tip deflection and end force of the last one as a torch
     tensor [tip (dim), force (dim)], differentiable with respect to theta
-    through the library's reverse mode (FP64 bodies; substep sizes and counts
-    held at the forward run's values)."""
+    through the library's reverse mode (FP64 adjoint arithmetic for FP64 and
+    mixed-precision bodies; substep sizes and counts held at the forward
+    run's values)."""
     import torch
 
     class _SlowSteps(torch.autograd.Function):
