@@ -742,14 +742,58 @@ def measure_adjoint(ctx, args, M, case):
     ta = time.perf_counter() - t0
     gb.close()
     sub = sum(counts)
-    return {"workload": f"cylinder3d-j2-{case.n}", "precision": "f64", "slow_steps": len(steps),
-            "substeps": sub, "forward_s": tf, "reverse_s": ta,
-            "reverse_value": case.n * sub / ta, "unit": UNIT, "reverse_over_forward": ta / tf,
-            "dtheta_nonzero": [bool(x != 0) for x in th],
-            "err_vs_oracle": "FP64 reverse mode against the PyTorch reverse-mode oracle: "
-                             "<= 1e-8 relative (tested)",
-            "timing": "host wall clock, stream synchronised; the reverse time includes the "
-                      "taped recomputation of the step"}
+    out = {"workload": f"cylinder3d-j2-{case.n}", "precision": "f64", "slow_steps": len(steps),
+           "substeps": sub, "forward_s": tf, "reverse_s": ta,
+           "reverse_value": case.n * sub / ta, "unit": UNIT, "reverse_over_forward": ta / tf,
+           "dtheta_nonzero": [bool(x != 0) for x in th],
+           "timing": "host wall clock, stream synchronised; the reverse time includes the "
+                     "taped recomputation of the step"}
+    if args.twins:
+        out["err_vs_oracle"] = adjoint_twin_error(ctx, M)
+    return out
+
+
+def adjoint_twin_error(ctx, M):
+    """Parameter gradients of the reverse mode (FP64 and mixed bodies) against
+    the PyTorch reverse-mode oracle on a small J2 cylinder (4 x 2 mm, two slow
+    steps of 8 substeps): the largest relative difference over the five
+    parameters the objective depends on (E and the hardening law)."""
+    import numpy as np
+    import torch
+    import oracle
+    from oracle import adjoint as A
+    from synth import bodies as B
+    case = B.cylinder3d(L=4e-3, R=1e-3, dx=0.25e-3, n_slow=10)
+    rng = np.random.default_rng(11)
+    w_tip, w_f = rng.normal(size=3), rng.normal(size=3)
+    nsub, out = 8, {"n": case.n, "slow_steps": 2, "substeps_per_slow_step": 8}
+    th_o = None
+    for prec, name in ((M.FP64, "fp64"), (M.MIXED, "mixed")):
+        gb = M.body_from_case(ctx, case, prec)
+        steps = [dict(ramp=l / case.plan.n_ramp, ke_tol=-1.0, max_substeps=nsub) for l in (1, 2)]
+        ck = []
+        for p in steps:
+            ck.append(gb.save_state())
+            gb.advance_slow_step(**p)
+        gb.adjoint_enable(nsub)
+        gb.adjoint_seed(tip_bar=w_tip, force_bar=w_f)
+        th = np.zeros(7)
+        for p, c in zip(reversed(steps), reversed(ck)):
+            gb.load_state(c)
+            th += gb.adjoint_slow_step(nsub, **p)
+        if th_o is None:
+            ob = oracle.body_from_case(case, damp_layout=gb.damping_layout())
+            tb = A.TorchBody(case, ob)
+            tt = tb.theta0().clone().requires_grad_(True)
+            st = tb.initial_state()
+            for p in steps:
+                st, ef, tip, _ = tb.slow_step(st, tt, p["ramp"], nsub)
+            L = (torch.from_numpy(w_tip) * tip).sum() + (torch.from_numpy(w_f) * ef).sum()
+            th_o = torch.autograd.grad(L, tt)[0].numpy()
+        gb.close()
+        out[f"{name}_theta_rel_err"] = float(max(abs(th[k] - th_o[k]) / abs(th_o[k])
+                                                 for k in range(5)))
+    return out
 
 
 def measure_next_rows(ctx, M, args):
