@@ -940,16 +940,24 @@ def run_ours(args, rank, world, local):
         if args.twins:
             cyl["err_vs_oracle"] = twin_error(ctx, M, B.cylinder3d(L=6e-3, R=1.5e-3, n_slow=500),
                                               2, 30, prec)
-    compare = (measure_compare(ctx, M, args) if args.compare_instances > 0 and rank == 0
-               and within_budget("compare") else None)
-    batch = (measure_batch(ctx, args, M, rank, world, dist) if args.batch_count > 0
-             and (world > 1 or within_budget("batch")) else None)
-    adjoint = (measure_adjoint(ctx, args, M, B.cylinder3d())
+    def leg(name, run):
+        """One side leg with the clocks seen during it (median SM clock, reasons)."""
+        h0 = time.monotonic()
+        out = run()
+        if isinstance(out, dict):
+            out["clocks"] = clocks.summary(h0, time.monotonic(), name)
+        return out
+
+    compare = (leg("compare", lambda: measure_compare(ctx, M, args))
+               if args.compare_instances > 0 and rank == 0 and within_budget("compare") else None)
+    batch = (leg("batch", lambda: measure_batch(ctx, args, M, rank, world, dist))
+             if args.batch_count > 0 and (world > 1 or within_budget("batch")) else None)
+    adjoint = (leg("adjoint", lambda: measure_adjoint(ctx, args, M, B.cylinder3d()))
                if args.adjoint_steps > 0 and rank == 0 and within_budget("adjoint") else None)
-    nxt = (measure_next_rows(ctx, M, args) if args.next_rows > 0 and rank == 0
-           and within_budget("next rows") else None)
-    study = (measure_ke_study(ctx, M, args.ke_study) if args.ke_study > 0 and rank == 0
-             and within_budget("criterion study") else None)
+    nxt = (leg("next rows", lambda: measure_next_rows(ctx, M, args))
+           if args.next_rows > 0 and rank == 0 and within_budget("next rows") else None)
+    study = (leg("criterion study", lambda: measure_ke_study(ctx, M, args.ke_study))
+             if args.ke_study > 0 and rank == 0 and within_budget("criterion study") else None)
     clocks.stop()
     if rank != 0:
         return
