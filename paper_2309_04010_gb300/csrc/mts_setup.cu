@@ -670,12 +670,18 @@ __global__ void k_halo_x(const long long *hoff, const int32_t *halo, long long n
     for (int k = 0; k < P; ++k) hx[e * P + k] = (R)(x[k] - o[k]);
 }
 
-__global__ void k_tile_w(const long long *off, long long n, int T, long long ntiles, long long *w) {
+// longest neighbour list whose visiting order is scheduled (longer lists keep
+// the CSR order)
+constexpr int kEllOrderCap = 128;
+
+__global__ void k_tile_w(const long long *off, long long n, int T, long long ntiles, long long *w,
+                         unsigned int *wmax) {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
     long long m = 0;
     for (long long i = t * T; i < min(n, (t + 1) * T); ++i) m = max(m, off[i + 1] - off[i]);
     w[t] = m * T;
+    if (m <= kEllOrderCap) atomicMax(wmax, (unsigned int)m);
 }
 
 __device__ int find_slot(const int32_t *h, long long len, int32_t key) {
@@ -688,11 +694,12 @@ __device__ int find_slot(const int32_t *h, long long len, int32_t key) {
     return (int)lo;
 }
 
-// longest neighbour list whose visiting order is bank-balanced (longer lists
-// keep the CSR order)
-constexpr int kEllOrderCap = 128;
-
-__global__ void k_local_ell(const long long *off, const int32_t *idx, long long n, int T, int dim,
+// Per tile: the local slot of every particle (lself) and its neighbours' halo
+// slots in CSR order, neighbour-major (entry j of tile lane k at j * T + k),
+// padded to the tile's width with the particle's own slot (a zero
+// contribution: the kernel gradient vanishes at r = 0).  Lanes past the end of
+// the body hold slot 0 and are never read.
+__global__ void k_local_ell(const long long *off, const int32_t *idx, long long n, int T,
                             long long ntiles, const long long *hoff, const int32_t *halo,
                             const long long *loff, int32_t *tw, uint16_t *lell, uint16_t *lself) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -703,49 +710,239 @@ __global__ void k_local_ell(const long long *off, const int32_t *idx, long long 
     if (lane == 0) tw[t] = (int32_t)width;
     const int32_t *h = halo + hoff[t];
     long long hl = hoff[t + 1] - hoff[t];
+    uint16_t *out = lell + loff[t] + lane;
     if (i >= n) {
-        for (long long j = 0; j < width; ++j) lell[loff[t] + j * T + lane] = 0;
+        for (long long j = 0; j < width; ++j) out[j * T] = 0;
         return;
     }
     int self = find_slot(h, hl, (int32_t)i);
     lself[i] = (uint16_t)self;
     long long deg = off[i + 1] - off[i];
-    uint16_t *out = lell + loff[t] + lane;
-    if (width > kEllOrderCap) {   // CSR order
-        for (long long j = 0; j < width; ++j)
-            out[j * T] = (uint16_t)(j < deg ? find_slot(h, hl, idx[off[i] + j]) : self);
-        return;
+    for (long long j = 0; j < width; ++j)
+        out[j * T] = (uint16_t)(j < deg ? find_slot(h, hl, idx[off[i] + j]) : self);
+}
+
+// Visiting order of the gathers.  The order in which a particle visits its
+// neighbours is free (it moves only the rounding of the sums).  The 3D gathers
+// stage one 16-byte unit (or a 48-byte record of three) per halo slot, so slot s
+// sits in bank group s mod 8 (3s + unit mod 8), and a 16-byte shared load is
+// served eight lanes at a time: its cost is, over those eight lanes, the
+// largest number of DIFFERENT slots that fall in one bank group (lanes reading
+// the same slot share one access).  In 2D the positions are 8-byte slots
+// served sixteen lanes at a time, residues mod 16.  The eight (sixteen) lanes
+// of a group are neighbouring particles whose lists overlap heavily, so the
+// schedule builds each step as a set of slots, at most one per residue, that
+// every lane of the group holds among its unvisited entries: residues are
+// taken in descending remaining demand (the sum over their slots of the
+// largest number of visits a lane still owes the slot), and for each the slot
+// held by the most lanes not yet served at this step (then the larger
+// demand, then the smaller slot).  Each lane takes, among the step's slots it
+// holds, the one of the most-demanded residue (then its own larger count, then
+// the smaller slot); a lane holding none takes its entry of the most-demanded
+// residue (a conflict).  Ties are broken by slot values only, so the order is
+// deterministic.  One warp per group; its lanes' lists (CSR order, written by
+// k_local_ell) are read into a shared-memory hash table of slot -> per-lane
+// counts and then overwritten in place, step by step.  Every lane of the group
+// emits exactly the multiset of entries it was given.
+struct EllSchedSmem {
+    static size_t bytes(int H, int G) {
+        return (size_t)H * 2 + (size_t)H * G + (size_t)H + (size_t)H * 2 + 4 * 4 * 17;
     }
-    // Visiting order: the 3D gathers stage one 16-byte unit (or a 48-byte
-    // record of three) per halo slot, so slot s sits in bank group s mod 8
-    // (3s mod 8) and a 16-byte shared load serves eight lanes at a time.  At
-    // step j, lane k takes its first unvisited slot with s = k + j (mod M),
-    // else its first unvisited slot: the lanes served together then read
-    // distinct banks whenever their lists allow.  M = 8 in 3D; M = 16 in 2D,
-    // where the positions are 8-byte slots loaded sixteen lanes at a time.
-    // Padding entries (the particle itself, zero contribution) take part like
-    // any slot.
-    uint16_t sl[kEllOrderCap];
-    for (long long e = 0; e < width; ++e)
-        sl[e] = (uint16_t)(e < deg ? find_slot(h, hl, idx[off[i] + e]) : self);
-    uint32_t used[kEllOrderCap / 32];
-    for (int q = 0; q < kEllOrderCap / 32; ++q) used[q] = 0u;
-    const int mask = dim == 2 ? 15 : 7;
-    const int k = lane & mask;
-    for (long long j = 0; j < width; ++j) {
-        const int r = (int)((k + j) & mask);
-        int pick = -1, any = -1;
-        for (int e = 0; e < (int)width; ++e) {
-            if ((used[e >> 5] >> (e & 31)) & 1u) continue;
-            if (any < 0) any = e;
-            if ((sl[e] & mask) == r) {
-                pick = e;
-                break;
-            }
+};
+
+template <int G>
+__device__ __forceinline__ unsigned ell_lane_mask(const uint32_t *cw, int nvalid) {
+    unsigned m = 0u;
+#pragma unroll
+    for (int w = 0; w < G / 4; ++w) {
+        const uint32_t x = cw[w];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            if ((x >> (8 * b)) & 0xffu) m |= 1u << (4 * w + b);
+    }
+    return m & ((1u << nvalid) - 1u);
+}
+
+template <int G>
+__device__ __forceinline__ int ell_lane_max(const uint32_t *cw) {
+    int mx = 0;
+#pragma unroll
+    for (int w = 0; w < G / 4; ++w) {
+        const uint32_t x = cw[w];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) mx = max(mx, (int)((x >> (8 * b)) & 0xffu));
+    }
+    return mx;
+}
+
+template <int G>
+__global__ void __launch_bounds__(32) k_ell_schedule(uint16_t *lell, const long long *loff,
+                                                     const int32_t *tw, int T, long long n,
+                                                     long long ngroups, int lgH) {
+    constexpr int M = G;                 // residues
+    constexpr int CW = G / 4;            // count words per table entry
+    constexpr uint16_t kEmpty = 0xffffu;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int H = 1 << lgH;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);                 // H x CW
+    uint16_t *key = reinterpret_cast<uint16_t *>(cnt + (size_t)H * CW); // H
+    uint16_t *bidx = key + H;                                           // H (bucketed entries)
+    uint8_t *umx = reinterpret_cast<uint8_t *>(bidx + H);               // H
+    int *boff = reinterpret_cast<int *>(umx + ((H + 15) & ~15));        // M + 1
+    int *bfill = boff + (M + 1);                                        // M
+    int *dem = bfill + M;                                               // M
+    int *sel = dem + M;                                                 // M
+    const int lane = threadIdx.x;
+    const unsigned full = 0xffffffffu;
+    const int nq = T / G;
+    for (long long gq = blockIdx.x; gq < ngroups; gq += gridDim.x) {
+        const long long t = gq / nq;
+        const int q = (int)(gq - t * nq);
+        const int W = tw[t];
+        const long long first = t * (long long)T + (long long)q * G;
+        const int nvalid = (int)min((long long)G, n - first);
+        if (W <= 1 || W > kEllOrderCap || nvalid <= 0) continue;
+        uint16_t *base = lell + loff[t] + (long long)q * G;
+        for (int h = lane; h < H; h += 32) {
+            key[h] = kEmpty;
+            umx[h] = 0;
+#pragma unroll
+            for (int w = 0; w < CW; ++w) cnt[h * CW + w] = 0u;
         }
-        if (pick < 0) pick = any;
-        used[pick >> 5] |= 1u << (pick & 31);
-        out[j * T] = sl[pick];
+        if (lane < M) {
+            bfill[lane] = 0;
+            dem[lane] = 0;
+            sel[lane] = -1;
+        }
+        __syncwarp();
+        // lists -> table of slot -> per-lane counts (linear probing; the table
+        // holds at least twice the entries, so a free cell always exists)
+        const int ne = nvalid * W;
+        for (int e = lane; e < ne; e += 32) {
+            const int k = e / W, j = e - k * W;
+            const uint16_t s = base[(long long)j * T + k];
+            unsigned h = ((unsigned)s * 0x9E3779B1u) >> (32 - lgH);
+            for (int probe = 0; probe < H; ++probe) {
+                const unsigned short old = atomicCAS(reinterpret_cast<unsigned short *>(key + h),
+                                                     (unsigned short)kEmpty, (unsigned short)s);
+                if (old == kEmpty || old == s) break;
+                h = (h + 1) & (unsigned)(H - 1);
+            }
+            atomicAdd(cnt + h * CW + (k >> 2), 1u << (8 * (k & 3)));
+        }
+        __syncwarp();
+        // bucket the occupied cells by residue; initial demand per residue
+        for (int h = lane; h < H; h += 32)
+            if (key[h] != kEmpty) atomicAdd(bfill + (key[h] % M), 1);
+        __syncwarp();
+        if (lane == 0) {
+            int acc = 0;
+            for (int r = 0; r < M; ++r) {
+                boff[r] = acc;
+                acc += bfill[r];
+                bfill[r] = 0;
+            }
+            boff[M] = acc;
+        }
+        __syncwarp();
+        for (int h = lane; h < H; h += 32)
+            if (key[h] != kEmpty) {
+                const int r = key[h] % M;
+                bidx[boff[r] + atomicAdd(bfill + r, 1)] = (uint16_t)h;
+                const int mx = ell_lane_max<G>(cnt + h * CW);
+                umx[h] = (uint8_t)mx;
+                atomicAdd(dem + r, mx);
+            }
+        __syncwarp();
+        for (int j = 0; j < W; ++j) {
+            int dm[M];
+#pragma unroll
+            for (int r = 0; r < M; ++r) dm[r] = dem[r];
+            unsigned unc = (1u << nvalid) - 1u, taken = 0u;
+            // the step's slots: residues by descending demand (then index)
+            for (int it = 0; it < M && unc; ++it) {
+                int r = -1, best = -1;
+#pragma unroll
+                for (int rr = 0; rr < M; ++rr)
+                    if (!((taken >> rr) & 1u) && dm[rr] > best) {
+                        best = dm[rr];
+                        r = rr;
+                    }
+                taken |= 1u << r;
+                unsigned bk = 0u, bm = 0u;
+                int bh = -1;
+                for (int x = boff[r] + lane; x < boff[r + 1]; x += 32) {
+                    const int h = bidx[x];
+                    const unsigned m = ell_lane_mask<G>(cnt + h * CW, nvalid) & unc;
+                    if (!m) continue;
+                    const unsigned kk = ((unsigned)__popc(m) << 24) | ((unsigned)umx[h] << 16) |
+                                        (unsigned)(0xffffu - key[h]);
+                    if (kk > bk) {
+                        bk = kk;
+                        bh = h;
+                        bm = m;
+                    }
+                }
+                const unsigned wk = __reduce_max_sync(full, bk);
+                if (wk == 0u) continue;
+                const unsigned src = __ffs(__ballot_sync(full, bk == wk)) - 1;
+                bh = __shfl_sync(full, bh, src);
+                bm = __shfl_sync(full, bm, src);
+                if (lane == 0) sel[r] = bh;
+                unc &= ~bm;
+            }
+            __syncwarp();
+            // each lane of the group takes its entry of this step
+            int pick = -1;
+            if (lane < nvalid) {
+                const int byte = 8 * (lane & 3), word = lane >> 2;
+                unsigned long long bk = 0ull;
+#pragma unroll
+                for (int r = 0; r < M; ++r) {
+                    const int h = sel[r];
+                    if (h < 0) continue;
+                    const unsigned c = (cnt[h * CW + word] >> byte) & 0xffu;
+                    if (!c) continue;
+                    const unsigned long long kk = ((unsigned long long)(dm[r] + 1) << 32) |
+                                                  ((unsigned long long)c << 16) |
+                                                  (unsigned long long)(0xffffu - key[h]);
+                    if (kk > bk) {
+                        bk = kk;
+                        pick = h;
+                    }
+                }
+                if (pick < 0) {   // no slot of this step: a conflict
+                    for (int x = 0; x < boff[M]; ++x) {
+                        const int h = bidx[x];
+                        const unsigned c = (cnt[h * CW + word] >> byte) & 0xffu;
+                        if (!c) continue;
+                        const unsigned long long kk = ((unsigned long long)(dm[key[h] % M] + 1) << 32) |
+                                                      ((unsigned long long)c << 16) |
+                                                      (unsigned long long)(0xffffu - key[h]);
+                        if (kk > bk) {
+                            bk = kk;
+                            pick = h;
+                        }
+                    }
+                }
+                base[(long long)j * T + lane] = key[pick];
+                atomicSub(cnt + pick * CW + word, 1u << byte);
+            }
+            __syncwarp();
+            // new demand of the slots taken (one lane per distinct slot)
+            const unsigned same = __match_any_sync(full, pick);
+            if (pick >= 0 && lane == __ffs(same) - 1) {
+                const int mx = ell_lane_max<G>(cnt + pick * CW);
+                const int d = (int)umx[pick] - mx;
+                if (d) {
+                    umx[pick] = (uint8_t)mx;
+                    atomicSub(dem + key[pick] % M, d);
+                }
+            }
+            if (lane < M) sel[lane] = -1;
+            __syncwarp();
+        }
+        __syncwarp();
     }
 }
 
@@ -900,16 +1097,37 @@ mts_status build_tiles(mts_body *b, Tmp &tmp, cudaStream_t st, int T) {
     NEED(w);
     MTS_TRY(dalloc_t(ctx, &b->lell_off, ntiles + 1));
     MTS_TRY(dalloc_t(ctx, &b->tile_w, ntiles + 1));
-    k_tile_w<<<grid_for(ntiles), TPB, 0, st>>>(b->nb_off, n, T, ntiles, w);
+    unsigned int *wmx = tmp.get<unsigned int>(1);
+    NEED(wmx);
+    MTS_CUDA(cudaMemsetAsync(wmx, 0, sizeof(unsigned), st));
+    k_tile_w<<<grid_for(ntiles), TPB, 0, st>>>(b->nb_off, n, T, ntiles, w, wmx);
     MTS_CUDA(cudaMemsetAsync(w + ntiles, 0, sizeof(long long), st));
     MTS_TRY(cub_excl_sum(tmp, w, b->lell_off, ntiles + 1, st));
     long long len = 0;
     MTS_TRY(to_host(&len, b->lell_off + ntiles, 1, st));
     MTS_TRY(dalloc_t(ctx, &b->lell, std::max(len, 1LL)));
     MTS_TRY(dalloc_t(ctx, &b->lself, n));
-    k_local_ell<<<grid_for(ntiles * T), TPB, 0, st>>>(b->nb_off, b->nb_idx, n, T, b->dim, ntiles,
+    k_local_ell<<<grid_for(ntiles * T), TPB, 0, st>>>(b->nb_off, b->nb_idx, n, T, ntiles,
                                                         b->halo_off, b->halo_idx, b->lell_off,
                                                         b->tile_w, b->lell, b->lself);
+    unsigned int wmax = 0;
+    MTS_TRY(to_host(&wmax, wmx, 1, st));
+    if (wmax > 1) {
+        const int G = b->dim == 2 ? 16 : 8;
+        int lgH = 6;
+        while ((1 << lgH) < 2 * G * (int)wmax) ++lgH;
+        const size_t sm = EllSchedSmem::bytes(1 << lgH, G);
+        const long long ngroups = ntiles * (T / G);
+        const unsigned grid = (unsigned)std::min(ngroups, 1LL << 20);
+        if (G == 16) {
+            MTS_CUDA(cudaFuncSetAttribute(k_ell_schedule<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_ell_schedule<16><<<grid, 32, sm, st>>>(b->lell, b->lell_off, b->tile_w, T, n, ngroups, lgH);
+        } else {
+            MTS_CUDA(cudaFuncSetAttribute(k_ell_schedule<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_ell_schedule<8><<<grid, 32, sm, st>>>(b->lell, b->lell_off, b->tile_w, T, n, ngroups, lgH);
+        }
+        MTS_CUDA(cudaGetLastError());
+    }
     b->T = T;
     b->ntiles = ntiles;
     return MTS_OK;

@@ -70,7 +70,7 @@ __device__ __forceinline__ void compute_F(const Args<R> &A, const R *sX, const R
             for (int c = 0; c < D; ++c) G[r][c] += du * d[c];
         }
     };
-    for_each_neighbour(row, T, w, [&](int l) {
+    for_each_neighbour_chunks(row, T, w, [&](int l) {
         R xb[P], ub[P];
         ld_vec<R, P>(xb, sX + l * P);
         ld_vec<R, P>(ub, sU + l * P);

@@ -73,4 +73,30 @@ __device__ __forceinline__ void for_each_neighbour(const uint16_t *row, int T, i
     }
 }
 
+// The same visit with the whole chunks of 8 run without a per-entry test and
+// the last, partial chunk tested entry by entry.  It issues ~18 % fewer
+// instructions in the F gather (the stress kernel, bound by instruction issue:
+// 2.4 % faster on the 2.5 M-particle plate); the force gather, whose shared-
+// memory loads dominate, ran slower with it and keeps the form above.
+template <class Body>
+__device__ __forceinline__ void for_each_neighbour_chunks(const uint16_t *row, int T, int w, Body body) {
+    constexpr int K = 8;
+    int cur[K], nxt[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) cur[u] = u < w ? (int)__ldg(row + u * T) : 0;
+    int j0 = 0;
+    for (; j0 + K <= w; j0 += K) {
+#pragma unroll
+        for (int u = 0; u < K; ++u)
+            nxt[u] = (j0 + K + u < w) ? (int)__ldg(row + (j0 + K + u) * T) : 0;
+#pragma unroll
+        for (int u = 0; u < K; ++u) body(cur[u]);
+#pragma unroll
+        for (int u = 0; u < K; ++u) cur[u] = nxt[u];
+    }
+#pragma unroll
+    for (int u = 0; u < K - 1; ++u)
+        if (u < w - j0) body(cur[u]);
+}
+
 }  // namespace mts
