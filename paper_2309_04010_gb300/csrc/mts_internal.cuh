@@ -53,6 +53,13 @@ __host__ __device__ __forceinline__ int damp_slot_pos(int s, int slot_bytes) {
     return slot_bytes == 16 ? (s ^ (((s >> 3) * 3) & 7)) : s;
 }
 __host__ __device__ __forceinline__ int damp_slot_count(int nb_mb) { return (nb_mb + 1 + 7) & ~7; }
+// pair_slot of a canonical pair: its slot in the padded per-level layout; bit
+// kSlotSwapBit set when the set-up stored the pair's two particles in the
+// other order in the slot word (low half: pair_b).  A free pair's update is
+// symmetric in its two particles bit for bit, so the order only moves the
+// shared-memory accesses.
+constexpr int kSlotSwapBit = 62;
+constexpr long long kSlotMask = (1LL << kSlotSwapBit) - 1;
 constexpr int kWholeAxis = 62; // owner-block shift of an unblocked axis
 constexpr int kWideThreads = 256;   // threads of the CTA-per-group damping kernel
 constexpr int kWideRing = 8;        // level buffers of its pair-data ring

@@ -480,9 +480,10 @@ __global__ void k_scatter(const T *src, const long long *order, long long m, T *
 }
 
 // padded kernel layout: level L of the canonical order occupies slots
-// [32 L, 32 L + 32); pair p sits at slot 32 L + (p - first pair of L)
+// [32 L, 32 L + 32); pair p sits at slot 32 L + lane (lane & 31 of k_level_lanes)
 // slot words hold byte offsets (slot index * bytes per velocity slot) of the
-// two particles in the damping kernel's staged velocities
+// two particles in the damping kernel's staged velocities, in the order the
+// lane assignment chose (bit 5 of lane: pair_b first)
 __global__ void k_fill_slots(const unsigned long long *key2s, long long m, const int32_t *grp_lvl,
                              const long long *lvl_pair, const uint32_t *ab, const int8_t *lane,
                              long long *slot, uint32_t *kab, int bps) {
@@ -491,69 +492,189 @@ __global__ void k_fill_slots(const unsigned long long *key2s, long long m, const
     const long long g = (long long)(key2s[p] >> 8);
     const int s = (int)(key2s[p] & 255);
     const long long L = grp_lvl[g] + s;
-    const long long sl = 32 * L + lane[p];
-    slot[p] = sl;
-    const uint32_t la = (uint32_t)damp_slot_pos((int)(ab[p] & 0xffffu), bps);
-    const uint32_t lb = (uint32_t)damp_slot_pos((int)(ab[p] >> 16), bps);
+    const int lv = lane[p];
+    const bool sw = (lv & 32) != 0;
+    const long long sl = 32 * L + (lv & 31);
+    slot[p] = sl | (sw ? (1LL << kSlotSwapBit) : 0LL);
+    uint32_t la = (uint32_t)damp_slot_pos((int)(ab[p] & 0xffffu), bps);
+    uint32_t lb = (uint32_t)damp_slot_pos((int)(ab[p] >> 16), bps);
+    if (sw) {
+        const uint32_t t = la;
+        la = lb;
+        lb = t;
+    }
     kab[sl] = (la * (uint32_t)bps) | ((lb * (uint32_t)bps) << 16);
 }
 
-// Lane of each pair inside its level (a level's pairs touch disjoint
-// particles, so any assignment gives the same result).  With 16-byte slots a
-// 128-bit shared access is served per quarter-warp, and two lanes of one
-// quarter that hit different slots of one 16-byte bank group conflict; the
-// pairs are placed, the most crowded bank groups first, in the quarter that
-// keeps the largest per-quarter count of their a and b bank groups lowest.
+// Lane and particle order of each pair inside its level.  A level's pairs
+// touch disjoint particles, so any assignment gives the same result, and a
+// free pair's update is symmetric in its particles bit for bit.  With 16-byte
+// slots a 128-bit shared access is served eight lanes (a quarter-warp) at a
+// time, and its cost there is the largest number of lanes whose slots fall in
+// one 16-byte bank group (empty lanes of a quarter with a pair read that
+// pair's slots: free).  A level step loads and stores both particles, so a
+// quarter costs 2 (mA + mB) wavefronts, mA and mB the largest bank-group
+// counts of its first and second particles (2 for a quarter without pairs:
+// its lanes load one dummy slot).  The pairs are placed greedily, the most
+// crowded bank groups first, in the quarter that keeps those counts lowest;
+// then a local search over the pairs that share a bank group in their quarter
+// tries reversing the pair, then moving it to each lane of the other quarters
+// (exchanging with that lane's pair, either in either order) and keeps the
+// first change that lowers the cost of the two quarters, up to four passes.
 // Other slot sizes keep the canonical order.
+__device__ __forceinline__ int lanes_max8(const uint8_t *h) {
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m = max(m, (int)h[k]);
+    return m;
+}
+
 __global__ void k_level_lanes(const long long *lvl_pair, long long nlev, const uint32_t *ab,
                               int bps, int8_t *lane) {
     const long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (L >= nlev) return;
     const long long p0 = lvl_pair[L];
     const int n = (int)(lvl_pair[L + 1] - p0);
-    if (bps != 16 || n <= 8 || n > 32) {
+    if (bps != 16 || n <= 1 || n > 32) {
         for (int k = 0; k < n; ++k) lane[p0 + k] = (int8_t)k;
         return;
     }
-    int ga[32], gb[32], ord[32];
-    int fa[8] = {0, 0, 0, 0, 0, 0, 0, 0}, fb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int ga[32], gb[32], ord[32], pos[32];
     for (int k = 0; k < n; ++k) {
         ga[k] = damp_slot_pos((int)(ab[p0 + k] & 0xffffu), bps) & 7;
         gb[k] = damp_slot_pos((int)(ab[p0 + k] >> 16), bps) & 7;
-        ++fa[ga[k]];
-        ++fb[gb[k]];
+        pos[k] = k;
     }
-    // visit order: descending fa[ga] + fb[gb], ties by canonical position
-    for (int k = 0; k < n; ++k) ord[k] = k;
-    for (int i = 1; i < n; ++i) {
-        const int x = ord[i], kx = fa[ga[x]] + fb[gb[x]];
-        int j = i - 1;
-        while (j >= 0 && fa[ga[ord[j]]] + fb[gb[ord[j]]] < kx) {
-            ord[j + 1] = ord[j];
-            --j;
+    if (n > 8) {
+        int fa[8] = {0, 0, 0, 0, 0, 0, 0, 0}, fb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = 0; k < n; ++k) {
+            ++fa[ga[k]];
+            ++fb[gb[k]];
         }
-        ord[j + 1] = x;
+        // visit order: descending fa[ga] + fb[gb], ties by canonical position
+        for (int k = 0; k < n; ++k) ord[k] = k;
+        for (int i = 1; i < n; ++i) {
+            const int x = ord[i], kx = fa[ga[x]] + fb[gb[x]];
+            int j = i - 1;
+            while (j >= 0 && fa[ga[ord[j]]] + fb[gb[ord[j]]] < kx) {
+                ord[j + 1] = ord[j];
+                --j;
+            }
+            ord[j + 1] = x;
+        }
+        int ca[4][8], cb[4][8], size[4] = {0, 0, 0, 0}, ma[4] = {0, 0, 0, 0}, mxb[4] = {0, 0, 0, 0};
+        for (int q = 0; q < 4; ++q)
+            for (int k = 0; k < 8; ++k) ca[q][k] = cb[q][k] = 0;
+        for (int i = 0; i < n; ++i) {
+            const int k = ord[i];
+            int best = -1, bc0 = 0, bc1 = 0;
+            for (int q = 0; q < 4; ++q) {
+                if (size[q] >= 8) continue;
+                const int c0 = max(ca[q][ga[k]] + 1, ma[q]) + max(cb[q][gb[k]] + 1, mxb[q]);
+                const int c1 = ca[q][ga[k]] + cb[q][gb[k]];
+                if (best < 0 || c0 < bc0 || (c0 == bc0 && (c1 < bc1 || (c1 == bc1 && size[q] < size[best])))) {
+                    best = q;
+                    bc0 = c0;
+                    bc1 = c1;
+                }
+            }
+            pos[k] = best * 8 + size[best];
+            ++size[best];
+            ma[best] = max(ma[best], ++ca[best][ga[k]]);
+            mxb[best] = max(mxb[best], ++cb[best][gb[k]]);
+        }
     }
-    int ca[4][8], cb[4][8], size[4] = {0, 0, 0, 0}, ma[4] = {0, 0, 0, 0}, mxb[4] = {0, 0, 0, 0};
+    // local search
+    int at[32];
+    bool fl[32];
+    uint8_t hA[4][8], hB[4][8];
+    int cnt[4] = {0, 0, 0, 0};
+    for (int i = 0; i < 32; ++i) at[i] = -1;
     for (int q = 0; q < 4; ++q)
-        for (int k = 0; k < 8; ++k) ca[q][k] = cb[q][k] = 0;
-    for (int i = 0; i < n; ++i) {
-        const int k = ord[i];
-        int best = -1, bc0 = 0, bc1 = 0;
-        for (int q = 0; q < 4; ++q) {
-            if (size[q] >= 8) continue;
-            const int c0 = max(ca[q][ga[k]] + 1, ma[q]) + max(cb[q][gb[k]] + 1, mxb[q]);
-            const int c1 = ca[q][ga[k]] + cb[q][gb[k]];
-            if (best < 0 || c0 < bc0 || (c0 == bc0 && (c1 < bc1 || (c1 == bc1 && size[q] < size[best])))) {
-                best = q;
-                bc0 = c0;
-                bc1 = c1;
+        for (int k = 0; k < 8; ++k) hA[q][k] = hB[q][k] = 0;
+    for (int k = 0; k < n; ++k) {
+        at[pos[k]] = k;
+        fl[k] = false;
+        ++hA[pos[k] >> 3][ga[k]];
+        ++hB[pos[k] >> 3][gb[k]];
+        ++cnt[pos[k] >> 3];
+    }
+    auto qcost = [&](int q) { return cnt[q] ? 2 * (lanes_max8(hA[q]) + lanes_max8(hB[q])) : 2; };
+    for (int pass = 0; pass < 4; ++pass) {
+        bool improved = false;
+        for (int i = 0; i < 32; ++i) {
+            const int k = at[i];
+            if (k < 0) continue;
+            const int qi = i >> 3;
+            const int a = fl[k] ? gb[k] : ga[k], b = fl[k] ? ga[k] : gb[k];
+            if (hA[qi][a] <= 1 && hB[qi][b] <= 1) continue;
+            const int base_i = qcost(qi);
+            // the pair reversed
+            --hA[qi][a]; --hB[qi][b]; ++hA[qi][b]; ++hB[qi][a];
+            if (qcost(qi) < base_i) {
+                fl[k] = !fl[k];
+                improved = true;
+                continue;
+            }
+            --hA[qi][b]; --hB[qi][a]; ++hA[qi][a]; ++hB[qi][b];
+            bool done = false;
+            for (int j = 0; j < 32 && !done; ++j) {
+                const int qj = j >> 3;
+                if (qj == qi) continue;
+                const int k2 = at[j];
+                const int base = base_i + qcost(qj);
+                const int a2 = k2 < 0 ? 0 : (fl[k2] ? gb[k2] : ga[k2]);
+                const int b2 = k2 < 0 ? 0 : (fl[k2] ? ga[k2] : gb[k2]);
+                for (int v = 0; v < (k2 < 0 ? 2 : 4) && !done; ++v) {
+                    const bool fi = v & 1, fj = (v >> 1) & 1;
+                    const int ai = fi ? b : a, bi = fi ? a : b;
+                    const int aj = fj ? b2 : a2, bj = fj ? a2 : b2;
+                    --hA[qi][a]; --hB[qi][b]; --cnt[qi];
+                    ++hA[qj][ai]; ++hB[qj][bi]; ++cnt[qj];
+                    if (k2 >= 0) {
+                        --hA[qj][a2]; --hB[qj][b2]; --cnt[qj];
+                        ++hA[qi][aj]; ++hB[qi][bj]; ++cnt[qi];
+                    }
+                    if (qcost(qi) + qcost(qj) < base) {
+                        at[i] = k2;
+                        at[j] = k;
+                        if (fi) fl[k] = !fl[k];
+                        if (k2 >= 0 && fj) fl[k2] = !fl[k2];
+                        done = improved = true;
+                        break;
+                    }
+                    if (k2 >= 0) {
+                        --hA[qi][aj]; --hB[qi][bj]; --cnt[qi];
+                        ++hA[qj][a2]; ++hB[qj][b2]; ++cnt[qj];
+                    }
+                    --hA[qj][ai]; --hB[qj][bi]; --cnt[qj];
+                    ++hA[qi][a]; ++hB[qi][b]; ++cnt[qi];
+                }
             }
         }
-        lane[p0 + k] = (int8_t)(best * 8 + size[best]);
-        ++size[best];
-        ma[best] = max(ma[best], ++ca[best][ga[k]]);
-        mxb[best] = max(mxb[best], ++cb[best][gb[k]]);
+        if (!improved) break;
+    }
+    for (int i = 0; i < 32; ++i)
+        if (at[i] >= 0) lane[p0 + at[i]] = (int8_t)(i | (fl[at[i]] ? 32 : 0));
+}
+
+// Empty slots of a quarter-warp that holds a pair take that pair's word
+// (coefficient 0: the lane loads what a neighbour lane loads, a broadcast,
+// and stores nothing); quarters without a pair keep the dummy slot.
+__global__ void k_fill_empty(uint32_t *kab, long long nlev, uint32_t dummy_word) {
+    const long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (L >= nlev) return;
+    uint32_t *w = kab + 32 * L;
+    for (int q = 0; q < 4; ++q) {
+        uint32_t first = dummy_word;
+        for (int k = 0; k < 8; ++k)
+            if (w[8 * q + k] != dummy_word) {
+                first = w[8 * q + k];
+                break;
+            }
+        if (first == dummy_word) continue;
+        for (int k = 0; k < 8; ++k)
+            if (w[8 * q + k] == dummy_word) w[8 * q + k] = first;
     }
 }
 
@@ -565,7 +686,7 @@ __global__ void k_fill_dummy(uint32_t *kab, long long ns, uint32_t dummy) {
 template <class R>
 __global__ void k_fill_slot_g(const R *g, const long long *slot, long long m, R *kg) {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p < m) kg[slot[p]] = g[p];
+    if (p < m) kg[slot[p] & kSlotMask] = g[p];
 }
 
 __global__ void k_group_of_pair(const long long *gscan, long long m, const int32_t *sub,
@@ -1393,6 +1514,9 @@ mts_status build_damping(mts_body *b, Tmp &tmp, cudaStream_t st, const int *cell
                                                   lane, b->pair_slot, b->kpad_ab, bps);
         k_fill_slot_g<R><<<grid_for(m), TPB, 0, st>>>((const R *)b->pair_g, b->pair_slot, m,
                                                        (R *)b->kpad_g);
+        if (bps == 16)
+            k_fill_empty<<<grid_for(nlev), TPB, 0, st>>>(b->kpad_ab, nlev,
+                                                         (uint32_t)dummy | ((uint32_t)dummy << 16));
         MTS_TRY(dalloc_t(ctx, &b->grp_cons, ngg));
         MTS_CUDA(cudaMemsetAsync(b->grp_cons, 0, ngg, st));   // flags start at zero
     }

@@ -995,13 +995,20 @@ __global__ void k_group_cons(const int32_t *tstart, const int32_t *tcnt, long lo
 }
 
 // blocks layout: the constrained axes of both particles in the low three bits
-// of each byte offset of the padded pair word (low half: pair_a)
+// of each byte offset of the padded pair word (low half: pair_a, or pair_b
+// where the set-up reversed the pair: kSlotSwapBit of pair_slot)
 __global__ void k_pair_fixword(uint32_t *kab, const long long *slot, const int32_t *pa,
                                const int32_t *pb, long long m, const uint8_t *flags, int fixmask) {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= m) return;
-    const uint32_t fa = flags[pa[p]] & fixmask, fb = flags[pb[p]] & fixmask;
-    uint32_t &w = kab[slot[p]];
+    const long long s = slot[p];
+    uint32_t fa = flags[pa[p]] & fixmask, fb = flags[pb[p]] & fixmask;
+    if ((s >> kSlotSwapBit) & 1) {
+        const uint32_t t = fa;
+        fa = fb;
+        fb = t;
+    }
+    uint32_t &w = kab[s & kSlotMask];
     w = (w & ~(7u | (7u << 16))) | fa | (fb << 16);
 }
 
@@ -1012,7 +1019,7 @@ __global__ void k_pair_fixsign(R *kg, const long long *slot, const int32_t *pa, 
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= m) return;
     const bool fix = (flags[pa[p]] | flags[pb[p]]) & fixmask;
-    R &c = kg[slot[p]];
+    R &c = kg[slot[p] & kSlotMask];
     const R a = c < R(0) ? -c : c;
     c = fix ? -a : a;
 }
