@@ -404,6 +404,22 @@ mts_status mts_adjoint_equilibrium(mts_body *body, int64_t max_iters, double tol
                                    double *theta_bar, int64_t *iters);
 
 /* ------------------------------------------------------------------ */
+/* Self-check                                                           */
+/* ------------------------------------------------------------------ */
+/* The paper has no counterpart to this call.  In mixed precision the drift
+ * and force kernels convert between FP32 and FP64 with integer operations
+ * (IEEE 754 binary32/binary64: the same bits as the hardware conversions,
+ * round to nearest even, off the FP64 pipe).  This call checks those
+ * conversions against the hardware's on n counter-hashed bit patterns
+ * (seeded; steered into subnormals, zeros, infinities, NaNs, overflow and
+ * exact rounding ties) on the context's device and stream, and waits.
+ * mismatches[0]: FP32 -> FP64 results that differ, mismatches[1]: FP64 ->
+ * FP32 (two NaNs count as equal).  Allocates 16 bytes of device memory
+ * through the context for the counts.  Errors: MTS_ERR_INVALID_ARG (NULL, n < 0),
+ * MTS_ERR_OOM, MTS_ERR_CUDA. */
+mts_status mts_selftest_conversions(mts_ctx *ctx, int64_t n, uint64_t seed, int64_t *mismatches);
+
+/* ------------------------------------------------------------------ */
 /* Allocation-free reduction                                            */
 /* ------------------------------------------------------------------ */
 /* The paper has no counterpart to this call; it exists for callers that

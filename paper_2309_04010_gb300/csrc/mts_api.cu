@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "mts_internal.cuh"
+#include "mts_device.cuh"
 
 namespace mts {
 
@@ -107,7 +108,7 @@ void body_free(mts_body *b) {
                      (void **)&b->adj_v, (void **)&b->adj_cp, (void **)&b->adj_c,
                      (void **)&b->adj_a, (void **)&b->adj_G, (void **)&b->adj_theta,
                      (void **)&b->adj_part, (void **)&b->adj_ctrl, (void **)&b->pd_blk,
-                     (void **)&b->pd_req, (void **)&b->pd_done};
+                     (void **)&b->pd_req, (void **)&b->pd_done, (void **)&b->d_first};
     for (void **pp : ptrs) {
         dfree(b->ctx, *pp);
         *pp = nullptr;
@@ -621,6 +622,7 @@ mts_status mts_body_create(mts_ctx *ctx, const mts_body_desc *desc, mts_body **o
     A((void **)&b->part_force, ((n + 63) / 64) * 4 * 8);
     A((void **)&b->part_drift, grid * 2 * 8);
     A((void **)&b->scratch, (size_t)n * 18 * 8);
+    A((void **)&b->d_first, 8);
     if (s == MTS_OK && cudaMallocHost((void **)&b->h_ctrl, sizeof(Control)) != cudaSuccess) {
         set_error("pinned allocation failed");
         s = MTS_ERR_OOM;
@@ -997,8 +999,12 @@ mts_status mts_diffusion_dt(mts_body *b, double *dt_paper, double *dt_stable) {
         *dt_stable = lam > 0 ? 1.8 / lam : INFINITY;
         return MTS_OK;
     }
-    double amax = 0;
-    MTS_TRY(diffusion_bound(b, &amax));
+    if (!b->diff_amax_ok || b->diff_amax_D != b->D) {
+        MTS_TRY(diffusion_bound(b, &b->diff_amax));
+        b->diff_amax_D = b->D;
+        b->diff_amax_ok = true;
+    }
+    const double amax = b->diff_amax;
     *dt_stable = amax > 0 ? 0.9 / amax : INFINITY;
     return MTS_OK;
 }
@@ -1252,30 +1258,91 @@ mts_status mts_substep_partial(mts_body *b, double dt, double ramp, int32_t upto
 }  // extern "C"
 
 namespace {
-// index of the first NaN or infinity of x[0, n), -1 if none.  A double is not
-// finite exactly when its eleven exponent bits are all ones; the test runs on
-// the bit patterns in blocks with a branch-free count (vectorised by the
-// compiler), and only a block that holds one is searched element by element.
-int64_t first_nonfinite(const double *x, int64_t n) {
-    constexpr uint64_t kExp = 0x7ff0000000000000ull;
-    constexpr int64_t kB = 4096;
-    for (int64_t b0 = 0; b0 < n; b0 += kB) {
-        const int64_t b1 = std::min(n, b0 + kB);
-        uint64_t bad = 0;
-        for (int64_t i = b0; i < b1; ++i) {
-            uint64_t v;
-            std::memcpy(&v, x + i, sizeof v);
-            bad += (v & kExp) == kExp;
+// smallest index of a non-finite value of x[0, n) (a double is not finite
+// exactly when its eleven exponent bits are all ones); *first starts at ~0
+// self-check of the integer-pipe conversions (f2d_bits, d2f_bits) against
+// the hardware's, on counter-hashed bit patterns steered into the edge cases:
+// binary32 subnormals, zeros, infinities and NaNs; binary64 values whose
+// binary32 result is normal, subnormal, zero or overflows, exact rounding
+// ties, binary64 subnormals and non-finite values
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {   // splitmix64 finaliser
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+__global__ void k_selftest_conv(long long n, unsigned long long seed, unsigned long long *mis) {
+    unsigned long long bad_f2d = 0, bad_d2f = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long x = mix64(seed + (unsigned long long)i), y = mix64(x);
+        uint32_t fb = (uint32_t)x;
+        switch ((x >> 32) & 7u) {
+            case 0: fb &= 0x807fffffu; break;                 // subnormal (or zero)
+            case 1: fb |= 0x7f800000u; break;                 // infinity or NaN
+            case 2: fb &= 0x80000000u; break;                 // signed zero
+            default: break;
         }
-        if (bad)
-            for (int64_t i = b0; i < b1; ++i)
-                if (!std::isfinite(x[i])) return i;
+        const float f = __uint_as_float(fb);
+        const double h1 = (double)f, h2 = f2d_bits(f);
+        if (!(isnan(h1) && isnan(h2)) && __double_as_longlong(h1) != __double_as_longlong(h2)) ++bad_f2d;
+        unsigned long long db = y;
+        const unsigned c = (unsigned)((x >> 40) & 7u);
+        if (c <= 4) {   // exponent field around the binary32 range (normal, subnormal, overflow)
+            const unsigned long long E = 850ull + (x >> 48) % 320ull;
+            db = (db & ~(0x7ffull << 52)) | (E << 52);
+            if (c == 4) db = (db & ~0x1fffffffull) | 0x10000000ull;   // exact tie at the last bit
+        } else if (c == 5) {
+            db &= ~(0x7ffull << 52);                               // binary64 subnormal
+        } else if (c == 6) {
+            db |= 0x7ffull << 52;                                  // infinity or NaN
+        }
+        const double d = __longlong_as_double((long long)db);
+        const float g1 = (float)d, g2 = d2f_bits(d);
+        if (!(isnan(g1) && isnan(g2)) && __float_as_uint(g1) != __float_as_uint(g2)) ++bad_d2f;
     }
-    return -1;
+    if (bad_f2d) atomicAdd(mis, bad_f2d);
+    if (bad_d2f) atomicAdd(mis + 1, bad_d2f);
+}
+
+__global__ void k_first_nonfinite(const double *x, long long n, unsigned long long *first) {
+    constexpr unsigned long long kExp = 0x7ff0000000000000ull;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long v = (unsigned long long)__double_as_longlong(x[i]);
+        if ((v & kExp) == kExp) atomicMin(first, (unsigned long long)i);
+    }
 }
 }  // namespace
 
 extern "C" {
+
+mts_status mts_selftest_conversions(mts_ctx *ctx, int64_t n, uint64_t seed, int64_t *mismatches) {
+    if (!ctx || !mismatches || n < 0) {
+        set_error("mts_selftest_conversions: invalid arguments");
+        return MTS_ERR_INVALID_ARG;
+    }
+    MTS_CUDA(cudaSetDevice(ctx->device));
+    unsigned long long *d = (unsigned long long *)dalloc(ctx, 2 * sizeof(unsigned long long));
+    if (!d) {
+        set_error("mts_selftest_conversions: device allocation failed");
+        return MTS_ERR_OOM;
+    }
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof h, ctx->stream);
+    if (e == cudaSuccess && n > 0) {
+        k_selftest_conv<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, ctx->stream>>>(n, seed, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, d);
+    MTS_CUDA(e);
+    mismatches[0] = (int64_t)h[0];
+    mismatches[1] = (int64_t)h[1];
+    return MTS_OK;
+}
 
 mts_status mts_read_field(mts_body *b, int32_t field, double *out, int64_t len) {
     if (!b || !out || !valid_field(field)) {
@@ -1305,17 +1372,24 @@ mts_status mts_write_field(mts_body *b, int32_t field, const double *in, int64_t
         set_error("mts_write_field: len %lld, expected %lld", (long long)len, (long long)(b->n * w));
         return MTS_ERR_INVALID_ARG;
     }
-    // the copy into the scratch buffer runs while the host checks the values;
-    // only a clean field is moved from there into the body's state
+    // the values are checked on the device once in the scratch buffer; only
+    // a clean field is moved from there into the body's state
     MTS_CUDA(cudaSetDevice(b->ctx->device));
-    MTS_CUDA(cudaMemcpyAsync(b->scratch, in, len * 8, cudaMemcpyHostToDevice, b->ctx->stream));
-    if (const int64_t t = first_nonfinite(in, len); t >= 0) {
-        MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));   // the copy has read `in`
-        set_error("mts_write_field: non-finite value at %lld", (long long)t);
+    cudaStream_t st = b->ctx->stream;
+    MTS_CUDA(cudaMemcpyAsync(b->scratch, in, len * 8, cudaMemcpyHostToDevice, st));
+    MTS_CUDA(cudaMemsetAsync(b->d_first, 0xff, sizeof(unsigned long long), st));
+    const long long blocks = std::min<long long>((len + 255) / 256, 4096);
+    k_first_nonfinite<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, st>>>(b->scratch, len, b->d_first);
+    MTS_CUDA(cudaGetLastError());
+    unsigned long long first = 0;
+    MTS_CUDA(cudaMemcpyAsync(&first, b->d_first, sizeof first, cudaMemcpyDeviceToHost, st));
+    MTS_CUDA(cudaStreamSynchronize(st));
+    if (first != ~0ull) {
+        set_error("mts_write_field: non-finite value at %lld", (long long)first);
         return MTS_ERR_NONFINITE;
     }
     MTS_TRY(scratch_to_field(b, field));
-    MTS_CUDA(cudaStreamSynchronize(b->ctx->stream));
+    MTS_CUDA(cudaStreamSynchronize(st));
     return MTS_OK;
 }
 

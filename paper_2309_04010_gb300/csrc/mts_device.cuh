@@ -10,6 +10,65 @@ namespace mts {
 template <int D> struct Pad { static constexpr int v = (D == 2) ? 2 : 4; };
 template <int D> struct MatS { static constexpr int v = (D == 2) ? 4 : 12; };
 
+// Conversions between IEEE 754 binary32 and binary64 done on the integer
+// pipe.  On this GPU a conversion to or from FP64 occupies the FP64 pipe like
+// an FP64 operation, and the FP64 pipe is the drift kernel's bound; these give
+// the same bits as the hardware conversions (round to nearest, ties to even)
+// from the formats' definitions: sign, biased exponent (bias 127 / 1023),
+// fraction (23 / 52 bits), subnormals at exponent field 0, infinities and
+// NaNs at the all-ones field (NaNs come out quiet).  mts_selftest_conversions
+// checks them against the hardware on random and edge-case bit patterns.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t s = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    uint32_t hi, lo;
+    if (e - 1u < 254u) {                       // normal
+        hi = s | ((e + 896u) << 20) | (m >> 3);
+        lo = m << 29;
+    } else if (e == 0u) {
+        if (m == 0u) {                         // signed zero
+            hi = s;
+            lo = 0u;
+        } else {                               // subnormal m 2^-149: normal in binary64
+            const int p = 31 - __clz(m);       // leading one at bit p (0..22)
+            const unsigned long long man = (unsigned long long)(m & ~(1u << p)) << (52 - p);
+            hi = s | ((uint32_t)(p + 874) << 20) | (uint32_t)(man >> 32);
+            lo = (uint32_t)man;
+        }
+    } else {                                   // infinity or NaN
+        hi = s | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u);
+        lo = m << 29;
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float d2f_bits(double d) {
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    const uint32_t s = hi & 0x80000000u;
+    const int E = (int)((hi >> 20) & 0x7ffu);
+    const uint32_t mh = hi & 0xfffffu;
+    if (E == 0x7ff) {                          // infinity or NaN
+        const uint32_t nan = (mh | lo) ? (0x400000u | (mh << 3) | (lo >> 29)) : 0u;
+        return __uint_as_float(s | 0x7f800000u | nan);
+    }
+    const int ef = E - 896;                    // binary32 exponent field of a normal result
+    if (ef >= 255) return __uint_as_float(s | 0x7f800000u);
+    if (ef >= 1) {                             // keep 23 fraction bits, round on the other 29
+        const uint32_t keep = (mh << 3) | (lo >> 29), rem = lo & 0x1fffffffu;
+        const uint32_t up = (rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u))) ? 1u : 0u;
+        return __uint_as_float(s | ((((uint32_t)ef << 23) | keep) + up));   // a carry may reach infinity
+    }
+    if (E == 0) return __uint_as_float(s);     // |d| < 2^-1022: rounds to zero
+    // subnormal (or zero) result: the 53-bit significand times 2^(E - 1075),
+    // in units of 2^-149, is sig >> (30 - ef)
+    const int sh = 30 - ef;
+    if (sh >= 54) return __uint_as_float(s);   // below half the smallest subnormal
+    const unsigned long long sig = ((unsigned long long)(mh | 0x100000u) << 32) | lo;
+    const unsigned long long q = sig >> sh, rem = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    const uint32_t up = (rem > half || (rem == half && (q & 1ull))) ? 1u : 0u;
+    return __uint_as_float(s | ((uint32_t)q + up));
+}
+
 // ------------------------------------------------------------------ loads
 template <class R> struct Vec2;
 template <> struct Vec2<float> { using T = float2; };
@@ -141,6 +200,11 @@ __device__ __forceinline__ void cp_async_wait_group() {
 
 // bulk prefetch of [g, g + bytes) into L2 (no completion to wait for; g and
 // bytes multiples of 16)
+// L2 prefetch of the line holding p (a hint: L2 is coherent, so it may be
+// issued before the data's producer has finished)
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 __device__ __forceinline__ void prefetch_l2_bulk(const void *g, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(__cvta_generic_to_global(g)),
                  "r"(bytes)

@@ -272,6 +272,10 @@ struct mts_body {
     bool has_diff;
     double D, beta, c0;
     int diff_mode;            // 0: one-pass Laplacian, 1: two-stage flux (deformed configuration)
+    // the one-pass operator's Gershgorin bound depends on the reference
+    // configuration and D only: kept for the D it was computed with
+    bool diff_amax_ok;
+    double diff_amax, diff_amax_D;
     // anisotropic kernel: positions are stored scaled by sk (X~ = s (.) X, the
     // kernel isotropic with h in those coordinates); V is the real volume
     int aniso;
@@ -283,6 +287,7 @@ struct mts_body {
     mts::Control *h_ctrl;   // pinned
     double *part_force, *part_drift;
     double *scratch;        // n x 9 doubles for field transfers
+    unsigned long long *d_first;   // first non-finite index of a written field
     double *h_stage;        // pinned staging for field transfers (n x 9)
     cudaGraphExec_t graph;
     int graph_chunk;

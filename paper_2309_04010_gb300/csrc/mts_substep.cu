@@ -109,6 +109,17 @@ __device__ __forceinline__ void unscale_F(const Args<R> &A, R (&F)[3][3]) {
 template <class R, int D, int MAT>
 __global__ void __launch_bounds__(TileThreads<R>::v) k_stress(Args<R> A) {
     chain_trigger();
+    {
+        // this particle's per-particle inputs, read after the F gather: into
+        // L2 while the previous kernel drains
+        const long long ip = blockIdx.x * (long long)A.T + threadIdx.x;
+        if (ip < A.n) {
+            prefetch_l2(A.B0 + ip * MatS<D>::v);
+            if (D == 3) prefetch_l2(A.X + ip * Pad<D>::v);
+            if (MAT != MTS_ELASTIC_SVK) prefetch_l2(A.cp + ip * 8);
+            if (A.swelling) prefetch_l2(A.c + ip);
+        }
+    }
     chain_wait();
     if (A.ctrl->done) return;
     constexpr int P = Pad<D>::v;
@@ -281,7 +292,12 @@ __global__ void __launch_bounds__(TileThreads<R>::v) k_force(Args<R> A) {
             ao[k] = acc[k] * A.inv_rho0;
             if (!((fx >> k) & 1)) {
                 v[k] += dt * ao[k];
-                a2 += (double)ao[k] * (double)ao[k];
+                if constexpr (sizeof(R) == 4) {
+                    const double ad = f2d_bits(ao[k]);   // exact widening on the integer pipe
+                    a2 += ad * ad;
+                } else {
+                    a2 += (double)ao[k] * (double)ao[k];
+                }
             }
             if (fx & kForceBit) fm[k] = A.mass * (double)ao[k];
         }
@@ -1044,48 +1060,74 @@ __global__ void __launch_bounds__(kBlock) k_drift(Args<R> A) {
     // partials of sum |v|^2 and max |v|^2; 1/2 m and the square root are
     // applied once, to the totals (max |v| = sqrt(max |v|^2) exactly)
     double v2sum = 0.0, v2max = 0.0;
+    R v2maxr = R(0);
     {
         const double dt = C->dt, ramp = C->ramp;
         const long long stride = (long long)gridDim.x * kBlock;
-        for (long long i = blockIdx.x * (long long)kBlock + threadIdx.x; i < A.n; i += stride) {
-            const uint8_t fx = A.flags[i];
-            R v[P];
-            ld_vec<R, P>(v, A.v + i * P);
-            double u[P];
-            ld_vec<double, P>(u, A.u + i * P);
-            // |v|^2 per particle in the velocity's own precision (in mixed
-            // precision a relative rounding of 2^-24 on FP32 velocities, two
-            // FP64 instructions fewer per particle); summed, maximised and
-            // compared in FP64
-            R v2r = R(0);
+        // the launch gives each thread up to kDriftPer particles (i0, i0 +
+        // stride, ...): all their loads are issued before the arithmetic
+        constexpr int kDriftPer = 4;
+        for (long long i0 = blockIdx.x * (long long)kBlock + threadIdx.x; i0 < A.n;
+             i0 += kDriftPer * stride) {
+            uint8_t fx[kDriftPer];
+            R v[kDriftPer][P];
+            double u[kDriftPer][P];
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                if ((fx >> k) & 1) {
-                    v[k] = R(0);
-                    u[k] = ramp * A.u_unit[i * P + k];
-                } else {
-                    u[k] += dt * (double)v[k];
+            for (int j = 0; j < kDriftPer; ++j) {
+                const long long i = i0 + j * stride;
+                if (i < A.n) {
+                    fx[j] = A.flags[i];
+                    ld_vec<R, P>(v[j], A.v + i * P);
+                    ld_vec<double, P>(u[j], A.u + i * P);
                 }
-                v2r += v[k] * v[k];
             }
-            const double v2 = (double)v2r;
-            st_vec<R, P>(A.v + i * P, v);
-            st_vec<double, P>(A.u + i * P, u);
-            if constexpr (sizeof(R) == 4) {
-                R uf[P];
 #pragma unroll
-                for (int k = 0; k < P; ++k) uf[k] = k < D ? (R)u[k] : R(0);   // padding stays 0
-                st_vec<R, P>(A.uf + i * P, uf);
+            for (int j = 0; j < kDriftPer; ++j) {
+                const long long i = i0 + j * stride;
+                if (i >= A.n) break;
+                // |v|^2 per particle in the velocity's own precision (in
+                // mixed precision a relative rounding of 2^-24 on FP32
+                // velocities); summed, maximised and compared in FP64.
+                // Mixed precision converts between FP32 and FP64 on the
+                // integer pipe: the same bits, off the FP64 pipe.
+                R v2r = R(0);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    if ((fx[j] >> k) & 1) {
+                        v[j][k] = R(0);
+                        u[j][k] = ramp * A.u_unit[i * P + k];
+                    } else {
+                        if constexpr (sizeof(R) == 4)
+                            u[j][k] += dt * f2d_bits(v[j][k]);
+                        else
+                            u[j][k] += dt * (double)v[j][k];
+                    }
+                    v2r += v[j][k] * v[j][k];
+                }
+                st_vec<R, P>(A.v + i * P, v[j]);
+                st_vec<double, P>(A.u + i * P, u[j]);
+                if constexpr (sizeof(R) == 4) {
+                    R uf[P];
+#pragma unroll
+                    for (int k = 0; k < P; ++k) uf[k] = k < D ? d2f_bits(u[j][k]) : R(0);   // padding stays 0
+                    st_vec<R, P>(A.uf + i * P, uf);
+                    v2sum += f2d_bits(v2r);
+                    v2maxr = fmaxf(v2maxr, v2r);       // widening is exact and monotonic
+                } else {
+                    v2sum += (double)v2r;
+                    v2max = fmax(v2max, (double)v2r);
+                }
             }
-            v2sum += v2;
-            v2max = fmax(v2max, v2);
         }
     }
+    // mixed precision: the warp's max |v|^2 taken in FP32, then widened (the
+    // same value: widening is exact and monotonic)
+    if constexpr (sizeof(R) == 4) v2max = f2d_bits(warp_max(v2maxr));
     double ke = v2sum, vmax = v2max;
     __shared__ double sh[2][kBlock / 32];
     __shared__ int is_last;
     ke = warp_sum(ke);
-    vmax = warp_max(vmax);
+    if constexpr (sizeof(R) != 4) vmax = warp_max(vmax);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
         sh[0][wid] = ke;

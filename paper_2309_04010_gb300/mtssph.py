@@ -135,6 +135,7 @@ def lib():
         "mts_read_field": [vp, i32, vp, i64],
         "mts_write_field": [vp, i32, vp, i64],
         "mts_kinetic_energy_noalloc": [vp, i32, i32, i64, d, vp, vp],
+        "mts_selftest_conversions": [vp, i64, C.c_uint64, vp],
         "mts_body_set_shapes": [vp, i32, i32],
         "mts_body_shapes": [vp, C.POINTER(i32), C.POINTER(i32)],
         "mts_body_autotune": [vp, i32, d, C.POINTER(i32), C.POINTER(i32), C.POINTER(d)],
@@ -583,6 +584,15 @@ def body_from_case(ctx: Context, case, precision: int = FP64, damp_layout: int =
     if case.tip_ids is not None and len(case.tip_ids):
         b.set_tip(case.tip_ids)
     return b
+
+
+def selftest_conversions(ctx: Context, n: int, seed: int = 1) -> tuple:
+    """mts_selftest_conversions: (FP32 -> FP64, FP64 -> FP32) mismatches of the
+    library's integer-pipe conversions against the hardware on n bit patterns."""
+    out = np.zeros(2, np.int64)
+    _check(lib().mts_selftest_conversions(ctx.handle, int(n), int(seed), _ptr(out)),
+           "mts_selftest_conversions")
+    return int(out[0]), int(out[1])
 
 
 def kinetic_energy_noalloc(v_dev_ptr: int, precision: int, dim: int, n: int, mass: float,
