@@ -120,13 +120,18 @@ __global__ void __launch_bounds__(TileThreads<R>::v) k_stress(Args<R> A) {
             if (A.swelling) prefetch_l2(A.c + ip);
         }
     }
-    chain_wait();
-    if (A.ctrl->done) return;
     constexpr int P = Pad<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
     R *sX = reinterpret_cast<R *>(smem);
     R *sU = reinterpret_cast<R *>(smem + second_off<R, P>(A.max_halo));
-    stage_halo<R, P, P>(A, sX, sU, A.uf);
+    // the halo's positions (set-up data) before the wait, u after it
+    const HaloPre<R> hp = stage_halo_pre<R, P>(A, sX);
+    chain_wait();
+    if (A.ctrl->done) {
+        cp_async_wait_all();
+        return;
+    }
+    stage_halo_post<R, P, P>(A, hp, sX, sU, A.uf);
     const long long i = blockIdx.x * (long long)A.T + threadIdx.x;
     if (i >= A.n) return;
     R F[3][3];
@@ -196,8 +201,6 @@ __device__ __forceinline__ void prefetch_group_levels(const Args<R> &A, int m0, 
 template <class R, int D>
 __global__ void __launch_bounds__(TileThreads<R>::v) k_force(Args<R> A) {
     chain_trigger();
-    chain_wait();
-    if (A.ctrl->done) return;
     constexpr int P = Pad<D>::v;
     constexpr int MS = MatS<D>::v;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -205,7 +208,14 @@ __global__ void __launch_bounds__(TileThreads<R>::v) k_force(Args<R> A) {
     // 2D: X and P B0 in two arrays
     R *sX = reinterpret_cast<R *>(smem);
     R *sP = D == 3 ? sX : reinterpret_cast<R *>(smem + second_off<R, P>(A.max_halo));
-    stage_halo<R, P, MS>(A, D == 3 ? nullptr : sX, sP, A.PB);
+    // the halo indices (and 2D positions) before the wait, P B0 after it
+    const HaloPre<R> hp = stage_halo_pre<R, P>(A, D == 3 ? nullptr : sX);
+    chain_wait();
+    if (A.ctrl->done) {
+        cp_async_wait_all();
+        return;
+    }
+    stage_halo_post<R, P, MS>(A, hp, D == 3 ? nullptr : sX, sP, A.PB);
     const long long t = blockIdx.x;
     const long long i = t * A.T + threadIdx.x;
     double amax = 0.0, fm[3] = {0.0, 0.0, 0.0};

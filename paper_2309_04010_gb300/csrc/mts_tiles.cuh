@@ -25,31 +25,63 @@ __host__ __device__ __forceinline__ size_t second_off(int max_halo) {
 // positions come from the per-tile table halo_x (computed once in FP64
 // relative to the tile's first particle), so in FP32 the separations keep
 // their relative precision however far the tile is from the body's corner.
-template <class R, int P, int NY>
-__device__ __forceinline__ int stage_halo(const Args<R> &A, R *sX, R *sY, const R *Y) {
+// Halo staging in two parts, so that the set-up data can move before the
+// previous kernel of the chain has finished: stage_halo_pre loads the first
+// kHaloPre x blockDim halo indices into registers and starts the copies of the
+// X rows (set-up data) into shared memory; stage_halo_post, after the chain
+// wait, starts the copies of the Y rows (state written by the previous
+// kernel), stages any halo entries beyond the first part, and waits for every
+// copy.  stage_halo runs both back to back.
+constexpr int kHaloPre = 4;
+
+template <class R>
+struct HaloPre {
+    long long h0;
+    int nh;
+    int g[kHaloPre];
+};
+
+template <class R, int P>
+__device__ __forceinline__ HaloPre<R> stage_halo_pre(const Args<R> &A, R *sX) {
+    HaloPre<R> h;
     const long long t = blockIdx.x;
-    const long long h0 = A.halo_off[t];
-    const int nh = (int)(A.halo_off[t + 1] - h0);
-    // indices first (independent loads), then asynchronous row copies
-    constexpr int U = 4;
-    for (int k0 = threadIdx.x; k0 < nh; k0 += U * blockDim.x) {
-        int g[U];
+    h.h0 = A.halo_off[t];
+    h.nh = (int)(A.halo_off[t + 1] - h.h0);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = k0 + u * blockDim.x;
-            g[u] = k < nh ? __ldg(A.halo_idx + h0 + k) : -1;
-        }
+    for (int u = 0; u < kHaloPre; ++u) {
+        const int k = threadIdx.x + u * blockDim.x;
+        h.g[u] = k < h.nh ? __ldg(A.halo_idx + h.h0 + k) : -1;
+    }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = k0 + u * blockDim.x;
-            if (g[u] < 0) continue;
-            if (sX) cp_async_reals<R, P>(sX + (size_t)k * P, A.halo_x + (size_t)(h0 + k) * P);
-            if (sY) cp_async_reals<R, NY>(sY + (size_t)k * NY, Y + (size_t)g[u] * NY);
-        }
+    for (int u = 0; u < kHaloPre; ++u) {
+        const int k = threadIdx.x + u * blockDim.x;
+        if (h.g[u] >= 0 && sX) cp_async_reals<R, P>(sX + (size_t)k * P, A.halo_x + (size_t)(h.h0 + k) * P);
+    }
+    return h;
+}
+
+template <class R, int P, int NY>
+__device__ __forceinline__ int stage_halo_post(const Args<R> &A, const HaloPre<R> &h, R *sX, R *sY,
+                                               const R *Y) {
+#pragma unroll
+    for (int u = 0; u < kHaloPre; ++u) {
+        const int k = threadIdx.x + u * blockDim.x;
+        if (h.g[u] >= 0 && sY) cp_async_reals<R, NY>(sY + (size_t)k * NY, Y + (size_t)h.g[u] * NY);
+    }
+    for (int k = threadIdx.x + kHaloPre * blockDim.x; k < h.nh; k += blockDim.x) {
+        const int g = __ldg(A.halo_idx + h.h0 + k);
+        if (sX) cp_async_reals<R, P>(sX + (size_t)k * P, A.halo_x + (size_t)(h.h0 + k) * P);
+        if (sY) cp_async_reals<R, NY>(sY + (size_t)k * NY, Y + (size_t)g * NY);
     }
     cp_async_wait_all();
     __syncthreads();
-    return nh;
+    return h.nh;
+}
+
+template <class R, int P, int NY>
+__device__ __forceinline__ int stage_halo(const Args<R> &A, R *sX, R *sY, const R *Y) {
+    const HaloPre<R> h = stage_halo_pre<R, P>(A, sX);
+    return stage_halo_post<R, P, NY>(A, h, sX, sY, Y);
 }
 
 // Visit the neighbour slots of one particle, reading the index stream 8
