@@ -135,6 +135,22 @@ __device__ __forceinline__ void st_vec(R *p, const R (&o)[N]) {
     }
 }
 
+// store of a velocity slot to shared memory as one access of the slot's
+// width: FP32 3D slots as a single 16-byte st.shared (left to itself, the
+// compiler splits some of these stores, and a split 16-byte store costs
+// more bank-conflict wavefronts than one 16-byte store)
+template <class R, int N>
+__device__ __forceinline__ void st_smem_vec(R *p, const R (&o)[N]) {
+    if constexpr (sizeof(R) == 4 && N == 4) {
+        const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(o[0]), "f"(o[1]),
+                     "f"(o[2]), "f"(o[3])
+                     : "memory");
+    } else {
+        st_vec<R, N>(p, o);
+    }
+}
+
 // load a D x D matrix stored with rows padded to Pad<D>
 template <class R, int D>
 __device__ __forceinline__ void ldg_mat(R (&M)[D][D], const R *p) {

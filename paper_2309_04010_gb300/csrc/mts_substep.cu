@@ -436,8 +436,8 @@ __device__ __forceinline__ void damp_pair_free(uint32_t w, R g, unsigned char *s
     // nothing: several empty lanes of a quarter-warp would store to one
     // address and replay; loads of one address are a broadcast
     if (g != R(0)) {
-        st_vec<R, P>(pa, va);
-        st_vec<R, P>(pb, vb);
+        st_smem_vec<R, P>(pa, va);
+        st_smem_vec<R, P>(pb, vb);
     }
 }
 
@@ -480,8 +480,8 @@ __device__ __forceinline__ void damp_pair_coded(uint32_t w, R g, unsigned char *
         }
     }
     if (g != R(0)) {        // empty slots store nothing (see damp_pair_free)
-        st_vec<R, P>(pa, va);
-        st_vec<R, P>(pb, vb);
+        st_smem_vec<R, P>(pa, va);
+        st_smem_vec<R, P>(pb, vb);
     }
 }
 
