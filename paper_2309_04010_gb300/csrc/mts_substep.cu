@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(TileThreads<R>::v) k_force(Args<R> A) {
 // blocks (+1 dummy slot, padded to a whole group of eight slots, 16-byte
 // aligned for cp.async), then the level slots; the pair words carry the
 // constrained axes, so no flags are staged
-constexpr int kDampChunk = 8;    // levels per chunk of the damping warp's level ring
+constexpr int kDampChunk = 4;    // levels per chunk of the damping warp's level ring
 template <class R, int D>
 struct DampSmem {
     __host__ __device__ static size_t vbytes(int mb) {
