@@ -124,7 +124,10 @@ __global__ void __launch_bounds__(TileThreads<R>::v) k_stress(Args<R> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     R *sX = reinterpret_cast<R *>(smem);
     R *sU = reinterpret_cast<R *>(smem + second_off<R, P>(A.max_halo));
-    // the halo's positions (set-up data) before the wait, u after it
+    // the halo's positions (set-up data) before the wait, u after it; the
+    // tile's neighbour slots (set-up data) into L2 meanwhile
+    if (threadIdx.x == 0 && A.tile_w[blockIdx.x] > 0)
+        prefetch_l2_bulk(A.lell + A.lell_off[blockIdx.x], (unsigned)(A.tile_w[blockIdx.x] * A.T * 2));
     const HaloPre<R> hp = stage_halo_pre<R, P>(A, sX);
     chain_wait();
     if (A.ctrl->done) {
@@ -209,6 +212,8 @@ __global__ void __launch_bounds__(TileThreads<R>::v) k_force(Args<R> A) {
     R *sX = reinterpret_cast<R *>(smem);
     R *sP = D == 3 ? sX : reinterpret_cast<R *>(smem + second_off<R, P>(A.max_halo));
     // the halo indices (and 2D positions) before the wait, P B0 after it
+    // (an L2 prefetch of the tile's neighbour slots, as in the stress kernel,
+    // made this kernel slower: 433 -> 439 us on the plate)
     const HaloPre<R> hp = stage_halo_pre<R, P>(A, D == 3 ? nullptr : sX);
     chain_wait();
     if (A.ctrl->done) {
@@ -786,7 +791,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 4) k_damp_persist(Ar
         const int nl = l1 - l0;
         const uint32_t *gab = A.pair_ab + 32LL * l0;
         const R *gg = A.pair_g + 32LL * l0;
-        // set-up data first: it does not depend on the earlier tasks
+        // set-up data first: it does not depend on the earlier tasks (the
+        // ring's later chunks stream from L2 once this prefetch has landed)
         if constexpr (RING) {
             damp_stage_chunk<R>(0, nl, (mode & 1) != 0, gab, gg, rw, rg, lane);
             damp_stage_chunk<R>(1, nl, (mode & 1) != 0, gab, gg, rw, rg, lane);
