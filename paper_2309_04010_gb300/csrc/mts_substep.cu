@@ -1082,7 +1082,7 @@ __global__ void __launch_bounds__(kBlock) k_drift(Args<R> A) {
         const long long stride = (long long)gridDim.x * kBlock;
         // the launch gives each thread up to kDriftPer particles (i0, i0 +
         // stride, ...): all their loads are issued before the arithmetic
-        constexpr int kDriftPer = 4;
+        constexpr int kDriftPer = 2;
         for (long long i0 = blockIdx.x * (long long)kBlock + threadIdx.x; i0 < A.n;
              i0 += kDriftPer * stride) {
             uint8_t fx[kDriftPer];
