@@ -228,6 +228,8 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *g, unsigned bytes) 
 }
 
 // ------------------------------------------------------------------ math
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 // square root for the neighbour loops: the hardware approximation in FP32

@@ -53,7 +53,9 @@ __device__ __forceinline__ void compute_F(const Args<R> &A, const R *sX, const R
     const int T = A.T;
     const uint16_t *row = A.lell + A.lell_off[t] + threadIdx.x;
     const int w = A.tile_w[t];
-    const R inv_h = A.inv_h, kcoef = A.kcoef;
+    // per neighbour V W'(r)/r = kcoef (1 - r/(2h))^3: the factor kcoef is
+    // applied once to the sum, and 1 - r/(2h) is one fused multiply-add
+    const R mhalf_inv_h = R(-0.5) * A.inv_h;   // exact: a power-of-two scaling
     auto accumulate = [&](const R (&xb)[P], const R (&ub)[P]) {
         R d[D], r2 = R(0);
 #pragma unroll
@@ -61,8 +63,8 @@ __device__ __forceinline__ void compute_F(const Args<R> &A, const R *sX, const R
             d[k] = xa[k] - xb[k];
             r2 += d[k] * d[k];
         }
-        const R tt = R(1) - R(0.5) * nsqrt(r2) * inv_h;
-        const R f = kcoef * tt * tt * tt;   // V W'(r)/r
+        const R tt = fma_r(nsqrt(r2), mhalf_inv_h, R(1));
+        const R f = tt * tt * tt;
 #pragma unroll
         for (int r = 0; r < D; ++r) {
             const R du = (ub[r] - ua[r]) * f;
@@ -76,6 +78,13 @@ __device__ __forceinline__ void compute_F(const Args<R> &A, const R *sX, const R
         ld_vec<R, P>(ub, sU + l * P);
         accumulate(xb, ub);
     });
+    {
+        const R kcoef = A.kcoef;
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) G[r][c] *= kcoef;
+    }
     R B[D][D];
     ldg_mat<R, D>(B, A.B0 + i * MatS<D>::v);
 #pragma unroll
